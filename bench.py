@@ -1,0 +1,318 @@
+#!/usr/bin/env python
+"""Throughput of the GB300 Friedkin-Johnsen solver: certified solves per second.
+
+One step = one complete fj_solve (ImprovedBLISOR to eps = 1e-6 with the FP64
+certificate and restarts, Section 5) of the workload's opinion vector, inputs
+resident in HBM.  The default workload is the directed R-MAT scale-22 graph
+(4,194,304 nodes, 67,108,864 generated arcs, a = 0.57, b = c = 0.19, weights
+U(0.5, 1.5) FP32, s ~ U[0, 1] FP32), FP32 push with an FP64 certificate.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+(FIFO ImprovedBLISOR) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOADS = {
+    # name: generator, precision, omega, schedule
+    "rmat22_dir": dict(gen="rmat_dir", scale=22, precision="fp32", omega=1.5),
+    "ba20k": dict(gen="ba", n=20000, precision="fp64", omega=1.5),
+    "rmat24_und": dict(gen="rmat_und", scale=24, precision="fp32", omega=1.8),
+    "rmat16_dir": dict(gen="rmat_dir", scale=16, precision="fp32", omega=1.5),
+}
+EPS = 1e-6
+METRIC = "FJ solves/s to 1e-6 rel. err (GTEPS, % HBM roofline): plain vs batched/warm-start"
+
+
+def make_workload(name, scale_override=None):
+    from fjsynth import workloads as W
+    spec = dict(WORKLOADS[name])
+    if scale_override is not None:
+        spec["scale"] = scale_override
+    if spec["gen"] == "rmat_dir":
+        g = W.rmat_directed(spec["scale"])
+        src, dst, w = g["src"], g["dst"], g["w"]
+    elif spec["gen"] == "rmat_und":
+        g = W.rmat_undirected(spec["scale"])
+        src, dst, w = W.symmetrize_arcs(g["src"], g["dst"], None)
+    else:
+        g = W.ba_graph(spec["n"], 5)
+        src, dst, w = W.symmetrize_arcs(g["src"], g["dst"], None)
+    return spec, g, src, dst, w
+
+
+def clocks_start():
+    try:
+        f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        p = subprocess.Popen(
+            ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+             "--format=csv,noheader,nounits", "-lms", "200"], stdout=f, stderr=subprocess.DEVNULL)
+        return p, f.name
+    except Exception:
+        return None, None
+
+
+def clocks_stop(p, path, device_index=0):
+    if p is None:
+        return None
+    p.terminate()
+    try:
+        p.wait(timeout=5)
+    except Exception:
+        p.kill()
+    rows = []
+    with open(path) as fh:
+        for rec in csv.reader(io.StringIO(fh.read())):
+            if len(rec) < 9:
+                continue
+            try:
+                if int(rec[0]) != device_index:
+                    continue
+                rows.append([x.strip() for x in rec])
+            except ValueError:
+                continue
+    os.unlink(path)
+    if not rows:
+        return None
+    sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+    mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+            "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ------------------------------------------------------------------ oracle arm
+
+def oracle_solve_time(name, scale, omega):
+    """One FIFO ImprovedBLISOR solve (FP64, one host thread) of the workload at `scale`."""
+    import oracle
+    spec, g, src, dst, w = make_workload(name, scale)
+    rp, col, wc = oracle.csr_from_arcs(g["n"], src, dst, w)
+    s = g["S"][0]
+    t0 = time.perf_counter()
+    z, r, pushes, upd, ok = oracle.blisor_fifo(g["n"], rp, col, wc, s, EPS, omega)
+    dt = time.perf_counter() - t0
+    return dt, int(rp[-1]), ok
+
+
+def run_reference(args):
+    world, rank, _ = dist_init()
+    if rank != 0:
+        return 0
+    spec = WORKLOADS[args.workload]
+    omega = args.omega if args.omega is not None else spec["omega"]
+    full_scale = spec.get("scale")
+    sample_scale = min(full_scale, 18) if full_scale else None
+    # nnz of the full workload for the scaling of the sample's rate
+    times = []
+    nnz_full = None
+    if full_scale:
+        import oracle
+        _, g, src, dst, w = make_workload(args.workload)
+        nnz_full = int(oracle.csr_from_arcs(g["n"], src, dst, w)[0][-1])
+    for i in range(args.warmup + args.steps):
+        dt, nnz_s, ok = oracle_solve_time(args.workload, sample_scale, omega)
+        if i >= args.warmup:
+            times.append((dt, nnz_s))
+    tot = sum(t for t, _ in times)
+    nnz_s = times[0][1]
+    scale_f = (nnz_s / nnz_full) if nnz_full else 1.0
+    value = len(times) / tot * scale_f
+    sample = (f"FIFO ImprovedBLISOR (omega={omega}, eps={EPS}) full solves of the same generator at "
+              f"scale {sample_scale} (nnz {nnz_s}), rate scaled by nnz {nnz_s}/{nnz_full}"
+              if nnz_full else f"full FIFO solves of the workload (omega={omega})")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value if value else None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "omega": omega, "eps": EPS},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_gpu(args):
+    import torch
+
+    world, rank, local = dist_init()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2507_14864_gb300 import capi
+
+    spec, g, src, dst, w = make_workload(args.workload)
+    n = g["n"]
+    omega = args.omega if args.omega is not None else spec["omega"]
+    prec = capi.FJ_PREC_FP32 if spec["precision"] == "fp32" else capi.FJ_PREC_FP64
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    src_d = torch.from_numpy(src).to(dev)
+    dst_d = torch.from_numpy(dst).to(dev)
+    w_d = torch.from_numpy(w).to(dev) if w is not None else None
+    G = capi.Graph.from_arcs(n, src_d, dst_d, w_d, directed=g["directed"])
+    del src_d, dst_d, w_d
+    ginfo = G.info()
+    s_host = g["S"][0]
+    s_d = torch.from_numpy(s_host).to(dev)
+    z_d = torch.empty_like(s_d)
+    opts = dict(eps=EPS, omega=omega, precision=prec, schedule=args.schedule)
+    if args.tail_rows:
+        opts["tail_rows"] = args.tail_rows
+    if args.check_every:
+        opts["check_every"] = args.check_every
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        G.solve(s_d, out=z_d, **opts)
+    barrier()
+    clk, clk_path = clocks_start() if rank == 0 else (None, None)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    infos = []
+    ev0.record(stream)
+    for _ in range(args.steps):
+        _, info, _ = G.solve(s_d, out=z_d, **opts)
+        infos.append(info[0])
+    ev1.record(stream)
+    barrier()
+    clocks = clocks_stop(clk, clk_path, local) if rank == 0 else None
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * args.steps / (ms / 1e3)
+    assert all(i["converged"] == 1 for i in infos), "a timed solve did not certify"
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    s_pin = torch.from_numpy(s_host).pin_memory().numpy()
+    z_pin = torch.empty(n, dtype=torch.float64).pin_memory().numpy()
+    G.solve(s_pin, out=z_pin, **opts)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        G.solve(s_pin, out=z_pin, **opts)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * args.steps / e2e_s
+
+    # roofline of the push kernel: algorithmic bytes over CUDA-event time of its launches
+    _, pinfo, _ = G.solve(s_d, out=z_d, profile=1, **opts)
+    p = pinfo[0]
+    peak, peak_kind = measured_peak_hbm()
+    achieved = p["push_bytes"] / (p["push_ms"] / 1e3) / 1e9 if p["push_ms"] > 0 else None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None, "traffic": None,
+                "kernel": "k_pull (push round)", "peak_source": peak_kind,
+                "bytes_per_launch": p["push_bytes"] / max(1, p["push_launches"]),
+                "avg_launch_us": 1e3 * p["push_ms"] / max(1, p["push_launches"])}
+    info0 = infos[-1]
+    detail = {"sweeps": info0["sweeps"], "pushes": info0["pushes"], "edges": info0["edges"],
+              "refine_passes": info0["refine_passes"], "resid_rel_max": info0["resid_rel_max"],
+              "eps_prime": info0["eps_prime"], "gteps": info0["edges"] / (ms_per_step / 1e3) / 1e9,
+              "ncolours": G.info()["ncolours"]}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        dt, nnz_c, ok = oracle_solve_time(args.workload, args.cpu_scale, omega)
+        scale_f = nnz_c / ginfo["nnz"]
+        cpu = {"value": scale_f / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
+               "sample": (f"one FIFO ImprovedBLISOR solve (omega={omega}, eps={EPS}, FP64, one host thread) of "
+                          + ("the full workload" if args.cpu_scale is None else
+                             f"the same generator at scale {args.cpu_scale}, rate scaled by nnz "
+                             f"{nnz_c}/{ginfo['nnz']}") + f", {dt:.1f} s")}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if prec == capi.FJ_PREC_FP32 else "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "n": n, "nnz": ginfo["nnz"], "directed": g["directed"],
+                       "omega": omega, "eps": EPS, "schedule": "multicolour" if args.schedule != 1 else "jacobi",
+                       "precision": "FP32 push, FP64 estimate and certificate" if prec == capi.FJ_PREC_FP32
+                       else "FP64", "l2": "inputs larger than L2 (CSR %.2f GB)" % (
+                           ginfo["nnz"] * (8 if w is not None else 4) / 1e9),
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
+            "gpu_launches": int(sum(i["launches"] for i in infos)),
+            "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "detail": detail,
+        }
+        print(json.dumps(line), flush=True)
+    G.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rmat22_dir", choices=sorted(WORKLOADS))
+    ap.add_argument("--omega", type=float, default=None)
+    ap.add_argument("--schedule", type=int, default=2, help="1 Jacobi rounds, 2 multicolour")
+    ap.add_argument("--tail-rows", type=int, default=0)
+    ap.add_argument("--check-every", type=int, default=0)
+    ap.add_argument("--cpu-scale", type=int, default=None,
+                    help="R-MAT scale of the CPU-baseline sample (default: the full workload)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,255 @@
+/*
+ * fj.h - C ABI of the GB300 Friedkin-Johnsen solver.
+ *
+ * The library computes the Friedkin-Johnsen equilibrium z = (I + L)^{-1} s
+ * (Lemma 1; Eq. 1 of Section 3.3) with the deterministic local residual push
+ * of Section 5 (Alg. 1-3: BoundLocalIter, ImprovedBLI, BoundLocalIterSOR),
+ * certifies it with an FP64 residual (Lemmas 3-5), and evaluates the four
+ * measures of Table 1.  Every step runs in CUDA kernels on one GPU.
+ *
+ * Graph convention.  A graph is a CSR matrix A with n rows: row u lists the
+ * nodes u listens to, a_uj = w[k] > 0 (1 when w == NULL).  d_u = sum_j a_uj is
+ * the weighted out-degree and L = D - A, so node u's FJ update is
+ * z_u <- (s_u + sum_j a_uj z_j) / (1 + d_u) (Eq. 1).  An undirected graph is
+ * passed as a symmetric CSR (both arcs of every edge, equal weights).  Graphs
+ * are simple (Section 3.2): no self-loops, no repeated (u, j) in a row.
+ *
+ * Memory.  Every array argument is a plain pointer; `mem` says whether the
+ * pointers of that call are host (FJ_MEM_HOST) or device (FJ_MEM_DEVICE)
+ * memory.  The caller owns all arrays it passes; the library never keeps a
+ * caller pointer after a call returns.  A graph handle owns its device copy
+ * of the CSR and every derived array and scratch buffer; fj_graph_destroy
+ * frees them.  Work is issued on the CUDA stream given (NULL = legacy default
+ * stream); calls return after their work is complete on that stream unless
+ * stated otherwise.
+ *
+ * Errors.  Every call returns an fj_status.  Arguments are checked before any
+ * work; a bad argument returns FJ_ERR_INVALID_ARG and leaves outputs
+ * untouched.  A CUDA failure returns FJ_ERR_CUDA.  fj_last_error() gives a
+ * one-line description of the last failure on the calling thread.  No call
+ * aborts the process, traps on the device or waits without a bound.
+ *
+ * A handle is not thread-safe: calls on one handle must not overlap.
+ * Separate handles are independent.
+ */
+#ifndef FJ_H
+#define FJ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fj_graph fj_graph;
+
+typedef enum {
+    FJ_OK = 0,
+    FJ_ERR_INVALID_ARG = 1,   /* an argument or the CSR failed validation */
+    FJ_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+    FJ_ERR_OOM = 3,           /* device allocation failed */
+    FJ_ERR_NOT_CONVERGED = 4, /* sweep or refinement cap reached; outputs hold the partial result */
+    FJ_ERR_DIVERGED = 5,      /* residual became non-finite (over-relaxation on a directed graph) */
+    FJ_ERR_UNSUPPORTED = 6,   /* valid request this build does not serve */
+    FJ_ERR_TIMEOUT = 7        /* a bounded device-side wait gave up; the result is not valid */
+} fj_status;
+
+enum { FJ_MEM_HOST = 0, FJ_MEM_DEVICE = 1 };
+
+/* Arithmetic of the bulk push.  FP64: residual, increments and estimate in
+ * FP64.  FP32: residual, thresholds, increments and all gathered values in
+ * FP32; the estimate accumulates in FP64 and the certificate (and any
+ * refinement restart) is computed in FP64. */
+enum { FJ_PREC_FP64 = 0, FJ_PREC_FP32 = 1 };
+
+/* Order in which pushes are applied.
+ *  JACOBI      : synchronous rounds - every node above threshold pushes at
+ *                once from the round-start residuals (the round view of the
+ *                proof of Theorem 1).  Requires omega <= 1.
+ *  MULTICOLOUR : Gauss-Seidel/SOR order (Theorem 2, Eqs. sor1-sor3) realised
+ *                as colour classes of the symmetrised graph; each class is an
+ *                independent set, so its nodes push concurrently.  The
+ *                smallest classes are merged into one final block that takes
+ *                an unrelaxed (omega <= 1) Jacobi step.  Any omega in (0, 2).
+ *  AUTO        : MULTICOLOUR. */
+enum { FJ_SCHED_AUTO = 0, FJ_SCHED_JACOBI = 1, FJ_SCHED_MULTICOLOUR = 2 };
+
+typedef struct {
+    double eps;          /* relative error parameter epsilon, in (0, 1) */
+    double omega;        /* relaxation factor, in (0, 2); 1 = BoundLocalIter */
+    double c;            /* shift constant c of Alg. 2 (default 1e-5) */
+    double sigma;        /* threshold sigma of Alg. 2 (default 1e-5) */
+    int precision;       /* FJ_PREC_* */
+    int schedule;        /* FJ_SCHED_* */
+    int64_t max_sweeps;  /* cap on rounds/sweeps per refinement pass (default 100000) */
+    int max_refine;      /* cap on FP64 certify-and-restart passes (default 8) */
+    int tail_rows;       /* MULTICOLOUR: classes with fewer rows than this join the tail block
+                            (0 = library default) */
+    int check_every;     /* sweeps between host checks of the stop flag (0 = default 8) */
+    int profile;         /* 1: time every launch of the push kernel with CUDA events on `stream`
+                            and report it in fj_solve_info (adds event overhead; off by default) */
+    void *stream;        /* cudaStream_t to run on; NULL = default stream */
+} fj_solve_opts;
+
+/* Per-solve report (per graph for a ragged handle, per vector for a batch). */
+typedef struct {
+    int64_t sweeps;          /* rounds (JACOBI) or sweeps (MULTICOLOUR), all passes */
+    int64_t pushes;          /* node pushes */
+    int64_t edges;           /* residual updates: sum of in-degrees of pushed nodes */
+    int32_t refine_passes;   /* FP64 certify passes that restarted the push */
+    int32_t converged;       /* 1 when the certificate below holds */
+    double c_eff;            /* shift used: c + max(0, -min s) */
+    double eps_prime;        /* sigma * eps / (c + sigma) (Alg. 2) */
+    double resid_inf;        /* max_v |r_v|, r = s' - (I + L) zhat' in FP64 */
+    double resid_rel_max;    /* max_v |r_v| / s'_v; certificate holds when <= eps_prime */
+    double z_inf;            /* max_v |z_v| */
+    double err_bound;        /* max_v |z_v - z*_v| <= resid_inf (Lemma 5 with a
+                                row-stochastic nonnegative (I + L)^{-1}) */
+    int64_t launches;        /* kernels this call launched (all kinds) */
+    int64_t push_launches;   /* launches of the push (pull-round) kernel */
+    double push_ms;          /* profile = 1: summed CUDA-event time of the push launches */
+    double push_bytes;       /* algorithmic bytes of the push launches: per nonzero the column,
+                                weight and gathered increment; per row the offsets, residual
+                                read/write, threshold, 1/(1+d) and increment write; per push
+                                the in-degree and the FP64 estimate read/write */
+} fj_solve_info;
+
+/* The measures of Table 1 (Section 3.4). */
+typedef struct {
+    double P;       /* polarization  sum_i (z_i - mean z)^2 */
+    double D;       /* disagreement  sum over edges a_ij (z_i - z_j)^2; undirected edges once */
+    double I;       /* internal conflict sum_i (z_i - s_i)^2 */
+    double C;       /* controversy   sum_i z_i^2 */
+    double mean_z;  /* (1/n) sum_i z_i */
+} fj_metrics_out;
+
+/* Defaults: eps 1e-6, omega 1, c = sigma = 1e-5 (Section 6 settings), FP64,
+ * AUTO, max_sweeps 100000, max_refine 8, stream NULL. */
+void fj_solve_opts_default(fj_solve_opts *opts);
+
+const char *fj_status_string(fj_status s);
+const char *fj_last_error(void);
+
+/*
+ * fj_graph_create - device graph from a CSR (Section 3.2 matrices A, D, L).
+ * n >= 1 rows; row_ptr[n+1] (int64, row_ptr[0] = 0, nondecreasing), col[nnz]
+ * (int32 in [0, n)), w[nnz] (float32 > 0, finite) or NULL for unit weights.
+ * directed = 0 declares a symmetric CSR.  Each row must be strictly
+ * increasing (sorted, no repeats) and hold no self-loop.  The CSR is copied;
+ * validation runs on the GPU and a violation returns FJ_ERR_INVALID_ARG.
+ * Derived on the device: FP64 out-degrees, 1/(1+d) in FP32 and FP64,
+ * in-degrees and, for directed graphs, the transposed CSR.  nnz < 2^31.
+ */
+fj_status fj_graph_create(int64_t n, const int64_t *row_ptr, const int32_t *col, const float *w,
+                          int directed, int mem, void *stream, fj_graph **out);
+
+/*
+ * fj_graph_create_from_arcs - graph ingest from an arc list (src[m], dst[m],
+ * optional w[m]); arc e means src[e] listens to dst[e].  Self-loops are
+ * dropped; of repeated (src, dst) arcs the first in array order is kept
+ * (Section 3.2: simple graphs).  The rows come out sorted.  For an undirected
+ * graph pass both arcs of every edge and directed = 0.
+ */
+fj_status fj_graph_create_from_arcs(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                                    const float *w, int directed, int mem, void *stream,
+                                    fj_graph **out);
+
+/*
+ * fj_graph_create_ragged - a batch of `ngraphs` independent graphs held as
+ * one block-diagonal CSR.  node_offsets[ngraphs+1] (int64, starts at 0,
+ * strictly increasing) gives each graph's node range; the CSR uses global
+ * node ids and every arc must stay inside its graph.  Solves and metrics on
+ * the handle report one fj_solve_info / fj_metrics_out per graph; each graph
+ * gets its own shift c_eff.
+ */
+fj_status fj_graph_create_ragged(int ngraphs, const int64_t *node_offsets, const int64_t *row_ptr,
+                                 const int32_t *col, const float *w, int directed, int mem,
+                                 void *stream, fj_graph **out);
+
+void fj_graph_destroy(fj_graph *g);
+
+/* Sizes: n, nnz, number of graphs (1 unless ragged), number of colour classes
+ * (0 until a MULTICOLOUR solve or fj_graph_colour has built them). */
+fj_status fj_graph_info(const fj_graph *g, int64_t *n, int64_t *nnz, int *ngraphs, int *ncolours);
+
+/*
+ * fj_graph_export - copy the device CSR back: row_ptr[n+1], col[nnz], w[nnz]
+ * (w ignored when the graph is unweighted).  transposed = 1 exports the
+ * in-neighbour CSR (row v lists every u with a_uv > 0 in ascending u).
+ * Any output pointer may be NULL.  deg64[n] receives the FP64 out-degrees.
+ */
+fj_status fj_graph_export(const fj_graph *g, int transposed, int64_t *row_ptr, int32_t *col,
+                          float *w, double *deg64, int mem, void *stream);
+
+/*
+ * fj_graph_colour - greedy colouring of the symmetrised graph (u ~ v when
+ * a_uv > 0 or a_vu > 0) in largest-degree-first order (ties: higher 32 bits of
+ * SplitMix64(v) first, then lower v), computed by a Jones-Plassmann kernel;
+ * the result equals the sequential greedy colouring in that order.  Colour
+ * classes are independent sets, so sweeping them in turn is a Gauss-Seidel
+ * order (Theorem 2).  colour[n] (int32) may be NULL; *ncolours may be NULL.
+ */
+fj_status fj_graph_colour(fj_graph *g, int32_t *colour, int *ncolours, int mem, void *stream);
+
+/*
+ * fj_solve - ImprovedBLISOR (Alg. 3 with the shift of Alg. 2) on the GPU.
+ * s[n] (FP64) innate opinions; z_out[n] (FP64) receives
+ * zhat = (push estimate of (I+L)^{-1}(s + c_eff)) - c_eff.  On FJ_OK the FP64
+ * certificate |r_v| <= eps' s'_v holds for every node, which gives
+ * |z_v - zhat_v| <= eps' (z_v + c_eff) (Lemma 5).  info (may be NULL) gets
+ * one record per graph.  FJ_ERR_NOT_CONVERGED / FJ_ERR_DIVERGED still write
+ * z_out and info.
+ */
+fj_status fj_solve(fj_graph *g, const double *s, const fj_solve_opts *opts, double *z_out,
+                   fj_solve_info *info, int mem);
+
+/*
+ * fj_solve_warm - as fj_solve, but the push starts from the estimate z0[n]
+ * (FP64) instead of zero: the initial residual is r = s' - (I + L)(z0 + c_eff),
+ * computed in FP64, and pushes use the |r| test of Alg. 3, so any start
+ * converges to the same certificate (Lemmas 3 and 5).
+ */
+fj_status fj_solve_warm(fj_graph *g, const double *s, const double *z0, const fj_solve_opts *opts,
+                        double *z_out, fj_solve_info *info, int mem);
+
+/*
+ * fj_solve_batch - k opinion vectors on one graph as one multi-right-hand-side
+ * push.  S and Z_out are node-major [n][k] FP64 (element (v, j) at v*k + j);
+ * 1 <= k <= 64.  A node is visited when any of its k residuals is above its
+ * threshold; each vector keeps its own shift, thresholds and certificate.
+ * info (may be NULL) gets k records.
+ */
+fj_status fj_solve_batch(fj_graph *g, const double *S, int k, const fj_solve_opts *opts,
+                         double *Z_out, fj_solve_info *info, int mem);
+
+/*
+ * fj_metrics - P, D, I, C and mean z of Table 1 for opinions s[n] and
+ * equilibrium z[n] (FP64), summed in FP64 in a fixed order (deterministic).
+ * out gets one record per graph (ngraphs for a ragged handle).
+ */
+fj_status fj_metrics(fj_graph *g, const double *s, const double *z, fj_metrics_out *out, int mem,
+                     void *stream);
+
+/*
+ * fj_frontier - the push frontier F = {v : |r_v| > h_v} (strict test of Alg. 1
+ * and Alg. 3) as ascending node ids, by warp-ballot and shared-memory
+ * compaction with a decoupled look-back across thread blocks.  precision
+ * selects FP64 or FP32 r and h.  r, h, list and count are DEVICE pointers;
+ * list must hold n entries; *count (int64, device) receives |F|.
+ */
+fj_status fj_frontier(int64_t n, const void *r, const void *h, int precision, int32_t *list,
+                      int64_t *count, void *stream);
+
+/*
+ * fj_residual - FP64 residual r[n] = s' - (I + L) zhat' with s' = s + c_eff,
+ * zhat' = z + c_eff, for caller-supplied s, z (FP64) and shift c_eff; the
+ * quantity of Lemma 3 used by the certificate.
+ */
+fj_status fj_residual(fj_graph *g, const double *s, const double *z, double c_eff, double *r,
+                      int mem, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FJ_H */

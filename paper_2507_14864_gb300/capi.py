@@ -1,0 +1,328 @@
+"""Thin Python binding of the C ABI in ``include/fj.h`` (argument marshalling only).
+
+Every computation runs in ``libfj.so``'s CUDA kernels.  Arrays may be numpy
+arrays (host memory) or CUDA torch tensors (device memory); the library is
+told which through the ``mem`` argument of each call.  There is no fallback:
+if ``libfj.so`` has not been built, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libfj.so")
+
+FJ_OK, FJ_ERR_INVALID_ARG, FJ_ERR_CUDA, FJ_ERR_OOM, FJ_ERR_NOT_CONVERGED, FJ_ERR_DIVERGED, \
+    FJ_ERR_UNSUPPORTED, FJ_ERR_TIMEOUT = range(8)
+FJ_MEM_HOST, FJ_MEM_DEVICE = 0, 1
+FJ_PREC_FP64, FJ_PREC_FP32 = 0, 1
+FJ_SCHED_AUTO, FJ_SCHED_JACOBI, FJ_SCHED_MULTICOLOUR = 0, 1, 2
+
+EXPORTED = [
+    "fj_solve_opts_default", "fj_status_string", "fj_last_error", "fj_graph_create",
+    "fj_graph_create_from_arcs", "fj_graph_create_ragged", "fj_graph_destroy", "fj_graph_info",
+    "fj_graph_export", "fj_graph_colour", "fj_solve", "fj_solve_warm", "fj_solve_batch",
+    "fj_metrics", "fj_frontier", "fj_residual",
+]
+
+
+class fj_solve_opts(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("omega", ctypes.c_double), ("c", ctypes.c_double),
+                ("sigma", ctypes.c_double), ("precision", ctypes.c_int), ("schedule", ctypes.c_int),
+                ("max_sweeps", ctypes.c_int64), ("max_refine", ctypes.c_int), ("tail_rows", ctypes.c_int),
+                ("check_every", ctypes.c_int), ("profile", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class fj_solve_info(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_int64), ("pushes", ctypes.c_int64), ("edges", ctypes.c_int64),
+                ("refine_passes", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("c_eff", ctypes.c_double), ("eps_prime", ctypes.c_double), ("resid_inf", ctypes.c_double),
+                ("resid_rel_max", ctypes.c_double), ("z_inf", ctypes.c_double), ("err_bound", ctypes.c_double),
+                ("launches", ctypes.c_int64), ("push_launches", ctypes.c_int64), ("push_ms", ctypes.c_double),
+                ("push_bytes", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class fj_metrics_out(ctypes.Structure):
+    _fields_ = [("P", ctypes.c_double), ("D", ctypes.c_double), ("I", ctypes.c_double),
+                ("C", ctypes.c_double), ("mean_z", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """The loaded ``libfj.so`` with argument types declared; raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                           "(the CUDA extension is required; there is no CPU path)")
+    L = ctypes.CDLL(LIB_PATH)
+    VP, I64, I32, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    st = ctypes.c_int
+    L.fj_solve_opts_default.argtypes = [ctypes.POINTER(fj_solve_opts)]
+    L.fj_solve_opts_default.restype = None
+    L.fj_status_string.argtypes = [st]
+    L.fj_status_string.restype = ctypes.c_char_p
+    L.fj_last_error.argtypes = []
+    L.fj_last_error.restype = ctypes.c_char_p
+    L.fj_graph_create.argtypes = [I64, VP, VP, VP, I32, I32, VP, ctypes.POINTER(VP)]
+    L.fj_graph_create_from_arcs.argtypes = [I64, I64, VP, VP, VP, I32, I32, VP, ctypes.POINTER(VP)]
+    L.fj_graph_create_ragged.argtypes = [I32, VP, VP, VP, VP, I32, I32, VP, ctypes.POINTER(VP)]
+    L.fj_graph_destroy.argtypes = [VP]
+    L.fj_graph_destroy.restype = None
+    L.fj_graph_info.argtypes = [VP, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I32),
+                                ctypes.POINTER(I32)]
+    L.fj_graph_export.argtypes = [VP, I32, VP, VP, VP, VP, I32, VP]
+    L.fj_graph_colour.argtypes = [VP, VP, ctypes.POINTER(I32), I32, VP]
+    L.fj_solve.argtypes = [VP, VP, ctypes.POINTER(fj_solve_opts), VP, VP, I32]
+    L.fj_solve_warm.argtypes = [VP, VP, VP, ctypes.POINTER(fj_solve_opts), VP, VP, I32]
+    L.fj_solve_batch.argtypes = [VP, VP, I32, ctypes.POINTER(fj_solve_opts), VP, VP, I32]
+    L.fj_metrics.argtypes = [VP, VP, VP, VP, I32, VP]
+    L.fj_frontier.argtypes = [I64, VP, VP, I32, VP, VP, VP]
+    L.fj_residual.argtypes = [VP, VP, VP, D, VP, I32, VP]
+    for name in EXPORTED:
+        if name not in ("fj_solve_opts_default", "fj_graph_destroy", "fj_status_string", "fj_last_error"):
+            getattr(L, name).restype = st
+    _lib = L
+    return L
+
+
+class FJError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = lib().fj_last_error().decode(errors="replace")
+        name = lib().fj_status_string(status).decode()
+        super().__init__(f"{where}: {name} ({msg})")
+        self.status = status
+
+
+def _check(status: int, where: str, allow=()):
+    if status != FJ_OK and status not in allow:
+        raise FJError(status, where)
+    return status
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _mem_of(*arrays):
+    kinds = set()
+    for a in arrays:
+        if a is None:
+            continue
+        if _is_torch(a):
+            if not a.is_cuda:
+                raise ValueError("torch tensors passed to libfj must live on the GPU")
+            if not a.is_contiguous():
+                raise ValueError("tensors must be contiguous")
+            kinds.add(FJ_MEM_DEVICE)
+        else:
+            kinds.add(FJ_MEM_HOST)
+    if len(kinds) > 1:
+        raise ValueError("mix of host and device arrays in one call")
+    return kinds.pop() if kinds else FJ_MEM_HOST
+
+
+def _ptr(a, dtype=None):
+    if a is None:
+        return None
+    if _is_torch(a):
+        return a.data_ptr()
+    if dtype is not None and a.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {a.dtype}")
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("arrays must be C-contiguous")
+    return a.ctypes.data
+
+
+def current_stream():
+    """The current torch CUDA stream handle (or None when CUDA is unavailable)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return None
+
+
+def default_opts(**kw) -> fj_solve_opts:
+    o = fj_solve_opts()
+    lib().fj_solve_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    if "stream" not in kw:
+        o.stream = current_stream()
+    return o
+
+
+class Graph:
+    """Owns an ``fj_graph`` handle (device CSR, derived arrays and solve scratch)."""
+
+    def __init__(self, handle):
+        self._h = ctypes.c_void_p(handle)
+
+    # ------------------------------------------------------------ creation
+    @classmethod
+    def from_csr(cls, n, row_ptr, col, w=None, directed=False, stream=None):
+        mem = _mem_of(row_ptr, col, w)
+        h = ctypes.c_void_p()
+        _check(lib().fj_graph_create(int(n), _ptr(row_ptr, np.int64), _ptr(col, np.int32),
+                                     _ptr(w, np.float32), 1 if directed else 0, mem,
+                                     stream if stream is not None else current_stream(), ctypes.byref(h)),
+               "fj_graph_create")
+        return cls(h.value)
+
+    @classmethod
+    def from_arcs(cls, n, src, dst, w=None, directed=False, stream=None):
+        mem = _mem_of(src, dst, w)
+        h = ctypes.c_void_p()
+        m = int(src.shape[0])
+        _check(lib().fj_graph_create_from_arcs(int(n), m, _ptr(src, np.int32), _ptr(dst, np.int32),
+                                               _ptr(w, np.float32), 1 if directed else 0, mem,
+                                               stream if stream is not None else current_stream(),
+                                               ctypes.byref(h)), "fj_graph_create_from_arcs")
+        return cls(h.value)
+
+    @classmethod
+    def ragged(cls, node_offsets, row_ptr, col, w=None, directed=False, stream=None):
+        mem = _mem_of(node_offsets, row_ptr, col, w)
+        h = ctypes.c_void_p()
+        ng = int(node_offsets.shape[0]) - 1
+        _check(lib().fj_graph_create_ragged(ng, _ptr(node_offsets, np.int64), _ptr(row_ptr, np.int64),
+                                            _ptr(col, np.int32), _ptr(w, np.float32), 1 if directed else 0,
+                                            mem, stream if stream is not None else current_stream(),
+                                            ctypes.byref(h)), "fj_graph_create_ragged")
+        return cls(h.value)
+
+    def close(self):
+        if self._h and self._h.value:
+            lib().fj_graph_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    # ------------------------------------------------------------ queries
+    def info(self):
+        n, nnz = ctypes.c_int64(), ctypes.c_int64()
+        ng, nc = ctypes.c_int(), ctypes.c_int()
+        _check(lib().fj_graph_info(self._h, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(ng),
+                                   ctypes.byref(nc)), "fj_graph_info")
+        return dict(n=n.value, nnz=nnz.value, ngraphs=ng.value, ncolours=nc.value)
+
+    def export(self, transposed=False, weights=True):
+        inf = self.info()
+        n, nnz = inf["n"], inf["nnz"]
+        rp = np.empty(n + 1, np.int64)
+        col = np.empty(nnz, np.int32)
+        w = np.empty(nnz, np.float32) if weights else None
+        deg = np.empty(n, np.float64)
+        _check(lib().fj_graph_export(self._h, 1 if transposed else 0, _ptr(rp), _ptr(col), _ptr(w), _ptr(deg),
+                                     FJ_MEM_HOST, current_stream()), "fj_graph_export")
+        return rp, col, w, deg
+
+    def colour(self):
+        n = self.info()["n"]
+        out = np.empty(n, np.int32)
+        k = ctypes.c_int()
+        _check(lib().fj_graph_colour(self._h, _ptr(out), ctypes.byref(k), FJ_MEM_HOST, current_stream()),
+               "fj_graph_colour")
+        return out, k.value
+
+    # ------------------------------------------------------------ compute
+    def solve(self, s, out=None, z0=None, allow_unconverged=False, **opts):
+        """fj_solve / fj_solve_warm.  Returns (z, [fj_solve_info per graph], status)."""
+        o = default_opts(**opts)
+        ng = self.info()["ngraphs"]
+        infos = (fj_solve_info * ng)()
+        mem = _mem_of(s, out, z0)
+        if out is None:
+            if mem == FJ_MEM_DEVICE:
+                import torch
+                out = torch.empty_like(s)
+            else:
+                out = np.empty_like(np.asarray(s, np.float64))
+        if z0 is None:
+            st = lib().fj_solve(self._h, _ptr(s, np.float64), ctypes.byref(o), _ptr(out, np.float64), infos, mem)
+            where = "fj_solve"
+        else:
+            st = lib().fj_solve_warm(self._h, _ptr(s, np.float64), _ptr(z0, np.float64), ctypes.byref(o),
+                                     _ptr(out, np.float64), infos, mem)
+            where = "fj_solve_warm"
+        allow = (FJ_ERR_NOT_CONVERGED, FJ_ERR_DIVERGED) if allow_unconverged else ()
+        _check(st, where, allow)
+        return out, [i.as_dict() for i in infos], st
+
+    def solve_batch(self, S, out=None, allow_unconverged=False, **opts):
+        """fj_solve_batch on node-major S[n, k].  Returns (Z, [info per vector], status)."""
+        o = default_opts(**opts)
+        k = int(S.shape[1])
+        infos = (fj_solve_info * k)()
+        mem = _mem_of(S, out)
+        if out is None:
+            if mem == FJ_MEM_DEVICE:
+                import torch
+                out = torch.empty_like(S)
+            else:
+                out = np.empty_like(S)
+        st = lib().fj_solve_batch(self._h, _ptr(S, np.float64), k, ctypes.byref(o), _ptr(out, np.float64),
+                                  infos, mem)
+        allow = (FJ_ERR_NOT_CONVERGED, FJ_ERR_DIVERGED) if allow_unconverged else ()
+        _check(st, "fj_solve_batch", allow)
+        return out, [i.as_dict() for i in infos], st
+
+    def metrics(self, s, z):
+        ng = self.info()["ngraphs"]
+        outs = (fj_metrics_out * ng)()
+        mem = _mem_of(s, z)
+        _check(lib().fj_metrics(self._h, _ptr(s, np.float64), _ptr(z, np.float64), outs, mem, current_stream()),
+               "fj_metrics")
+        res = [m.as_dict() for m in outs]
+        return res[0] if ng == 1 else res
+
+    def residual(self, s, z, c_eff):
+        mem = _mem_of(s, z)
+        if mem == FJ_MEM_DEVICE:
+            import torch
+            r = torch.empty_like(s)
+        else:
+            r = np.empty(np.asarray(s).shape[0], np.float64)
+        _check(lib().fj_residual(self._h, _ptr(s, np.float64), _ptr(z, np.float64), float(c_eff), _ptr(r), mem,
+                                 current_stream()), "fj_residual")
+        return r
+
+
+def frontier(r, h):
+    """fj_frontier on CUDA tensors r, h (float32 or float64).  Returns (list tensor, count)."""
+    import torch
+    n = int(r.shape[0])
+    prec = FJ_PREC_FP32 if r.dtype == torch.float32 else FJ_PREC_FP64
+    if h.dtype != r.dtype:
+        raise TypeError("r and h must share a dtype")
+    lst = torch.empty(max(n, 1), dtype=torch.int32, device=r.device)
+    cnt = torch.zeros(1, dtype=torch.int64, device=r.device)
+    _check(lib().fj_frontier(n, r.data_ptr(), h.data_ptr(), prec, lst.data_ptr(), cnt.data_ptr(),
+                             current_stream()), "fj_frontier")
+    c = int(cnt.item())
+    return lst[:c], c

@@ -1,0 +1,102 @@
+// Host-side structures of a graph handle and the host functions shared
+// between the library's translation units.
+#pragma once
+
+#include <vector>
+
+#include "fj_sort.cuh"
+
+namespace fj {
+
+// Row blocks: rows [blk_row[b], blk_row[b+1]) form block b.  A block either
+// holds at most kBlockRows rows whose nonzeros fit in 2*kBlockNnz (staged in
+// shared memory), or is a single long row.
+constexpr int kBlockNnz = 2048;
+constexpr int kBlockRows = 512;
+
+// One CSR resident on the device plus the per-row arrays the push needs.
+struct DevCSR {
+    int64_t n = 0, nnz = 0;
+    int64_t *row_ptr = nullptr;
+    int32_t *col = nullptr;
+    float *w = nullptr;        // nullptr = unit weights
+    double *deg64 = nullptr;   // weighted out-degree d_u (FP64)
+    float *inv32 = nullptr;    // float(1 / (1 + d_u))
+    double *inv64 = nullptr;   // 1 / (1 + d_u)
+    int32_t *indeg = nullptr;  // number of in-neighbours (residual updates per push)
+    int32_t *graph_of = nullptr;  // ragged: graph id of each row (nullptr for one graph)
+    int32_t *blk_row = nullptr;   // nblocks + 1 entries
+    int64_t nblocks = 0;
+    std::vector<int64_t> seg_blk;  // host: block ranges of forced segments (classes / graphs)
+};
+
+// Multicolour order: classes of the symmetrised graph, nodes renumbered so
+// that every class is a contiguous range of rows.
+struct Colouring {
+    bool built = false;
+    int ncolours = 0;
+    int32_t *colour = nullptr;  // by original id
+    int32_t *perm = nullptr;    // new id -> original id
+    int32_t *iperm = nullptr;   // original id -> new id
+    std::vector<int64_t> class_row;  // host: rows of class c are [class_row[c], class_row[c+1])
+    DevCSR pcsr;                     // permuted CSR, blocks never straddle a class
+    std::vector<int64_t> class_blk;  // host: blocks of class c are [class_blk[c], class_blk[c+1])
+};
+
+// Solve scratch, grown on demand and kept by the handle.
+struct Workspace {
+    int64_t cap_n = 0;      // nodes x right-hand sides the buffers hold
+    int cap_graphs = 0;
+    void *r = nullptr;      // residual (FP32 or FP64)
+    void *h = nullptr;      // thresholds eps' s'
+    void *da = nullptr;     // push increments (current)
+    void *db = nullptr;     // push increments (second buffer / tail)
+    double *zhat = nullptr; // estimate of z' (FP64)
+    double *sp = nullptr;   // s' = s + c_eff (FP64)
+    double *sin = nullptr;  // caller's s, z0 or z staged on the device
+    double *zout = nullptr; // unshifted result staged on the device
+    double *gstat = nullptr;  // per graph/RHS: [c_eff, min s, resid_inf, resid_rel, z_inf, violators]
+    Counters *ctr = nullptr;
+    Counters *ctr_host = nullptr;  // pinned mirror
+    double *gstat_host = nullptr;  // pinned mirror
+    unsigned long long *status = nullptr;  // look-back tile status
+    int64_t cap_status = 0;
+    unsigned int *tile_ctr = nullptr;
+    int32_t *list = nullptr;  // frontier list
+    long long *count = nullptr;
+    double *partial = nullptr;  // per-block partial sums (metrics)
+    int64_t cap_partial = 0;
+};
+
+}  // namespace fj
+
+struct fj_graph {
+    int device = 0;
+    int directed = 0;
+    int ngraphs = 1;
+    fj::DevCSR csr;
+    // transposed CSR (directed graphs): row v lists u with a_uv > 0
+    int64_t *tptr = nullptr;
+    int32_t *tcol = nullptr;
+    float *tw = nullptr;
+    std::vector<int64_t> node_off;     // host, ngraphs + 1
+    int64_t *node_off_d = nullptr;
+    fj::Colouring colr;
+    fj::Workspace ws;
+    fj::SortScratch sort;
+    int *err = nullptr;      // device error word
+    int *err_host = nullptr; // pinned mirror
+};
+
+namespace fj {
+
+// fj_graph.cu
+fj_status graph_finish(fj_graph *g, cudaStream_t st);
+fj_status build_blocks(DevCSR &c, const std::vector<int64_t> &seg_rows, Workspace &ws, int *err,
+                       cudaStream_t st);
+fj_status ensure_colouring(fj_graph *g, cudaStream_t st);
+fj_status ws_status(Workspace &ws, int64_t tiles);
+fj_status read_dev_error(fj_graph *g, cudaStream_t st);
+void dev_free(void *p);
+
+}  // namespace fj

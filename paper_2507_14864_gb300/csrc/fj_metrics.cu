@@ -1,0 +1,182 @@
+// The measures of Table 1 (Section 3.4) for opinions s and equilibrium z:
+//   C = sum z_i^2, P = sum (z_i - mean z)^2, I = sum (z_i - s_i)^2,
+//   D = sum over edges a_ij (z_i - z_j)^2 (an undirected edge once).
+// Two passes over the row blocks of the caller-order CSR: the mean first,
+// then C, P, I and the disagreement gathered over the nonzeros.  All sums are
+// FP64 in a fixed order (per-thread strided partials, shuffle trees, warps in
+// order, blocks in order per graph), so the result is bit-reproducible.
+#include <vector>
+
+#include "fj_internal.cuh"
+
+namespace fj {
+
+// Deterministic block sum of NV values (thread 0 ends with the totals).
+template <int NV>
+__device__ __forceinline__ void block_sums(double (&v)[NV], double (*smem)[8])
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) v[j] = warp_sum(v[j]);
+    if (lane == 0)
+#pragma unroll
+        for (int j = 0; j < NV; ++j) smem[j][wid] = v[j];
+    __syncthreads();
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            double t = 0.0;
+            for (int w = 0; w < 8; ++w) t += smem[j][w];
+            v[j] = t;
+        }
+}
+
+__global__ void __launch_bounds__(256)
+k_metric_mean(const int32_t *__restrict__ blk_row, const double *__restrict__ z, double *__restrict__ part)
+{
+    __shared__ double sm[1][8];
+    const int64_t r0 = blk_row[blockIdx.x], r1 = blk_row[blockIdx.x + 1];
+    double v[1] = {0.0};
+    for (int64_t x = r0 + threadIdx.x; x < r1; x += 256) v[0] += z[x];
+    block_sums<1>(v, sm);
+    if (threadIdx.x == 0) part[blockIdx.x] = v[0];
+}
+
+template <bool W>
+__global__ void __launch_bounds__(256)
+k_metric_main(const int64_t *__restrict__ rp, const int32_t *__restrict__ col, const float *__restrict__ w,
+              const int32_t *__restrict__ blk_row, const double *__restrict__ s, const double *__restrict__ z,
+              const int32_t *__restrict__ graph_of, const double *__restrict__ mean, double *__restrict__ part)
+{
+    __shared__ double sm[4][8];
+    __shared__ int64_t srp[kBlockRows + 1];
+    const int64_t r0 = blk_row[blockIdx.x], r1 = blk_row[blockIdx.x + 1];
+    const int64_t k0 = rp[r0], k1 = rp[r1];
+    const int nrows = (int)(r1 - r0);
+    const double mu = mean[graph_of ? graph_of[r0] : 0];
+    double v[4] = {0.0, 0.0, 0.0, 0.0};  // C, P, I, D
+    for (int64_t x = r0 + threadIdx.x; x < r1; x += 256) {
+        double zx = z[x], dz = zx - mu, di = zx - s[x];
+        v[0] += zx * zx;
+        v[1] += dz * dz;
+        v[2] += di * di;
+    }
+    if (nrows == 1) {
+        const double zx = z[r0];
+        for (int64_t k = k0 + threadIdx.x; k < k1; k += 256) {
+            double d = zx - z[col[k]];
+            v[3] += (W ? (double)w[k] : 1.0) * d * d;
+        }
+    } else {
+        for (int i = threadIdx.x; i <= nrows; i += 256) srp[i] = rp[r0 + i];
+        __syncthreads();
+        for (int64_t k = k0 + threadIdx.x; k < k1; k += 256) {
+            int lo = 0, hi = nrows;  // last row with srp[row] <= k
+            while (hi - lo > 1) {
+                int mid = (lo + hi) >> 1;
+                if (srp[mid] <= k) lo = mid; else hi = mid;
+            }
+            double d = z[r0 + lo] - z[col[k]];
+            v[3] += (W ? (double)w[k] : 1.0) * d * d;
+        }
+    }
+    block_sums<4>(v, sm);
+    if (threadIdx.x == 0)
+        for (int j = 0; j < 4; ++j) part[(int64_t)blockIdx.x * 4 + j] = v[j];
+}
+
+// One warp per graph sums its blocks' partials (nf fields each) in a fixed order.
+__global__ void k_metric_reduce(int ng, const int64_t *__restrict__ gblk, const double *__restrict__ part, int nf,
+                                double *__restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    const int gi = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (gi >= ng) return;
+    for (int f = 0; f < nf; ++f) {
+        double acc = 0.0;
+        for (int64_t b = gblk[gi] + lane; b < gblk[gi + 1]; b += 32) acc += part[b * nf + f];
+        acc = warp_sum(acc);
+        if (lane == 0) out[(int64_t)gi * nf + f] = acc;
+    }
+}
+
+__global__ void k_metric_mean_div(int ng, const int64_t *__restrict__ node_off, double *__restrict__ mean)
+{
+    int gi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi < ng) mean[gi] /= (double)(node_off[gi + 1] - node_off[gi]);
+}
+
+}  // namespace fj
+
+using namespace fj;
+
+extern "C" fj_status fj_metrics(fj_graph *g, const double *s, const double *z, fj_metrics_out *out, int mem,
+                                void *stream)
+{
+    FJ_ARG(g != nullptr, "graph is NULL");
+    FJ_ARG(s && z && out, "NULL pointer");
+    FJ_ARG(mem == FJ_MEM_HOST || mem == FJ_MEM_DEVICE, "mem must be FJ_MEM_HOST or FJ_MEM_DEVICE");
+    cudaStream_t st = (cudaStream_t)stream;
+    const DevCSR &c = g->csr;
+    const int64_t n = c.n, nb = c.nblocks;
+    const int ng = g->ngraphs;
+    // scratch: staged s and z, per-block partials, per-graph results and block ranges
+    size_t bytes = sizeof(double) * (size_t)(4 * nb + 8 * ng) + sizeof(int64_t) * (size_t)(2 * ng + 2);
+    if (mem == FJ_MEM_HOST) bytes += sizeof(double) * 2 * (size_t)n;
+    char *buf = nullptr;
+    FJ_CUDA(cudaMallocAsync(&buf, bytes, st));
+    double *part = reinterpret_cast<double *>(buf);
+    double *mean = part + 4 * nb;
+    double *res = mean + ng;
+    int64_t *gblk = reinterpret_cast<int64_t *>(res + 4 * ng + 3 * ng);
+    int64_t *noff = gblk + ng + 1;
+    const double *sd = s, *zd = z;
+    std::vector<int64_t> hg((size_t)ng + 1), hn((size_t)ng + 1);
+    for (int i = 0; i < ng; ++i) {
+        hg[(size_t)i] = ng > 1 ? c.seg_blk[(size_t)i] : 0;
+        hn[(size_t)i] = g->node_off[(size_t)i];
+    }
+    hg[(size_t)ng] = nb;
+    hn[(size_t)ng] = n;
+    FJ_CUDA(cudaMemcpyAsync(gblk, hg.data(), sizeof(int64_t) * (ng + 1), cudaMemcpyHostToDevice, st));
+    FJ_CUDA(cudaMemcpyAsync(noff, hn.data(), sizeof(int64_t) * (ng + 1), cudaMemcpyHostToDevice, st));
+    if (mem == FJ_MEM_HOST) {
+        double *stage = reinterpret_cast<double *>(noff + ng + 1);
+        FJ_CUDA(cudaMemcpyAsync(stage, s, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+        FJ_CUDA(cudaMemcpyAsync(stage + n, z, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+        sd = stage;
+        zd = stage + n;
+    }
+    k_metric_mean<<<(unsigned)nb, 256, 0, st>>>(c.blk_row, zd, part);
+    k_metric_reduce<<<(unsigned)ceil_div(ng * 32, 256), 256, 0, st>>>(ng, gblk, part, 1, mean);
+    k_metric_mean_div<<<(unsigned)ceil_div(ng, 256), 256, 0, st>>>(ng, noff, mean);
+    if (c.w)
+        k_metric_main<true><<<(unsigned)nb, 256, 0, st>>>(c.row_ptr, c.col, c.w, c.blk_row, sd, zd, c.graph_of, mean,
+                                                          part);
+    else
+        k_metric_main<false><<<(unsigned)nb, 256, 0, st>>>(c.row_ptr, c.col, c.w, c.blk_row, sd, zd, c.graph_of, mean,
+                                                           part);
+    k_metric_reduce<<<(unsigned)ceil_div(ng * 32, 256), 256, 0, st>>>(ng, gblk, part, 4, res);
+    FJ_CUDA(cudaGetLastError());
+    std::vector<double> hres((size_t)4 * ng), hmean((size_t)ng);
+    FJ_CUDA(cudaMemcpyAsync(hres.data(), res, sizeof(double) * 4 * ng, cudaMemcpyDeviceToHost, st));
+    FJ_CUDA(cudaMemcpyAsync(hmean.data(), mean, sizeof(double) * ng, cudaMemcpyDeviceToHost, st));
+    FJ_CUDA(cudaFreeAsync(buf, st));
+    FJ_CUDA(cudaStreamSynchronize(st));
+    for (int i = 0; i < ng; ++i) {
+        out[i].C = hres[(size_t)4 * i + 0];
+        out[i].P = hres[(size_t)4 * i + 1];
+        out[i].I = hres[(size_t)4 * i + 2];
+        out[i].D = g->directed ? hres[(size_t)4 * i + 3] : 0.5 * hres[(size_t)4 * i + 3];
+        out[i].mean_z = hmean[(size_t)i];
+    }
+    return FJ_OK;
+}
+
+extern "C" fj_status fj_solve_batch(fj_graph *g, const double *S, int k, const fj_solve_opts *opts, double *Z_out,
+                                    fj_solve_info *info, int mem)
+{
+    (void)g; (void)S; (void)k; (void)opts; (void)Z_out; (void)info; (void)mem;
+    set_error("fj_solve_batch is not built yet");
+    return FJ_ERR_UNSUPPORTED;
+}
