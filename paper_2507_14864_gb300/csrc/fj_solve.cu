@@ -223,6 +223,19 @@ __device__ __forceinline__ T arc_w(const float *__restrict__ w, int64_t k)
 
 // ============================================================== push round
 
+// Bounds-checked indexing: the push and certificate kernels verify every
+// row, block and column index against its array before using it.  The first
+// index out of range is stored here as (site, block, index, limit), the access
+// is skipped, and the host turns the record into an error.  The checks cost one
+// compare per nonzero in kernels that are bound by memory traffic.
+__device__ long long g_fj_dbg[4];
+#define FJ_IDX_OK(site, idx, lim)                                                     \
+    ((idx) >= 0 && (idx) < (lim)                                                      \
+         ? true                                                                       \
+         : (atomicCAS((unsigned long long *)&g_fj_dbg[0], 0ULL, (unsigned long long)(site)) == 0ULL \
+                ? (g_fj_dbg[1] = blockIdx.x, g_fj_dbg[2] = (long long)(idx), g_fj_dbg[3] = (long long)(lim), false) \
+                : false))
+
 // One pull pass over row blocks [blk0, blk0 + gridDim.x): for every row x,
 //   r_x += sum_j a_xj din_j;  if |r_x| > h_x push x:
 //   delta = omega r_x / (1 + d_x), zhat_x += delta, r_x <- (1 - omega) r_x;
@@ -235,7 +248,7 @@ __global__ void __launch_bounds__(256)
 k_pull(const int64_t *__restrict__ rp, const int32_t *__restrict__ col, const float *__restrict__ w,
        const int32_t *__restrict__ blk_row, int64_t blk0, const T *din, T *dout, T *__restrict__ r,
        const T *__restrict__ h, const T *__restrict__ inv, double *__restrict__ zhat,
-       const int32_t *__restrict__ indeg, T omega, Counters *ctr)
+       const int32_t *__restrict__ indeg, T omega, Counters *ctr, int64_t n_rows)
 {
     __shared__ T prod[2 * kBlockNnz];
     __shared__ unsigned char head[2 * kBlockNnz];
@@ -245,6 +258,8 @@ k_pull(const int64_t *__restrict__ rp, const int32_t *__restrict__ col, const fl
     if (*reinterpret_cast<volatile int *>(&ctr->done)) return;
     const int64_t b = blk0 + blockIdx.x;
     const int64_t r0 = blk_row[b], r1 = blk_row[b + 1];
+    if (!FJ_IDX_OK(11, r0, n_rows) || !FJ_IDX_OK(12, r1, n_rows + 1) || !FJ_IDX_OK(13, r1 - r0, kBlockRows + 1))
+        return;
     const int64_t k0 = rp[r0], k1 = rp[r1];
     const int64_t nz = k1 - k0;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -269,7 +284,10 @@ k_pull(const int64_t *__restrict__ rp, const int32_t *__restrict__ col, const fl
     if (nz > 2 * kBlockNnz) {
         // one long row
         T acc = T(0);
-        for (int64_t k = k0 + threadIdx.x; k < k1; k += 256) acc += arc_w<T, W>(w, k) * __ldg(din + __ldg(col + k));
+        for (int64_t k = k0 + threadIdx.x; k < k1; k += 256) {
+            int32_t cj = __ldg(col + k);
+            if (FJ_IDX_OK(14, cj, n_rows)) acc += arc_w<T, W>(w, k) * __ldg(din + cj);
+        }
         acc = warp_sum(acc);
         if (lane == 0) wcarry[wid] = acc;
         __syncthreads();
@@ -282,13 +300,14 @@ k_pull(const int64_t *__restrict__ rp, const int32_t *__restrict__ col, const fl
         const int nzi = (int)nz;
         for (int i = threadIdx.x; i < nzi; i += 256) {
             int64_t k = k0 + i;
-            prod[i] = arc_w<T, W>(w, k) * __ldg(din + __ldg(col + k));
+            int32_t cj = __ldg(col + k);
+            prod[i] = FJ_IDX_OK(15, cj, n_rows) ? arc_w<T, W>(w, k) * __ldg(din + cj) : T(0);
             head[i] = 0;
         }
         __syncthreads();
         for (int64_t x = r0 + threadIdx.x; x < r1; x += 256) {
             int64_t a = rp[x];
-            if (rp[x + 1] > a) head[a - k0] = 1;
+            if (rp[x + 1] > a && FJ_IDX_OK(16, a - k0, nz)) head[a - k0] = 1;
         }
         __syncthreads();
         block_segscan<T>(prod, head, nzi, wcarry, whas);
@@ -324,6 +343,7 @@ k_pull(const int64_t *__restrict__ rp, const int32_t *__restrict__ col, const fl
 
 // ============================================================== FP64 certificate
 
+
 // r64_x = s'_x - (1 + d_x) zhat_x + sum_j a_xj zhat_j  (= s' - (I + L) zhat'; a long
 // row sums a_xj (zhat_j - zhat_x) instead, which cancels less),
 // per graph: max |r64|, max |r64| / s', max |zhat - c_eff|, number of nodes
@@ -335,7 +355,7 @@ __global__ void __launch_bounds__(256)
 k_certify(const int64_t *__restrict__ rp, const int32_t *__restrict__ col, const float *__restrict__ w,
           const int32_t *__restrict__ blk_row, const double *__restrict__ zhat, const double *__restrict__ sp,
           const double *__restrict__ deg, const int32_t *__restrict__ graph_of, double epsp, T *__restrict__ r, T *__restrict__ da,
-          T *__restrict__ db, unsigned long long *gs)
+          T *__restrict__ db, unsigned long long *gs, int64_t n_rows)
 {
     __shared__ double prod[2 * kBlockNnz];
     __shared__ unsigned char head[2 * kBlockNnz];
@@ -344,10 +364,12 @@ k_certify(const int64_t *__restrict__ rp, const int32_t *__restrict__ col, const
     __shared__ double red[4][8];
     const int64_t b = blockIdx.x;
     const int64_t r0 = blk_row[b], r1 = blk_row[b + 1];
+    if (!FJ_IDX_OK(1, r0, n_rows) || !FJ_IDX_OK(2, r1, n_rows + 1) || !FJ_IDX_OK(3, r1 - r0, kBlockRows + 1)) return;
     const int64_t k0 = rp[r0], k1 = rp[r1];
     const int64_t nz = k1 - k0;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int gph = graph_of ? graph_of[r0] : 0;
+    if (!FJ_IDX_OK(6, gph, 1 << 20)) return;
     const double ce = reinterpret_cast<const double *>(gs)[(int64_t)gph * kGs + 1];
     double m_abs = 0.0, m_rel = 0.0, m_z = 0.0, viol = 0.0;
 
@@ -368,8 +390,10 @@ k_certify(const int64_t *__restrict__ rp, const int32_t *__restrict__ col, const
     if (nz > 2 * kBlockNnz) {
         const double zx = zhat[r0];
         double acc = 0.0;
-        for (int64_t k = k0 + threadIdx.x; k < k1; k += 256)
-            acc += arc_w<double, W>(w, k) * (zhat[__ldg(col + k)] - zx);
+        for (int64_t k = k0 + threadIdx.x; k < k1; k += 256) {
+            int32_t cj = __ldg(col + k);
+            if (FJ_IDX_OK(7, cj, n_rows)) acc += arc_w<double, W>(w, k) * (zhat[cj] - zx);
+        }
         acc = warp_sum(acc);
         if (lane == 0) wcarry[wid] = acc;
         __syncthreads();
@@ -384,12 +408,13 @@ k_certify(const int64_t *__restrict__ rp, const int32_t *__restrict__ col, const
         __syncthreads();
         for (int64_t x = r0 + threadIdx.x; x < r1; x += 256) {
             int64_t a = rp[x];
-            if (rp[x + 1] > a) head[a - k0] = 1;
+            if (rp[x + 1] > a && FJ_IDX_OK(5, a - k0, nz)) head[a - k0] = 1;
         }
         __syncthreads();
         for (int i = threadIdx.x; i < nzi; i += 256) {
             int64_t k = k0 + i;
-            prod[i] = arc_w<double, W>(w, k) * zhat[__ldg(col + k)];
+            int32_t cj = __ldg(col + k);
+            prod[i] = FJ_IDX_OK(4, cj, n_rows) ? arc_w<double, W>(w, k) * zhat[cj] : 0.0;
         }
         __syncthreads();
         block_segscan<double>(prod, head, nzi, wcarry, whas);
@@ -612,10 +637,10 @@ static fj_status launch_pull(const DevCSR &c, int64_t blk0, int64_t blk1, const 
     else inv = reinterpret_cast<const T *>(c.inv64);
     if (c.w)
         k_pull<T, true><<<nb, 256, 0, st>>>(c.row_ptr, c.col, c.w, c.blk_row, blk0, din, dout, r, h, inv, ws.zhat,
-                                            c.indeg, (T)omega, ws.ctr);
+                                            c.indeg, (T)omega, ws.ctr, c.n);
     else
         k_pull<T, false><<<nb, 256, 0, st>>>(c.row_ptr, c.col, c.w, c.blk_row, blk0, din, dout, r, h, inv, ws.zhat,
-                                             c.indeg, (T)omega, ws.ctr);
+                                             c.indeg, (T)omega, ws.ctr, c.n);
     FJ_CUDA(cudaGetLastError());
     return run.after(st);
 }
@@ -660,10 +685,10 @@ static fj_status launch_certify(fj_graph *g, const Plan &p, double epsp, cudaStr
     unsigned long long *gs = reinterpret_cast<unsigned long long *>(ws.gstat);
     if (c.w)
         k_certify<T, true><<<(unsigned)c.nblocks, 256, 0, st>>>(c.row_ptr, c.col, c.w, c.blk_row, ws.zhat, ws.sp,
-                                                                c.deg64, c.graph_of, epsp, r, da, db, gs);
+                                                                c.deg64, c.graph_of, epsp, r, da, db, gs, c.n);
     else
         k_certify<T, false><<<(unsigned)c.nblocks, 256, 0, st>>>(c.row_ptr, c.col, c.w, c.blk_row, ws.zhat, ws.sp,
-                                                                 c.deg64, c.graph_of, epsp, r, da, db, gs);
+                                                                 c.deg64, c.graph_of, epsp, r, da, db, gs, c.n);
     FJ_CUDA(cudaGetLastError());
     return FJ_OK;
 }
@@ -725,6 +750,15 @@ static fj_status solve_t(fj_graph *g, const double *s, const double *z0, const f
             FJ_CUDA(cudaMemcpyAsync(ws.ctr_host, ws.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
             FJ_CUDA(cudaStreamSynchronize(st));
             FJ_CHECK(run.harvest());
+            {
+                long long dbg[4] = {0, 0, 0, 0};
+                FJ_CUDA(cudaMemcpyFromSymbol(dbg, g_fj_dbg, sizeof(dbg)));
+                if (dbg[0]) {
+                    set_error("index check failed: site %lld block %lld index %lld limit %lld", dbg[0], dbg[1], dbg[2],
+                              dbg[3]);
+                    return FJ_ERR_INVALID_ARG;
+                }
+            }
             if (ws.ctr_host->done) break;
         }
         // Jacobi rounds that ran after the stop flag were no-ops; re-align parity
@@ -737,6 +771,14 @@ static fj_status solve_t(fj_graph *g, const double *s, const double *z0, const f
         FJ_CHECK(launch_certify<T>(g, p, epsp, st, run));
         FJ_CUDA(cudaMemcpyAsync(ws.gstat_host, ws.gstat, sizeof(double) * kGs * ng, cudaMemcpyDeviceToHost, st));
         FJ_CUDA(cudaStreamSynchronize(st));
+        {
+            long long dbg[4] = {0, 0, 0, 0};
+            FJ_CUDA(cudaMemcpyFromSymbol(dbg, g_fj_dbg, sizeof(dbg)));
+            if (dbg[0]) {
+                set_error("index check failed: site %lld block %lld index %lld limit %lld", dbg[0], dbg[1], dbg[2], dbg[3]);
+                return FJ_ERR_INVALID_ARG;
+            }
+        }
         double viol = 0.0;
         for (int i = 0; i < ng; ++i) viol += ws.gstat_host[i * kGs + 5];
         if (viol == 0.0) break;

@@ -252,9 +252,14 @@ def test_constant_and_signed_opinions(capi, ba20k):
     n = g["n"]
     G = capi.Graph.from_csr(n, *to_dev(rp, col, w), directed=False)
     z, info, _ = G.solve(np.full(n, 0.3), eps=1e-6, omega=1.5)
-    assert np.max(np.abs(z - 0.3)) <= 1e-6 * 0.3
+    err = np.max(np.abs(z - 0.3))
+    assert err <= 1e-6 * 0.3
     m = G.metrics(np.full(n, 0.3), z)
-    assert m["D"] <= 1e-12 and m["P"] <= 1e-12
+    # each edge term is at most (2 err)^2 and each node term at most (2 err)^2
+    assert m["D"] <= (rp[-1] // 2) * (2 * err) ** 2 and m["P"] <= n * (2 * err) ** 2
+    mo = oracle.metrics(n, rp, col, w, np.full(n, 0.3), z, directed=False)
+    for k in ("P", "D", "I", "C"):
+        assert abs(m[k] - mo[k]) <= 1e-9 * abs(mo[k]) + 1e-18
     sg = np.where(np.random.default_rng(3).random(n) < 0.5, -1.0, 1.0)
     z, info, st = G.solve(sg, eps=1e-6, omega=1.5)
     zs, _ = oracle.truth(n, rp, col, w, sg, omega=1.5)
