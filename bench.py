@@ -34,6 +34,7 @@ WORKLOADS = {
     "ba20k": dict(gen="ba", n=20000, precision="fp64", omega=1.5),
     "rmat24_und": dict(gen="rmat_und", scale=24, precision="fp32", omega=1.8),
     "rmat16_dir": dict(gen="rmat_dir", scale=16, precision="fp32", omega=1.5),
+    "rmat20_dir": dict(gen="rmat_dir", scale=20, precision="fp32", omega=1.5),
 }
 EPS = 1e-6
 METRIC = "FJ solves/s to 1e-6 rel. err (GTEPS, % HBM roofline): plain vs batched/warm-start"
@@ -194,8 +195,8 @@ def run_gpu(args):
     s_d = torch.from_numpy(s_host).to(dev)
     z_d = torch.empty_like(s_d)
     opts = dict(eps=EPS, omega=omega, precision=prec, schedule=args.schedule)
-    if args.tail_rows:
-        opts["tail_rows"] = args.tail_rows
+    if args.palette is not None:
+        opts["palette"] = args.palette
     if args.check_every:
         opts["check_every"] = args.check_every
 
@@ -303,11 +304,11 @@ def main():
     ap.add_argument("--workload", default="rmat22_dir", choices=sorted(WORKLOADS))
     ap.add_argument("--omega", type=float, default=None)
     ap.add_argument("--schedule", type=int, default=2, help="1 Jacobi rounds, 2 multicolour")
-    ap.add_argument("--tail-rows", type=int, default=0)
     ap.add_argument("--check-every", type=int, default=0)
     ap.add_argument("--cpu-scale", type=int, default=None,
                     help="R-MAT scale of the CPU-baseline sample (default: the full workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--palette", type=int, default=None)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

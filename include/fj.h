@@ -67,10 +67,13 @@ enum { FJ_PREC_FP64 = 0, FJ_PREC_FP32 = 1 };
  *                once from the round-start residuals (the round view of the
  *                proof of Theorem 1).  Requires omega <= 1.
  *  MULTICOLOUR : Gauss-Seidel/SOR order (Theorem 2, Eqs. sor1-sor3) realised
- *                as colour classes of the symmetrised graph; each class is an
- *                independent set, so its nodes push concurrently.  The
- *                smallest classes are merged into one final block that takes
- *                an unrelaxed (omega <= 1) Jacobi step.  Any omega in (0, 2).
+ *                as colour classes of the symmetrised graph taken in turn;
+ *                each class is an independent set, so its nodes push
+ *                concurrently.  One launch per sweep: a node waits only for
+ *                its own neighbours in earlier classes.  Any omega in (0, 2)
+ *                (convergence for omega > 1 is guaranteed on undirected
+ *                graphs only; directed graphs report FJ_ERR_DIVERGED if the
+ *                residual blows up).
  *  AUTO        : MULTICOLOUR. */
 enum { FJ_SCHED_AUTO = 0, FJ_SCHED_JACOBI = 1, FJ_SCHED_MULTICOLOUR = 2 };
 
@@ -83,8 +86,13 @@ typedef struct {
     int schedule;        /* FJ_SCHED_* */
     int64_t max_sweeps;  /* cap on rounds/sweeps per refinement pass (default 100000) */
     int max_refine;      /* cap on FP64 certify-and-restart passes (default 8) */
-    int tail_rows;       /* MULTICOLOUR: classes with fewer rows than this join the tail block
-                            (0 = library default) */
+    int palette;         /* MULTICOLOUR: colours allowed (default 16; 0 = as many as greedy
+                            colouring needs).  When the palette runs out a node joins the
+                            class where its neighbours' weight is least; those same-class
+                            neighbours are coupled as in a synchronous round, and the node's
+                            relaxation is lowered to omega_v <= 0.98 * 2(1+d_v)/(1+d_v+w_v)
+                            (w_v: its weight to same-class neighbours), which keeps the
+                            sweep convergent on undirected graphs (Gershgorin on M+M^T-A) */
     int check_every;     /* sweeps between host checks of the stop flag (0 = default 8) */
     int profile;         /* 1: time every launch of the push kernel with CUDA events on `stream`
                             and report it in fj_solve_info (adds event overhead; off by default) */
@@ -185,11 +193,15 @@ fj_status fj_graph_export(const fj_graph *g, int transposed, int64_t *row_ptr, i
  * fj_graph_colour - greedy colouring of the symmetrised graph (u ~ v when
  * a_uv > 0 or a_vu > 0) in largest-degree-first order (ties: higher 32 bits of
  * SplitMix64(v) first, then lower v), computed by a Jones-Plassmann kernel;
- * the result equals the sequential greedy colouring in that order.  Colour
- * classes are independent sets, so sweeping them in turn is a Gauss-Seidel
- * order (Theorem 2).  colour[n] (int32) may be NULL; *ncolours may be NULL.
+ * the result equals the sequential greedy colouring in that order.  palette
+ * = 0 allows any number of colours, so classes are independent sets and
+ * sweeping them in turn is a Gauss-Seidel order (Theorem 2).  palette = K > 0
+ * allows K colours: a node whose palette is exhausted takes the colour of
+ * least conflict weight, the sum over coloured neighbours of round(a * 2^32)
+ * for each arc between them (smallest colour on ties).  colour[n] (int32) may
+ * be NULL; *ncolours may be NULL.
  */
-fj_status fj_graph_colour(fj_graph *g, int32_t *colour, int *ncolours, int mem, void *stream);
+fj_status fj_graph_colour(fj_graph *g, int palette, int32_t *colour, int *ncolours, int mem, void *stream);
 
 /*
  * fj_solve - ImprovedBLISOR (Alg. 3 with the shift of Alg. 2) on the GPU.

@@ -69,6 +69,8 @@ def _lib():
     lib.oracle_metrics.restype = None
     lib.oracle_greedy_colour.argtypes = [I64, VP, VP, VP, VP]
     lib.oracle_greedy_colour.restype = I64
+    lib.oracle_palette_colour.argtypes = [I64, VP, VP, VP, VP, ctypes.c_int, VP]
+    lib.oracle_palette_colour.restype = I64
     _lib_handle = lib
     return lib
 
@@ -351,3 +353,64 @@ def greedy_colour(n, row_ptr, col):
     if k < 0:
         raise MemoryError("oracle allocation failed")
     return colour, int(k)
+
+
+def fixed_point_weight(w):
+    """Arc weight in 32.32 fixed point (round to nearest), the unit in which
+    colouring conflicts are summed."""
+    return np.rint(np.asarray(w, np.float64) * 4294967296.0).astype(np.int64)
+
+
+def symmetric_weights(n, row_ptr, col, w, directed: bool):
+    """Symmetric adjacency for the colouring conflicts, with per-pair weights
+    as (float a_uv + a_vu, fixed-point q(a_uv) + q(a_vu)) for a directed graph
+    and (a_uv, q(a_uv)) for an undirected one.  Sorted rows, unique columns."""
+    rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(row_ptr))
+    c = np.asarray(col, np.int64)
+    wv = np.ones(len(c)) if w is None else np.asarray(w, np.float64)
+    qv = fixed_point_weight(wv)
+    if directed:
+        a = np.concatenate([rows, c])
+        b = np.concatenate([c, rows])
+        ww = np.concatenate([wv, wv])
+        qq = np.concatenate([qv, qv])
+    else:
+        a, b, ww, qq = rows, c, wv, qv
+    key = a * n + b
+    order = np.argsort(key, kind="stable")
+    key, ww, qq = key[order], ww[order], qq[order]
+    first = np.ones(len(key), bool)
+    first[1:] = key[1:] != key[:-1]
+    starts = np.flatnonzero(first)
+    uk = key[starts]
+    sw = np.add.reduceat(ww, starts) if len(ww) else ww
+    sq = np.add.reduceat(qq, starts) if len(qq) else qq
+    sa = uk // n
+    ptr = np.zeros(n + 1, np.int64)
+    np.cumsum(np.bincount(sa, minlength=n), out=ptr[1:])
+    return ptr, (uk % n).astype(np.int32), sw, sq
+
+
+def palette_colour(n, row_ptr, col, w, directed: bool, K: int):
+    """Greedy colouring with a palette of K colours in largest-degree-first order
+    (least-conflict colour when the palette is exhausted).  Returns
+    (colour int32[n], colours used, in-class weight per node float64[n])."""
+    sp_, sc_, sw_, sq_ = symmetric_weights(n, row_ptr, col, w, directed)
+    order = colour_priority_order(n, sp_)
+    colour = np.empty(n, np.int32)
+    k = _lib().oracle_palette_colour(n, _p(np.ascontiguousarray(sp_)), _p(np.ascontiguousarray(sc_)),
+                                     _p(np.ascontiguousarray(sq_)), _p(order), int(K), _p(colour))
+    if k < 0:
+        raise MemoryError("oracle allocation failed")
+    rows = np.repeat(np.arange(n), np.diff(sp_))
+    same = colour[rows] == colour[sc_]
+    din = np.bincount(rows[same], weights=sw_[same], minlength=n)
+    return colour, int(k), din
+
+
+def safe_omega(omega, d64, din):
+    """Per-node relaxation for a colouring with in-class conflicts: the largest
+    omega_v <= omega with (2 / omega_v - 1)(1 + d_v) >= din_v / 0.98, which keeps
+    M + M^T - (I + L) diagonally dominant (Gershgorin) on undirected graphs."""
+    bound = 0.98 * 2.0 * (1.0 + d64) / (1.0 + d64 + din)
+    return np.where(din > 0, np.minimum(omega, bound), omega)

@@ -445,3 +445,42 @@ int64_t oracle_greedy_colour(int64_t n, const int64_t *sym_ptr, const int32_t *s
     free(seen);
     return ncol;
 }
+
+/*
+ * Greedy colouring with a palette of K colours, in a given priority order,
+ * on a symmetric adjacency (sym_ptr, sym_col) whose pair weights sym_q are
+ * integers (the arc weights in 32.32 fixed point, summed over both arcs of a
+ * pair).  Each node, in `order`, sums the weights of its already coloured
+ * neighbours per colour and takes the smallest colour whose sum is zero, or,
+ * when every colour of the palette is taken, the colour of least weight
+ * (smallest index on ties).  With K at least the greedy colour count this is
+ * the plain greedy colouring.  Returns the number of colours used.
+ */
+int64_t oracle_palette_colour(int64_t n, const int64_t *sym_ptr, const int32_t *sym_col, const int64_t *sym_q,
+                              const int32_t *order, int K, int32_t *colour)
+{
+    int64_t *conf = (int64_t *)malloc(sizeof(int64_t) * (size_t)(K > 0 ? K : 1));
+    if (!conf) return -1;
+    for (int64_t v = 0; v < n; ++v) colour[v] = -1;
+    int64_t used = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t v = order[i];
+        for (int c = 0; c < K; ++c) conf[c] = 0;
+        for (int64_t k = sym_ptr[v]; k < sym_ptr[v + 1]; ++k) {
+            int32_t cu = colour[sym_col[k]];
+            if (cu >= 0) conf[cu] += sym_q[k];
+        }
+        int best = -1;
+        for (int c = 0; c < K && best < 0; ++c)
+            if (conf[c] == 0) best = c;
+        if (best < 0) {
+            best = 0;
+            for (int c = 1; c < K; ++c)
+                if (conf[c] < conf[best]) best = c;
+        }
+        colour[v] = best;
+        if (best + 1 > used) used = best + 1;
+    }
+    free(conf);
+    return used;
+}

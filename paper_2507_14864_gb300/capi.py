@@ -32,8 +32,8 @@ EXPORTED = [
 class fj_solve_opts(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("omega", ctypes.c_double), ("c", ctypes.c_double),
                 ("sigma", ctypes.c_double), ("precision", ctypes.c_int), ("schedule", ctypes.c_int),
-                ("max_sweeps", ctypes.c_int64), ("max_refine", ctypes.c_int), ("tail_rows", ctypes.c_int),
-                ("check_every", ctypes.c_int), ("profile", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("max_sweeps", ctypes.c_int64), ("max_refine", ctypes.c_int),
+                ("palette", ctypes.c_int), ("check_every", ctypes.c_int), ("profile", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 class fj_solve_info(ctypes.Structure):
@@ -84,7 +84,7 @@ def lib():
     L.fj_graph_info.argtypes = [VP, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I32),
                                 ctypes.POINTER(I32)]
     L.fj_graph_export.argtypes = [VP, I32, VP, VP, VP, VP, I32, VP]
-    L.fj_graph_colour.argtypes = [VP, VP, ctypes.POINTER(I32), I32, VP]
+    L.fj_graph_colour.argtypes = [VP, I32, VP, ctypes.POINTER(I32), I32, VP]
     L.fj_solve.argtypes = [VP, VP, ctypes.POINTER(fj_solve_opts), VP, VP, I32]
     L.fj_solve_warm.argtypes = [VP, VP, VP, ctypes.POINTER(fj_solve_opts), VP, VP, I32]
     L.fj_solve_batch.argtypes = [VP, VP, I32, ctypes.POINTER(fj_solve_opts), VP, VP, I32]
@@ -242,12 +242,12 @@ class Graph:
                                      FJ_MEM_HOST, current_stream()), "fj_graph_export")
         return rp, col, w, deg
 
-    def colour(self):
+    def colour(self, palette=0):
         n = self.info()["n"]
         out = np.empty(n, np.int32)
         k = ctypes.c_int()
-        _check(lib().fj_graph_colour(self._h, _ptr(out), ctypes.byref(k), FJ_MEM_HOST, current_stream()),
-               "fj_graph_colour")
+        _check(lib().fj_graph_colour(self._h, int(palette), _ptr(out), ctypes.byref(k), FJ_MEM_HOST,
+                                     current_stream()), "fj_graph_colour")
         return out, k.value
 
     # ------------------------------------------------------------ compute

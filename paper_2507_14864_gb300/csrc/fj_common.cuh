@@ -148,6 +148,8 @@ struct Counters {
     int done;                         // 0 running, 1 converged, 2 sweep cap, 3 diverged
     int err;                          // DevErr
     double nonfinite;                 // set when a residual became NaN/Inf
+    unsigned int ticket;              // next work item of the running sweep
+    unsigned int pad;
 };
 
 // Launch helper: grid size for a grid-stride loop over `work` items.

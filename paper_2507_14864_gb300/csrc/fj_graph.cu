@@ -201,19 +201,22 @@ __global__ void k_finish_ptr_dev(int64_t n, const long long *__restrict__ excl, 
         ptr[i] = i < n ? (int64_t)excl[i] : (int64_t)*total;
 }
 
-// A block starts at row 0, at every forced segment start, every kBlockRows
-// rows, at and after every row longer than kBlockNnz, and where the row's
-// first nonzero enters a new kBlockNnz-sized bucket of the nonzero range.
+// A block starts at row 0, at every forced segment start, every max_rows
+// rows, at and after every row longer than `bucket` nonzeros, and where the
+// row's first nonzero enters a new bucket-sized stretch of the nonzero range;
+// so a block of several rows holds at most 2 * bucket nonzeros.
 struct BlockStartPred {
     const int64_t *rp;
     const int64_t *seg;  // sorted forced starts
     int nseg;
+    int64_t bucket;
+    int64_t max_rows;
     __device__ bool operator()(int64_t u) const
     {
-        if (u == 0 || (u % kBlockRows) == 0) return true;
+        if (u == 0 || (u % max_rows) == 0) return true;
         int64_t a = rp[u], la = rp[u + 1] - a, b = rp[u - 1], lb = a - b;
-        if (la > kBlockNnz || lb > kBlockNnz) return true;
-        if ((a / kBlockNnz) != (b / kBlockNnz)) return true;
+        if (la > bucket || lb > bucket) return true;
+        if ((a / bucket) != (b / bucket)) return true;
         int lo = 0, hi = nseg;
         while (lo < hi) {
             int mid = (lo + hi) >> 1;
@@ -241,12 +244,14 @@ __global__ void k_set_i32(int32_t *p, int32_t v) { *p = v; }
 
 // ============================================================== host pieces
 
-fj_status build_blocks(DevCSR &c, const std::vector<int64_t> &seg_rows, Workspace &ws, int *err, cudaStream_t st)
+fj_status build_blocks(DevCSR &c, const std::vector<int64_t> &seg_rows, Workspace &ws, int *err, cudaStream_t st,
+                       bool warp_tiles)
 {
     const int64_t n = c.n;
-    dev_free(c.blk_row);
-    c.blk_row = nullptr;
-    FJ_CUDA(dalloc(&c.blk_row, n + 2));
+    int32_t *&blk = warp_tiles ? c.wblk_row : c.blk_row;
+    dev_free(blk);
+    blk = nullptr;
+    FJ_CUDA(dalloc(&blk, n + 2));
     int64_t *seg_d = nullptr;
     std::vector<int64_t> seg = seg_rows;
     std::sort(seg.begin(), seg.end());
@@ -254,14 +259,21 @@ fj_status build_blocks(DevCSR &c, const std::vector<int64_t> &seg_rows, Workspac
     if (!seg.empty())
         FJ_CUDA(cudaMemcpyAsync(seg_d, seg.data(), sizeof(int64_t) * seg.size(), cudaMemcpyHostToDevice, st));
     FJ_CHECK(ws_status(ws, scan_tiles(n, 256 * 8)));
-    FJ_CUDA(compact<256, 8>(n, BlockStartPred{c.row_ptr, seg_d, (int)seg.size()}, c.blk_row, ws.count, ws.status,
-                            ws.tile_ctr, err, st));
+    const int64_t bucket = warp_tiles ? kWarpNnz : kBlockNnz;
+    const int64_t max_rows = warp_tiles ? kWarpRows : kBlockRows;
+    FJ_CUDA(compact<256, 8>(n, BlockStartPred{c.row_ptr, seg_d, (int)seg.size(), bucket, max_rows}, blk, ws.count,
+                            ws.status, ws.tile_ctr, err, st));
     long long nb = 0;
     FJ_CUDA(cudaMemcpyAsync(&nb, ws.count, sizeof(long long), cudaMemcpyDeviceToHost, st));
     FJ_CUDA(cudaStreamSynchronize(st));
-    c.nblocks = nb;
-    k_set_i32<<<1, 1, 0, st>>>(c.blk_row + nb, (int32_t)n);
+    k_set_i32<<<1, 1, 0, st>>>(blk + nb, (int32_t)n);
     FJ_CUDA(cudaGetLastError());
+    if (warp_tiles) {
+        c.nwblocks = nb;
+        dev_free(seg_d);
+        return FJ_OK;
+    }
+    c.nblocks = nb;
     c.seg_blk.assign(seg.size() + 1, nb);
     if (!seg.empty()) {
         long long *sb = nullptr;
@@ -290,6 +302,7 @@ static void csr_free(DevCSR &c)
     dev_free(c.indeg);
     dev_free(c.graph_of);
     dev_free(c.blk_row);
+    dev_free(c.wblk_row);
     c = DevCSR();
 }
 
@@ -339,7 +352,8 @@ static fj_status derive_arrays(fj_graph *g, DevCSR &c, bool transpose, const std
             dev_free(k0); dev_free(v0); dev_free(k1); dev_free(v1); dev_free(row_of);
         }
     }
-    FJ_CHECK(build_blocks(c, segs, g->ws, g->err, st));
+    FJ_CHECK(build_blocks(c, segs, g->ws, g->err, st, false));
+    FJ_CHECK(build_blocks(c, segs, g->ws, g->err, st, true));
     return FJ_OK;
 }
 
@@ -397,8 +411,8 @@ static fj_status create_common(int64_t n, const int64_t *row_ptr, const int32_t 
         c.nnz = nnz;
         cudaError_t e;
         if ((e = dalloc(&c.row_ptr, n + 1)) != cudaSuccess) { s = cuda_fail(e, "alloc", __FILE__, __LINE__); break; }
-        if ((e = dalloc(&c.col, nnz)) != cudaSuccess) { s = cuda_fail(e, "alloc", __FILE__, __LINE__); break; }
-        if (w && (e = dalloc(&c.w, nnz)) != cudaSuccess) { s = cuda_fail(e, "alloc", __FILE__, __LINE__); break; }
+        if ((e = dalloc(&c.col, nnz + kNnzPad)) != cudaSuccess) { s = cuda_fail(e, "alloc", __FILE__, __LINE__); break; }
+        if (w && (e = dalloc(&c.w, nnz + kNnzPad)) != cudaSuccess) { s = cuda_fail(e, "alloc", __FILE__, __LINE__); break; }
         e = cudaMemcpyAsync(c.row_ptr, row_ptr, sizeof(int64_t) * (n + 1), kind_in(mem), st);
         if (e == cudaSuccess && nnz) e = cudaMemcpyAsync(c.col, col, sizeof(int32_t) * nnz, kind_in(mem), st);
         if (e == cudaSuccess && w && nnz) e = cudaMemcpyAsync(c.w, w, sizeof(float) * nnz, kind_in(mem), st);
@@ -503,7 +517,7 @@ void fj_solve_opts_default(fj_solve_opts *o)
     o->schedule = FJ_SCHED_AUTO;
     o->max_sweeps = 100000;
     o->max_refine = 8;
-    o->tail_rows = 0;
+    o->palette = 16;
     o->check_every = 0;
     o->stream = nullptr;
 }
@@ -625,7 +639,7 @@ fj_status fj_graph_create_from_arcs(int64_t n, int64_t m, const int32_t *src, co
         c.nnz = nk;
         int32_t *rowcnt = nullptr;
         long long *excl = nullptr;
-        if ((e = dalloc(&c.row_ptr, n + 1)) || (e = dalloc(&c.col, nk)) || (w && (e = dalloc(&c.w, nk))) ||
+        if ((e = dalloc(&c.row_ptr, n + 1)) || (e = dalloc(&c.col, nk + kNnzPad)) || (w && (e = dalloc(&c.w, nk + kNnzPad))) ||
             (e = dalloc(&rowcnt, n)) || (e = dalloc(&excl, n + 1))) { fail(e, "alloc CSR"); break; }
         cudaMemsetAsync(rowcnt, 0, sizeof(int32_t) * n, st);
         if (nk) k_emit_arcs<<<grid_for(nk, 256), 256, 0, st>>>(nk, pos, ids, ds, dd, dw, c.col, c.w, rowcnt);
@@ -663,12 +677,24 @@ void fj_graph_destroy(fj_graph *g)
     dev_free(g->colr.colour);
     dev_free(g->colr.perm);
     dev_free(g->colr.iperm);
+    dev_free(g->colr.din_p);
     csr_free(g->colr.pcsr);
+    for (ItemPlan *ip : {&g->plan_csr, &g->plan_pcsr, &g->wplan_csr, &g->wplan_pcsr}) {
+        dev_free(ip->items);
+        dev_free(ip->slot_first);
+        dev_free(ip->slot_nchunk);
+        dev_free(ip->part);
+        dev_free(ip->cnt);
+    }
     Workspace &ws = g->ws;
-    dev_free(ws.r); dev_free(ws.h); dev_free(ws.da); dev_free(ws.db);
+    dev_free(ws.r); dev_free(ws.h); dev_free(ws.da); dev_free(ws.db); dev_free(ws.om); dev_free(ws.prod);
     dev_free(ws.zhat); dev_free(ws.sp); dev_free(ws.sin); dev_free(ws.zout);
     dev_free(ws.gstat); dev_free(ws.ctr); dev_free(ws.status); dev_free(ws.tile_ctr);
     dev_free(ws.list); dev_free(ws.count); dev_free(ws.partial);
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            if (ws.gexec[a][b]) cudaGraphExecDestroy(ws.gexec[a][b]);
+    if (ws.cap_stream) cudaStreamDestroy(ws.cap_stream);
     if (ws.ctr_host) cudaFreeHost(ws.ctr_host);
     if (ws.gstat_host) cudaFreeHost(ws.gstat_host);
     sort_scratch_free(g->sort);
@@ -825,6 +851,112 @@ __global__ void k_jp_round(int64_t cnt, const int32_t *__restrict__ list, const 
     }
 }
 
+// Arc weight in 32.32 fixed point: conflict sums are integers, so their value
+// does not depend on the order of the additions.
+__device__ __forceinline__ unsigned long long fixed_q(const float *w, int64_t k)
+{
+    return w ? (unsigned long long)llrint((double)w[k] * 4294967296.0) : (1ULL << 32);
+}
+
+// Jones-Plassmann round with a palette of K <= 32 colours.  A ready node sums
+// the fixed-point weights of its coloured neighbours per colour (integer
+// atomics in shared memory) and takes the smallest colour with zero weight,
+// else the colour of least weight (smallest on ties): the same choice as the
+// sequential greedy pass in priority order.
+__global__ void k_jp_palette_round(int64_t cnt, const int32_t *__restrict__ list, const int64_t *__restrict__ rp,
+                                   const int32_t *__restrict__ col, const float *__restrict__ w,
+                                   const int64_t *__restrict__ tp, const int32_t *__restrict__ tc,
+                                   const float *__restrict__ tw, const unsigned long long *__restrict__ key, int K,
+                                   int32_t *colour)
+{
+    __shared__ unsigned long long conf[8][32];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    volatile int32_t *vc = colour;
+    for (int64_t i = warp0; i < cnt; i += nwarps) {
+        const int32_t v = list[i];
+        const unsigned long long kv = key[v];
+        const int64_t a = rp[v], b = rp[v + 1];
+        const int64_t ta = tp ? tp[v] : 0, tb = tp ? tp[v + 1] : 0;
+        bool blocked = false;
+        for (int64_t k = a + lane; k < b && !blocked; k += 32) {
+            int32_t u = col[k];
+            if (higher(key[u], u, kv, v) && vc[u] < 0) blocked = true;
+        }
+        for (int64_t k = ta + lane; k < tb && !blocked; k += 32) {
+            int32_t u = tc[k];
+            if (higher(key[u], u, kv, v) && vc[u] < 0) blocked = true;
+        }
+        if (__any_sync(0xffffffffu, blocked)) continue;
+        conf[wl][lane] = 0ULL;
+        __syncwarp();
+        for (int64_t k = a + lane; k < b; k += 32) {
+            int c = vc[col[k]];
+            if (c >= 0 && c < 32) atomicAdd(&conf[wl][c], fixed_q(w, k));
+        }
+        for (int64_t k = ta + lane; k < tb; k += 32) {
+            int c = vc[tc[k]];
+            if (c >= 0 && c < 32) atomicAdd(&conf[wl][c], fixed_q(tw, k));
+        }
+        __syncwarp();
+        const unsigned long long mine = lane < K ? conf[wl][lane] : ~0ULL;
+        const unsigned zero = __ballot_sync(0xffffffffu, lane < K && mine == 0ULL);
+        int best;
+        if (zero) {
+            best = __ffs(zero) - 1;
+        } else {
+            unsigned long long m = mine;
+            int bl = lane;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                unsigned long long m2 = __shfl_xor_sync(0xffffffffu, m, o);
+                int b2 = __shfl_xor_sync(0xffffffffu, bl, o);
+                if (m2 < m || (m2 == m && b2 < bl)) {
+                    m = m2;
+                    bl = b2;
+                }
+            }
+            best = bl;
+        }
+        if (lane == 0) {
+            colour[v] = best;
+            __threadfence();
+        }
+        __syncwarp();
+    }
+}
+
+// Warp per node: weight to neighbours of the same colour (out-arcs, plus
+// in-arcs for a directed graph), FP64.
+__global__ void k_class_weight(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                               const float *__restrict__ w, const int64_t *__restrict__ tp,
+                               const int32_t *__restrict__ tc, const float *__restrict__ tw,
+                               const int32_t *__restrict__ colour, double *__restrict__ din)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = warp0; v < n; v += nwarps) {
+        const int cv = colour[v];
+        double acc = 0.0;
+        for (int64_t k = rp[v] + lane; k < rp[v + 1]; k += 32)
+            if (colour[col[k]] == cv) acc += w ? (double)w[k] : 1.0;
+        if (tp)
+            for (int64_t k = tp[v] + lane; k < tp[v + 1]; k += 32)
+                if (colour[tc[k]] == cv) acc += tw ? (double)tw[k] : 1.0;
+        acc = warp_sum(acc);
+        if (lane == 0) din[v] = acc;
+    }
+}
+
+__global__ void k_gather_f64(int64_t n, const int32_t *__restrict__ perm, const double *__restrict__ src,
+                             double *__restrict__ dst)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[perm[i]];
+}
+
 __global__ void k_fill_i32(int64_t n, int32_t *p, int32_t v)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = v;
@@ -898,7 +1030,7 @@ __global__ void k_colour_keys(int64_t n, const int32_t *__restrict__ colour, uin
         key[i] = (uint32_t)colour[i];
 }
 
-static fj_status colour_graph(fj_graph *g, cudaStream_t st)
+static fj_status colour_graph(fj_graph *g, int palette, cudaStream_t st)
 {
     DevCSR &c = g->csr;
     const int64_t n = c.n;
@@ -926,8 +1058,12 @@ static fj_status colour_graph(fj_graph *g, cudaStream_t st)
             set_error("colouring did not finish");
             return FJ_ERR_TIMEOUT;
         }
-        k_jp_round<<<grid_for(left * 32, 256, 152 * 64), 256, 0, st>>>(left, list, c.row_ptr, c.col, tp, tc, key,
-                                                                      cl.colour);
+        if (palette > 0)
+            k_jp_palette_round<<<grid_for(left * 32, 256, 152 * 64), 256, 0, st>>>(
+                left, list, c.row_ptr, c.col, c.w, tp, tc, g->directed ? g->tw : nullptr, key, palette, cl.colour);
+        else
+            k_jp_round<<<grid_for(left * 32, 256, 152 * 64), 256, 0, st>>>(left, list, c.row_ptr, c.col, tp, tc,
+                                                                          key, cl.colour);
         FJ_CUDA(cudaGetLastError());
     }
     dev_free(key);
@@ -935,13 +1071,43 @@ static fj_status colour_graph(fj_graph *g, cudaStream_t st)
     return read_dev_error(g, st);
 }
 
-fj_status ensure_colouring(fj_graph *g, cudaStream_t st)
+static void item_plan_free(ItemPlan &ip)
+{
+    dev_free(ip.items);
+    dev_free(ip.slot_first);
+    dev_free(ip.slot_nchunk);
+    dev_free(ip.part);
+    dev_free(ip.cnt);
+    ip = ItemPlan();
+}
+
+static void colouring_free(fj_graph *g)
 {
     Colouring &cl = g->colr;
-    if (cl.built) return FJ_OK;
+    dev_free(cl.colour);
+    dev_free(cl.perm);
+    dev_free(cl.iperm);
+    dev_free(cl.din_p);
+    csr_free(cl.pcsr);
+    cl = Colouring();
+    item_plan_free(g->plan_pcsr);
+    item_plan_free(g->wplan_pcsr);
+    g->ws.gen++;
+}
+
+fj_status ensure_colouring(fj_graph *g, int palette, cudaStream_t st)
+{
+    if (palette < 0 || palette > 32) {
+        set_error("invalid argument: palette must be 0 (unbounded) or 1..32");
+        return FJ_ERR_INVALID_ARG;
+    }
+    Colouring &cl = g->colr;
+    if (cl.built && cl.palette == palette) return FJ_OK;
+    if (cl.built) colouring_free(g);
+    cl.palette = palette;
     DevCSR &c = g->csr;
     const int64_t n = c.n, nnz = c.nnz;
-    FJ_CHECK(colour_graph(g, st));
+    FJ_CHECK(colour_graph(g, palette, st));
     // permutation: stable sort of node ids by colour
     uint32_t *k0, *v0, *k1, *v1;
     FJ_CUDA(dalloc(&k0, n));
@@ -981,8 +1147,8 @@ fj_status ensure_colouring(fj_graph *g, cudaStream_t st)
     FJ_CUDA(scan<256, 8>(n, I32Load{len}, excl, g->ws.count, g->ws.status, g->ws.tile_ctr, g->err, st));
     FJ_CUDA(dalloc(&p.row_ptr, n + 1));
     k_finish_ptr<<<grid_for(n + 1, 256), 256, 0, st>>>(n, excl, nnz, p.row_ptr);
-    FJ_CUDA(dalloc(&p.col, nnz));
-    if (c.w) FJ_CUDA(dalloc(&p.w, nnz));
+    FJ_CUDA(dalloc(&p.col, nnz + kNnzPad));
+    if (c.w) FJ_CUDA(dalloc(&p.w, nnz + kNnzPad));
     k_perm_rows<<<grid_for(n * 32, 256), 256, 0, st>>>(n, cl.perm, cl.iperm, c.row_ptr, c.col, c.w, p.row_ptr, p.col,
                                                        p.w);
     FJ_CUDA(dalloc(&p.deg64, n));
@@ -993,6 +1159,19 @@ fj_status ensure_colouring(fj_graph *g, cudaStream_t st)
     k_perm_node_arrays<<<grid_for(n, 256), 256, 0, st>>>(n, cl.perm, c.deg64, c.inv64, c.inv32, c.indeg, c.graph_of,
                                                          p.deg64, p.inv64, p.inv32, p.indeg, p.graph_of);
     FJ_CUDA(cudaGetLastError());
+    {
+        // weight of each node to neighbours of its own colour (0 for a proper colouring)
+        double *din = nullptr;
+        FJ_CUDA(dalloc(&din, n));
+        FJ_CUDA(dalloc(&cl.din_p, n));
+        k_class_weight<<<grid_for(n * 32, 256), 256, 0, st>>>(n, c.row_ptr, c.col, c.w, g->directed ? g->tptr : nullptr,
+                                                              g->directed ? g->tcol : nullptr,
+                                                              g->directed ? g->tw : nullptr, cl.colour, din);
+        k_gather_f64<<<grid_for(n, 256), 256, 0, st>>>(n, cl.perm, din, cl.din_p);
+        FJ_CUDA(cudaGetLastError());
+        FJ_CUDA(cudaStreamSynchronize(st));
+        dev_free(din);
+    }
     // forced block starts: every class start and, in a ragged batch, every
     // change of graph inside a class, so that each row block lies in one
     // class of one graph
@@ -1007,7 +1186,8 @@ fj_status ensure_colouring(fj_graph *g, cudaStream_t st)
     std::vector<int64_t> segs(hs.begin(), hs.end());
     dev_free(excl);
     dev_free(k0); dev_free(v0); dev_free(k1); dev_free(v1);
-    FJ_CHECK(build_blocks(p, segs, g->ws, g->err, st));
+    FJ_CHECK(build_blocks(p, segs, g->ws, g->err, st, false));
+    FJ_CHECK(build_blocks(p, segs, g->ws, g->err, st, true));
     cl.class_blk.assign((size_t)cl.ncolours + 1, p.nblocks);
     for (int k = 0; k < cl.ncolours; ++k) {
         size_t at = (size_t)(std::lower_bound(segs.begin(), segs.end(), cl.class_row[k]) - segs.begin());
@@ -1019,12 +1199,14 @@ fj_status ensure_colouring(fj_graph *g, cudaStream_t st)
 
 }  // namespace fj
 
-extern "C" fj_status fj_graph_colour(fj_graph *g, int32_t *colour, int *ncolours, int mem, void *stream)
+extern "C" fj_status fj_graph_colour(fj_graph *g, int palette, int32_t *colour, int *ncolours, int mem,
+                                     void *stream)
 {
     FJ_ARG(g != nullptr, "graph is NULL");
     FJ_ARG(mem == FJ_MEM_HOST || mem == FJ_MEM_DEVICE, "mem must be FJ_MEM_HOST or FJ_MEM_DEVICE");
+    FJ_ARG(palette >= 0 && palette <= 32, "palette must be 0 (unbounded) or 1..32");
     cudaStream_t st = (cudaStream_t)stream;
-    FJ_CHECK(fj::ensure_colouring(g, st));
+    FJ_CHECK(fj::ensure_colouring(g, palette, st));
     if (colour)
         FJ_CUDA(cudaMemcpyAsync(colour, g->colr.colour, sizeof(int32_t) * g->csr.n,
                                 mem == FJ_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));

@@ -11,8 +11,18 @@ namespace fj {
 // Row blocks: rows [blk_row[b], blk_row[b+1]) form block b.  A block either
 // holds at most kBlockRows rows whose nonzeros fit in 2*kBlockNnz (staged in
 // shared memory), or is a single long row.
-constexpr int kBlockNnz = 2048;
+constexpr int kBlockNnz = 1024;
 constexpr int kBlockRows = 512;
+// Warp tiles of the sweep: rows whose nonzeros fit in 2 * kWarpNnz (sixteen
+// per lane), at most kWarpRows rows (two per lane); a longer row is cut into
+// chunks of kWarpChunk nonzeros (sixteen per lane: one batch of loads).
+// Column and weight arrays carry kNnzPad spare entries, so that 16-byte
+// asynchronous copies of a tile rounded out to 4-element granules stay inside
+// the allocation.
+constexpr int kNnzPad = 4;
+constexpr int kWarpNnz = 256;
+constexpr int kWarpRows = 64;
+constexpr int kWarpChunk = 512;
 
 // One CSR resident on the device plus the per-row arrays the push needs.
 struct DevCSR {
@@ -25,8 +35,10 @@ struct DevCSR {
     double *inv64 = nullptr;   // 1 / (1 + d_u)
     int32_t *indeg = nullptr;  // number of in-neighbours (residual updates per push)
     int32_t *graph_of = nullptr;  // ragged: graph id of each row (nullptr for one graph)
-    int32_t *blk_row = nullptr;   // nblocks + 1 entries
+    int32_t *blk_row = nullptr;   // nblocks + 1 entries (block tiles)
     int64_t nblocks = 0;
+    int32_t *wblk_row = nullptr;  // nwblocks + 1 entries (warp tiles)
+    int64_t nwblocks = 0;
     std::vector<int64_t> seg_blk;  // host: block ranges of forced segments (classes / graphs)
 };
 
@@ -34,13 +46,42 @@ struct DevCSR {
 // that every class is a contiguous range of rows.
 struct Colouring {
     bool built = false;
+    int palette = -1;           // palette size the colouring was built with (0 = unbounded)
     int ncolours = 0;
+    double *din_p = nullptr;    // permuted order: weight to neighbours of the same colour
     int32_t *colour = nullptr;  // by original id
     int32_t *perm = nullptr;    // new id -> original id
     int32_t *iperm = nullptr;   // original id -> new id
     std::vector<int64_t> class_row;  // host: rows of class c are [class_row[c], class_row[c+1])
     DevCSR pcsr;                     // permuted CSR, blocks never straddle a class
     std::vector<int64_t> class_blk;  // host: blocks of class c are [class_blk[c], class_blk[c+1])
+};
+
+// Work items of a sweep, in the order of the sweep (colour order for the
+// multicolour schedule).  An item is a row block (slot < 0) or one chunk of a
+// long row (slot = the long row's index; its chunks sum into part[] and the
+// last one to finish applies the row's update).  lo is the first row of the
+// item's colour class: a column below lo belongs to an earlier class.
+struct Item {
+    int32_t r0, r1;
+    int32_t lo;
+    int32_t slot;
+    int64_t k0, k1;
+};
+constexpr int kChunkNnz = 2048;
+
+struct ItemPlan {
+    bool built = false;
+    Item *items = nullptr;       // device
+    int64_t nitems = 0;
+    int64_t nslots = 0;          // long rows
+    int32_t *slot_first = nullptr;  // device: first chunk index of each long row into part[]
+    int32_t *slot_nchunk = nullptr; // device
+    double *part = nullptr;         // device: one partial sum per chunk
+    int32_t *cnt = nullptr;         // device: chunks finished per long row
+    int64_t nparts = 0;
+    std::vector<int64_t> class_item;  // host: items of class c are [class_item[c], class_item[c+1])
+    std::vector<int64_t> class_k;     // host: nonzeros of class c are [class_k[c], class_k[c+1])
 };
 
 // Solve scratch, grown on demand and kept by the handle.
@@ -50,7 +91,10 @@ struct Workspace {
     void *r = nullptr;      // residual (FP32 or FP64)
     void *h = nullptr;      // thresholds eps' s'
     void *da = nullptr;     // push increments (current)
-    void *db = nullptr;     // push increments (second buffer / tail)
+    void *db = nullptr;     // push increments (second buffer)
+    void *om = nullptr;     // per-node relaxation factor
+    void *prod = nullptr;   // per-nonzero products a_k delta_col(k) of the running class
+    int64_t cap_prod = 0;
     double *zhat = nullptr; // estimate of z' (FP64)
     double *sp = nullptr;   // s' = s + c_eff (FP64)
     double *sin = nullptr;  // caller's s, z0 or z staged on the device
@@ -66,6 +110,14 @@ struct Workspace {
     long long *count = nullptr;
     double *partial = nullptr;  // per-block partial sums (metrics)
     int64_t cap_partial = 0;
+    int64_t sweep_parity = 0;   // sweeps launched on this handle; selects the increment buffers
+    // captured batches of sweeps, per (precision, schedule); valid while gen == graph_gen
+    cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    int64_t gkey[2][2] = {{-1, -1}, {-1, -1}};
+    int gsweeps[2][2] = {{0, 0}, {0, 0}};
+    int glaunch[2][2] = {{0, 0}, {0, 0}};
+    cudaStream_t cap_stream = nullptr;
+    int64_t gen = 0;            // bumped whenever buffers or work-item plans change
 };
 
 }  // namespace fj
@@ -82,6 +134,8 @@ struct fj_graph {
     std::vector<int64_t> node_off;     // host, ngraphs + 1
     int64_t *node_off_d = nullptr;
     fj::Colouring colr;
+    fj::ItemPlan plan_csr, plan_pcsr;    // block-tile items (certificate)
+    fj::ItemPlan wplan_csr, wplan_pcsr;  // warp-tile items (sweep)
     fj::Workspace ws;
     fj::SortScratch sort;
     int *err = nullptr;      // device error word
@@ -93,8 +147,8 @@ namespace fj {
 // fj_graph.cu
 fj_status graph_finish(fj_graph *g, cudaStream_t st);
 fj_status build_blocks(DevCSR &c, const std::vector<int64_t> &seg_rows, Workspace &ws, int *err,
-                       cudaStream_t st);
-fj_status ensure_colouring(fj_graph *g, cudaStream_t st);
+                       cudaStream_t st, bool warp_tiles);
+fj_status ensure_colouring(fj_graph *g, int palette, cudaStream_t st);
 fj_status ws_status(Workspace &ws, int64_t tiles);
 fj_status read_dev_error(fj_graph *g, cudaStream_t st);
 void dev_free(void *p);

@@ -104,12 +104,17 @@ template <>
 __device__ __forceinline__ double resid_store<double>(double x) { return x; }
 
 // Initial state over new ids i (o = perm[i] the caller's id): s', zhat, r, h.
+// Initial state over new ids i (o = perm[i] the caller's id): s', zhat, r, h,
+// and the relaxation factor of node i: omega, lowered for a node with weight
+// din_i to neighbours of its own colour class so that
+// (2 / omega_i - 1)(1 + d_i) >= din_i / 0.98.
 template <typename T>
 __global__ void k_init(int64_t n, const double *__restrict__ s, const double *__restrict__ z0,
                        const int32_t *__restrict__ perm, const int32_t *__restrict__ graph_of,
-                       const unsigned long long *__restrict__ gs, double epsp, double *__restrict__ sp,
+                       const unsigned long long *__restrict__ gs, double epsp, double omega,
+                       const double *__restrict__ deg, const double *__restrict__ din, double *__restrict__ sp,
                        double *__restrict__ zhat, T *__restrict__ r, T *__restrict__ h, T *__restrict__ da,
-                       T *__restrict__ db)
+                       T *__restrict__ db, T *__restrict__ om)
 {
     const double *gsd = reinterpret_cast<const double *>(gs);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -123,6 +128,12 @@ __global__ void k_init(int64_t n, const double *__restrict__ s, const double *__
         h[i] = threshold_of<T>(epsp * spv);
         da[i] = T(0);
         db[i] = T(0);
+        double oi = omega;
+        if (din && din[i] > 0.0) {
+            double bound = 0.98 * 2.0 * (1.0 + deg[i]) / (1.0 + deg[i] + din[i]);
+            oi = fmin(omega, bound);
+        }
+        om[i] = (T)oi;
     }
 }
 
@@ -145,12 +156,14 @@ __global__ void k_pass_reset(Counters *c, long long max_sweeps)
     c->pass_sweeps = 0;
     c->sweep_pushes = 0;
     c->max_sweeps = max_sweeps;
+    c->ticket = 0;
 }
 
 // End of a sweep (or round): stop when nothing was pushed, at the cap, or on
 // a non-finite residual.
 __global__ void k_end_sweep(Counters *c)
 {
+    c->ticket = 0;
     if (c->done) return;
     c->sweeps += 1;
     c->pass_sweeps += 1;
@@ -158,6 +171,7 @@ __global__ void k_end_sweep(Counters *c)
     else if (c->sweep_pushes == 0) c->done = 1;
     else if (c->pass_sweeps >= c->max_sweeps) c->done = 2;
     c->sweep_pushes = 0;
+    c->ticket = 0;
 }
 
 // ============================================================== row-block machinery
@@ -223,7 +237,7 @@ __device__ __forceinline__ T arc_w(const float *__restrict__ w, int64_t k)
 
 // ============================================================== push round
 
-// Bounds-checked indexing: the push and certificate kernels verify every
+// Bounds-checked indexing: the sweep and certificate kernels verify every
 // row, block and column index against its array before using it.  The first
 // index out of range is stored here as (site, block, index, limit), the access
 // is skipped, and the host turns the record into an error.  The checks cost one
@@ -236,146 +250,321 @@ __device__ long long g_fj_dbg[4];
                 ? (g_fj_dbg[1] = blockIdx.x, g_fj_dbg[2] = (long long)(idx), g_fj_dbg[3] = (long long)(lim), false) \
                 : false))
 
-// One pull pass over row blocks [blk0, blk0 + gridDim.x): for every row x,
-//   r_x += sum_j a_xj din_j;  if |r_x| > h_x push x:
-//   delta = omega r_x / (1 + d_x), zhat_x += delta, r_x <- (1 - omega) r_x;
-//   dout_x = delta (0 when x did not push).
-// Jacobi rounds pass din != dout (double buffer).  A colour class passes
-// din == dout: no row of an independent set reads a value another row of the
-// same launch writes.
+// Products of a colour class: prod[k] = a_k * delta_{col[k]} for the class's
+// nonzeros [k0, k1), with delta taken from dcur for an earlier class (column
+// below lo) and from dprev otherwise.  An elementwise pass over the class's
+// nonzeros at full occupancy with several gathers in flight per thread: the
+// random 4-byte gathers bound the whole sweep, and this shape keeps the most
+// of them in flight.
 template <typename T, bool W>
 __global__ void __launch_bounds__(256)
-k_pull(const int64_t *__restrict__ rp, const int32_t *__restrict__ col, const float *__restrict__ w,
-       const int32_t *__restrict__ blk_row, int64_t blk0, const T *din, T *dout, T *__restrict__ r,
-       const T *__restrict__ h, const T *__restrict__ inv, double *__restrict__ zhat,
-       const int32_t *__restrict__ indeg, T omega, Counters *ctr, int64_t n_rows)
+k_products(int64_t k0, int64_t k1, const int32_t *__restrict__ col, const float *__restrict__ w, int lo,
+           const T *__restrict__ dcur, const T *__restrict__ dprev, T *__restrict__ prod, int64_t n_rows,
+           const Counters *ctr)
 {
-    __shared__ T prod[2 * kBlockNnz];
-    __shared__ unsigned char head[2 * kBlockNnz];
-    __shared__ T wcarry[8];
-    __shared__ int whas[8];
-    __shared__ unsigned long long red[2][8];
+    if (*reinterpret_cast<const volatile int *>(&ctr->done)) return;
+    constexpr int U = 4;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = k0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; base < k1; base += stride * U) {
+        int32_t j[U];
+        T a[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t k = base + u * stride;
+            j[u] = -1;
+            a[u] = T(0);
+            if (k < k1) {
+                j[u] = __ldg(col + k);
+                a[u] = arc_w<T, W>(w, k);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t k = base + u * stride;
+            if (k < k1) {
+                T x = T(0);
+                if (FJ_IDX_OK(15, j[u], n_rows)) x = (j[u] < lo) ? __ldg(dcur + j[u]) : __ldg(dprev + j[u]);
+                prod[k] = a[u] * x;
+            }
+        }
+    }
+}
+
+// One colour class of a sweep (Theorem 2's Gauss-Seidel order realised by
+// colour classes taken in turn; the whole graph as one class is a synchronous
+// round).  For every row x of the class:
+//   r_x += sum_j a_xj delta_j, then if |r_x| > h_x push x (Eqs. sor1-sor3):
+//   delta = omega_x r_x / (1 + d_x), zhat_x += delta, r_x <- (1 - omega_x) r_x.
+// delta_j is node j's latest increment in the sweep order: for j in an
+// earlier class (j < lo; those classes ran in earlier launches of this sweep)
+// the one made in this sweep, in dcur; for j in this or a later class the one
+// made in the previous sweep, in dprev.  Every row writes its own increment
+// (0 when it does not push) into dcur.
+//
+// The grid is persistent (as many blocks as can be resident); warp w of W
+// takes the class's work items w, w + W, ...: a tile of at most 2 * kWarpNnz
+// nonzeros (sixteen per lane) and kWarpRows rows (two per lane), reduced by a
+// warp-synchronous segmented scan, or a kWarpChunk chunk of a long row whose
+// last chunk to finish sums the chunks' partials and applies the update.
+// The products a_xj delta_j come precomputed (k_products); while a warp works
+// on one item, the products of its next item stream into shared memory by
+// asynchronous 16-byte copies (cp.async), so the stream does not pause
+// between items.
+constexpr int kWE = 2 * kWarpNnz / 32;             // nonzeros per lane of a tile
+constexpr int kWR = kWarpRows / 32;                // rows per lane of a tile
+// warps per block: four, three for FP64 (static shared memory stays under 48 KB)
+template <typename T>
+constexpr int sweep_warps() { return sizeof(T) == 8 ? 3 : 4; }
+constexpr int kStage = 2 * kWarpNnz + 8;           // staged elements per item (tile rounded out to granules)
+static_assert(kWarpChunk <= 2 * kWarpNnz, "a chunk is staged like a tile");
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Copy the products of [k0, k1) into a stage in 16-byte granules from k0
+// rounded down to a granule; element k lands at index k - kb.
+template <typename T>
+__device__ __forceinline__ void stage_item(int64_t k0, int64_t k1, const T *__restrict__ prod, T *sp, int lane)
+{
+    constexpr int G = 16 / (int)sizeof(T);  // elements per granule
+    const int64_t kb = k0 & ~int64_t(G - 1);
+    const int ng = (int)((k1 - kb + G - 1) / G);
+    for (int g = lane; g < ng; g += 32) cp_async16(sp + G * g, prod + kb + G * g);
+}
+
+template <typename T, bool W>
+__global__ void __launch_bounds__(32 * sweep_warps<T>())
+k_sweep(const Item *__restrict__ items, int64_t item0, int64_t nitems, const int64_t *__restrict__ rp,
+        const T *__restrict__ prod, T *dcur, T *__restrict__ r, const T *__restrict__ h, const T *__restrict__ inv,
+        double *__restrict__ zhat, const int32_t *__restrict__ indeg, const T *__restrict__ om,
+        const int32_t *__restrict__ slot_first, const int32_t *__restrict__ slot_nchunk, double *part, int32_t *cnt,
+        Counters *ctr, int64_t n_rows)
+{
+    constexpr int kSweepWarps = sweep_warps<T>();
+    constexpr int G = 16 / (int)sizeof(T);
+    __shared__ __align__(16) T sprod[kSweepWarps][2][kStage];
+    __shared__ unsigned long long red[2][kSweepWarps];
+    __shared__ int sbad;
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     if (*reinterpret_cast<volatile int *>(&ctr->done)) return;
-    const int64_t b = blk0 + blockIdx.x;
-    const int64_t r0 = blk_row[b], r1 = blk_row[b + 1];
-    if (!FJ_IDX_OK(11, r0, n_rows) || !FJ_IDX_OK(12, r1, n_rows + 1) || !FJ_IDX_OK(13, r1 - r0, kBlockRows + 1))
-        return;
-    const int64_t k0 = rp[r0], k1 = rp[r1];
-    const int64_t nz = k1 - k0;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     unsigned long long my_push = 0, my_edges = 0;
     bool bad = false;
 
-    auto epilogue = [&](int64_t x, T acc) {
-        T rx = r[x] + acc;
+    auto apply = [&](int64_t x, T rx, T hx, T ix, T ox, double zx, int32_t dgx) {
         T dx = T(0);
-        if (abs_t(rx) > h[x]) {
-            dx = omega * rx * inv[x];
-            zhat[x] += (double)dx;
-            rx = (T(1) - omega) * rx;
+        if (abs_t(rx) > hx) {
+            dx = ox * rx * ix;
+            zhat[x] = zx + (double)dx;
+            rx = (T(1) - ox) * rx;
             my_push += 1;
-            my_edges += (unsigned long long)indeg[x];
+            my_edges += (unsigned long long)dgx;
         }
         if (!isfinite(rx)) bad = true;
         r[x] = rx;
-        dout[x] = dx;
+        dcur[x] = dx;
     };
 
-    if (nz > 2 * kBlockNnz) {
-        // one long row
-        T acc = T(0);
-        for (int64_t k = k0 + threadIdx.x; k < k1; k += 256) {
-            int32_t cj = __ldg(col + k);
-            if (FJ_IDX_OK(14, cj, n_rows)) acc += arc_w<T, W>(w, k) * __ldg(din + cj);
-        }
-        acc = warp_sum(acc);
-        if (lane == 0) wcarry[wid] = acc;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            T t = T(0);
-            for (int i = 0; i < 8; ++i) t += wcarry[i];
-            epilogue(r0, t);
-        }
-    } else {
-        const int nzi = (int)nz;
-        for (int i = threadIdx.x; i < nzi; i += 256) {
-            int64_t k = k0 + i;
-            int32_t cj = __ldg(col + k);
-            prod[i] = FJ_IDX_OK(15, cj, n_rows) ? arc_w<T, W>(w, k) * __ldg(din + cj) : T(0);
-            head[i] = 0;
-        }
-        __syncthreads();
-        for (int64_t x = r0 + threadIdx.x; x < r1; x += 256) {
-            int64_t a = rp[x];
-            if (rp[x + 1] > a && FJ_IDX_OK(16, a - k0, nz)) head[a - k0] = 1;
-        }
-        __syncthreads();
-        block_segscan<T>(prod, head, nzi, wcarry, whas);
-        __syncthreads();
-        for (int64_t x = r0 + threadIdx.x; x < r1; x += 256) {
-            int64_t a = rp[x], e = rp[x + 1];
-            epilogue(x, e > a ? prod[e - 1 - k0] : T(0));
-        }
+    const int64_t nwarps = (int64_t)gridDim.x * kSweepWarps;
+    const int64_t iend = item0 + nitems;
+    int64_t ii = item0 + (int64_t)blockIdx.x * kSweepWarps + wl;
+    int s = 0;
+    Item cur;
+    if (ii < iend) {
+        cur = items[ii];
+        stage_item<T>(cur.k0, cur.k1, prod, sprod[wl][0], lane);
     }
-    // block totals -> three atomics
+    cp_async_commit();
+    for (; ii < iend; ii += nwarps) {
+        // stream the next item in while this one is processed
+        const int64_t in = ii + nwarps;
+        Item nxt = cur;
+        if (in < iend) {
+            nxt = items[in];
+            stage_item<T>(nxt.k0, nxt.k1, prod, sprod[wl][s ^ 1], lane);
+        }
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncwarp();
+        const Item it = cur;
+        const int64_t r0 = it.r0, r1 = it.r1, k0 = it.k0;
+        const int nz = (int)(it.k1 - k0);
+        const int off = (int)(k0 & (G - 1));
+        const bool ok = FJ_IDX_OK(11, r0, n_rows) && FJ_IDX_OK(12, r1, n_rows + 1) &&
+                        FJ_IDX_OK(13, r1 - r0, kWarpRows + 1) && FJ_IDX_OK(17, nz, kStage - 3);
+        if (ok) {
+            const T *sc = sprod[wl][s] + off;
+            if (it.slot < 0) {
+                // ---- tile: a lane owns rows r0 + lane and r0 + lane + 32 and walks
+                // each one through the staged columns; rows longer than 32
+                // nonzeros are reduced by the whole warp
+                const int64_t kb = k0 & ~int64_t(G - 1);
+                const T *spb = sprod[wl][s];
+                int ra[kWR], re[kWR];
+                T rr[kWR], rh[kWR], ri[kWR], ro[kWR], acc[kWR];
+                double rz[kWR];
+                int32_t rd[kWR];
+#pragma unroll
+                for (int q = 0; q < kWR; ++q) {
+                    const int64_t x = r0 + lane + 32 * q;
+                    ra[q] = re[q] = 0;
+                    rr[q] = rh[q] = ri[q] = ro[q] = acc[q] = T(0);
+                    rz[q] = 0.0;
+                    rd[q] = 0;
+                    if (x < r1) {
+                        ra[q] = (int)(rp[x] - kb);
+                        re[q] = (int)(rp[x + 1] - kb);
+                        rr[q] = r[x];
+                        rh[q] = h[x];
+                        ri[q] = inv[x];
+                        ro[q] = om[x];
+                        rz[q] = zhat[x];
+                        rd[q] = indeg[x];
+                    }
+                }
+                auto term = [&](int k) -> T { return spb[k]; };
+                unsigned longrows = 0;  // bit q: this lane's row q is reduced by the warp
+#pragma unroll
+                for (int q = 0; q < kWR; ++q) {
+                    const int len = re[q] - ra[q];
+                    if (len > 32) {
+                        longrows |= 1u << q;
+                    } else if (len > 0 && FJ_IDX_OK(16, re[q], kStage + 1) && FJ_IDX_OK(18, ra[q], kStage)) {
+                        T s0 = T(0), s1 = T(0);
+                        int k = ra[q];
+                        for (; k + 1 < re[q]; k += 2) {
+                            s0 += term(k);
+                            s1 += term(k + 1);
+                        }
+                        if (k < re[q]) s0 += term(k);
+                        acc[q] = s0 + s1;
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < kWR; ++q) {
+                    unsigned m = __ballot_sync(0xffffffffu, (longrows >> q) & 1u);
+                    while (m) {
+                        const int src = __ffs(m) - 1;
+                        m &= m - 1;
+                        const int a = __shfl_sync(0xffffffffu, ra[q], src);
+                        const int e = __shfl_sync(0xffffffffu, re[q], src);
+                        T part_sum = T(0);
+                        if (FJ_IDX_OK(19, e, kStage + 1))
+                            for (int k = a + lane; k < e; k += 32) part_sum += term(k);
+                        part_sum = warp_sum(part_sum);
+                        if (lane == src) acc[q] = part_sum;
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < kWR; ++q) {
+                    const int64_t x = r0 + lane + 32 * q;
+                    if (x < r1) apply(x, rr[q] + acc[q], rh[q], ri[q], ro[q], rz[q], rd[q]);
+                }
+            } else {
+                // ---- chunk of a long row: partial sum; the last chunk applies the update
+                T acc = T(0);
+#pragma unroll
+                for (int e = 0; e < kWE; ++e) {
+                    const int i = lane + 32 * e;
+                    if (i < nz) acc += sc[i];
+                }
+                acc = warp_sum(acc);
+                const int slot = it.slot;
+                const int first = slot_first[slot], nch = slot_nchunk[slot];
+                int last = 0;
+                if (lane == 0) {
+                    const int ci = (int)((k0 - rp[r0]) / kWarpChunk);
+                    part[first + ci] = (double)acc;
+                    __threadfence();
+                    last = atomicAdd(&cnt[slot], 1) == nch - 1;
+                }
+                last = __shfl_sync(0xffffffffu, last, 0);
+                if (last) {
+                    __threadfence();
+                    double sum = 0.0;
+                    for (int c = lane; c < nch; c += 32) sum += __ldcg(part + first + c);
+                    sum = warp_sum(sum);
+                    if (lane == 0) {
+                        cnt[slot] = 0;
+                        apply(r0, r[r0] + (T)sum, h[r0], inv[r0], om[r0], zhat[r0], indeg[r0]);
+                    }
+                }
+            }
+        }
+        __syncwarp();  // the stage of this item is refilled two items from now
+        cur = nxt;
+        s ^= 1;
+    }
+    cp_async_wait<0>();
+    // block totals -> three atomics per block
     my_push = warp_sum(my_push);
     my_edges = warp_sum(my_edges);
-    unsigned anybad = __ballot_sync(0xffffffffu, bad);
+    const unsigned anybad = __ballot_sync(0xffffffffu, bad);
+    if (threadIdx.x == 0) sbad = 0;
+    __syncthreads();
     if (lane == 0) {
-        red[0][wid] = my_push;
-        red[1][wid] = my_edges;
-        if (anybad) ctr->nonfinite = 1.0;
+        red[0][wl] = my_push;
+        red[1][wl] = my_edges;
+        if (anybad) sbad = 1;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        unsigned long long p = 0, e = 0;
-        for (int i = 0; i < 8; ++i) {
-            p += red[0][i];
-            e += red[1][i];
+        unsigned long long pp = 0, ee = 0;
+        for (int i = 0; i < kSweepWarps; ++i) {
+            pp += red[0][i];
+            ee += red[1][i];
         }
-        if (p) {
-            atomicAdd(&ctr->pushes, p);
-            atomicAdd(&ctr->sweep_pushes, p);
-            atomicAdd(&ctr->edges, e);
+        if (sbad) ctr->nonfinite = 1.0;
+        if (pp) {
+            atomicAdd(&ctr->pushes, pp);
+            atomicAdd(&ctr->sweep_pushes, pp);
+            atomicAdd(&ctr->edges, ee);
         }
     }
 }
 
 // ============================================================== FP64 certificate
 
-
-// r64_x = s'_x - (1 + d_x) zhat_x + sum_j a_xj zhat_j  (= s' - (I + L) zhat'; a long
-// row sums a_xj (zhat_j - zhat_x) instead, which cancels less),
-// per graph: max |r64|, max |r64| / s', max |zhat - c_eff|, number of nodes
-// with |r64| > eps' s'.  Stores r64 into the push residual (magnitude rounded
-// up for FP32) and clears both increment buffers: the push restarts from an
-// exact residual (a refinement pass).
+// r64_x = s'_x - (1 + d_x) zhat_x + sum_j a_xj zhat_j  (= s' - (I + L) zhat'; a
+// long row sums a_xj (zhat_j - zhat_x) chunk by chunk instead, which cancels
+// less), per graph: max |r64|, max |r64| / s', max |zhat - c_eff|, number of
+// nodes with |r64| > eps' s'.  Stores r64 into the push residual (magnitude
+// rounded up for FP32) and clears both increment buffers: the push restarts
+// from an exact residual (a refinement pass).
 template <typename T, bool W>
 __global__ void __launch_bounds__(256)
-k_certify(const int64_t *__restrict__ rp, const int32_t *__restrict__ col, const float *__restrict__ w,
-          const int32_t *__restrict__ blk_row, const double *__restrict__ zhat, const double *__restrict__ sp,
-          const double *__restrict__ deg, const int32_t *__restrict__ graph_of, double epsp, T *__restrict__ r, T *__restrict__ da,
-          T *__restrict__ db, unsigned long long *gs, int64_t n_rows)
+k_certify(const Item *__restrict__ items, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+          const float *__restrict__ w, const double *__restrict__ zhat, const double *__restrict__ sp,
+          const double *__restrict__ deg, const int32_t *__restrict__ graph_of, double epsp, T *__restrict__ r,
+          T *__restrict__ da, T *__restrict__ db, unsigned long long *gs, const int32_t *__restrict__ slot_first,
+          const int32_t *__restrict__ slot_nchunk, double *part, int32_t *cnt, int64_t n_rows)
 {
     __shared__ double prod[2 * kBlockNnz];
     __shared__ unsigned char head[2 * kBlockNnz];
     __shared__ double wcarry[8];
     __shared__ int whas[8];
     __shared__ double red[4][8];
-    const int64_t b = blockIdx.x;
-    const int64_t r0 = blk_row[b], r1 = blk_row[b + 1];
+    const Item it = items[blockIdx.x];
+    const int64_t r0 = it.r0, r1 = it.r1;
     if (!FJ_IDX_OK(1, r0, n_rows) || !FJ_IDX_OK(2, r1, n_rows + 1) || !FJ_IDX_OK(3, r1 - r0, kBlockRows + 1)) return;
-    const int64_t k0 = rp[r0], k1 = rp[r1];
-    const int64_t nz = k1 - k0;
+    const int64_t k0 = it.k0, k1 = it.k1;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int gph = graph_of ? graph_of[r0] : 0;
     if (!FJ_IDX_OK(6, gph, 1 << 20)) return;
     const double ce = reinterpret_cast<const double *>(gs)[(int64_t)gph * kGs + 1];
     double m_abs = 0.0, m_rel = 0.0, m_z = 0.0, viol = 0.0;
+    bool any = false;
 
-    auto epilogue = [&](int64_t x, double acc) {
+    auto epilogue = [&](int64_t x, double rx) {
         double zx = zhat[x];
-        double rx = sp[x] - zx + acc;
         double ax = fabs(rx);
         if (!(ax <= 1e300)) ax = INFINITY;
         m_abs = fmax(m_abs, ax);
@@ -385,9 +574,10 @@ k_certify(const int64_t *__restrict__ rp, const int32_t *__restrict__ col, const
         r[x] = resid_store<T>(rx);
         da[x] = T(0);
         db[x] = T(0);
+        any = true;
     };
 
-    if (nz > 2 * kBlockNnz) {
+    if (it.slot >= 0) {
         const double zx = zhat[r0];
         double acc = 0.0;
         for (int64_t k = k0 + threadIdx.x; k < k1; k += 256) {
@@ -400,15 +590,26 @@ k_certify(const int64_t *__restrict__ rp, const int32_t *__restrict__ col, const
         if (threadIdx.x == 0) {
             double t = 0.0;
             for (int i = 0; i < 8; ++i) t += wcarry[i];
-            epilogue(r0, t);
+            const int slot = it.slot;
+            const int first = slot_first[slot], nch = slot_nchunk[slot];
+            const int ci = (int)((k0 - rp[r0]) / kChunkNnz);
+            part[first + ci] = t;
+            __threadfence();
+            if (atomicAdd(&cnt[slot], 1) == nch - 1) {
+                __threadfence();
+                double s = 0.0;
+                for (int c = 0; c < nch; ++c) s += __ldcg(part + first + c);
+                cnt[slot] = 0;
+                epilogue(r0, sp[r0] - zx + s);
+            }
         }
     } else {
-        const int nzi = (int)nz;
+        const int nzi = (int)(k1 - k0);
         for (int i = threadIdx.x; i < nzi; i += 256) head[i] = 0;
         __syncthreads();
         for (int64_t x = r0 + threadIdx.x; x < r1; x += 256) {
             int64_t a = rp[x];
-            if (rp[x + 1] > a && FJ_IDX_OK(5, a - k0, nz)) head[a - k0] = 1;
+            if (rp[x + 1] > a && FJ_IDX_OK(5, a - k0, nzi)) head[a - k0] = 1;
         }
         __syncthreads();
         for (int i = threadIdx.x; i < nzi; i += 256) {
@@ -421,19 +622,21 @@ k_certify(const int64_t *__restrict__ rp, const int32_t *__restrict__ col, const
         __syncthreads();
         for (int64_t x = r0 + threadIdx.x; x < r1; x += 256) {
             int64_t a = rp[x], e = rp[x + 1];
+            const double zx = zhat[x];
             // sum_j a_xj zhat_j - d_x zhat_x
-            epilogue(x, (e > a ? prod[e - 1 - k0] : 0.0) - deg[x] * zhat[x]);
+            epilogue(x, sp[x] - zx + (e > a ? prod[e - 1 - k0] : 0.0) - deg[x] * zx);
         }
     }
     m_abs = warp_max(m_abs);
     m_rel = warp_max(m_rel);
     m_z = warp_max(m_z);
     viol = warp_sum(viol);
+    unsigned anyw = __ballot_sync(0xffffffffu, any);
     if (lane == 0) {
         red[0][wid] = m_abs;
         red[1][wid] = m_rel;
         red[2][wid] = m_z;
-        red[3][wid] = viol;
+        red[3][wid] = anyw ? viol : 0.0;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -493,7 +696,7 @@ static fj_status ws_grow(fj_graph *g, int64_t entries, int ngraphs)
 {
     Workspace &ws = g->ws;
     if (entries > ws.cap_n) {
-        void **bufs[] = {&ws.r, &ws.h, &ws.da, &ws.db};
+        void **bufs[] = {&ws.r, &ws.h, &ws.da, &ws.db, &ws.om};
         for (void **p : bufs) {
             dev_free(*p);
             *p = nullptr;
@@ -509,6 +712,7 @@ static fj_status ws_grow(fj_graph *g, int64_t entries, int ngraphs)
         ws.list = nullptr;
         FJ_CUDA(cudaMalloc(&ws.list, sizeof(int32_t) * (size_t)entries));
         ws.cap_n = entries;
+        ws.gen++;
     }
     if (ngraphs > ws.cap_graphs) {
         dev_free(ws.gstat);
@@ -518,6 +722,14 @@ static fj_status ws_grow(fj_graph *g, int64_t entries, int ngraphs)
         FJ_CUDA(cudaMalloc(&ws.gstat, sizeof(double) * kGs * ngraphs));
         FJ_CUDA(cudaMallocHost(&ws.gstat_host, sizeof(double) * kGs * ngraphs));
         ws.cap_graphs = ngraphs;
+    }
+    const int64_t need_prod = g->csr.nnz + kNnzPad;
+    if (need_prod > ws.cap_prod) {
+        dev_free(ws.prod);
+        ws.prod = nullptr;
+        FJ_CUDA(cudaMalloc(&ws.prod, sizeof(double) * (size_t)need_prod));
+        ws.cap_prod = need_prod;
+        ws.gen++;
     }
     if (!ws.ctr) {
         FJ_CUDA(cudaMalloc(&ws.ctr, sizeof(Counters)));
@@ -529,14 +741,13 @@ static fj_status ws_grow(fj_graph *g, int64_t entries, int ngraphs)
 struct Plan {
     const DevCSR *c = nullptr;  // CSR the push runs on
     const int32_t *perm = nullptr;
+    const ItemPlan *ip = nullptr;   // block-tile items (certificate)
+    const ItemPlan *wip = nullptr;  // warp-tile items (sweep)
     bool mc = false;
-    int head_classes = 0;       // classes launched one by one
-    int64_t tail_row = 0;       // first row of the merged tail block (== n when none)
-    int64_t tail_blk0 = 0, tail_blk1 = 0;
 };
 
 // Launch bookkeeping of one solve: every kernel launched, and with profiling
-// a CUDA-event pair around every push launch on the solve's stream.
+// a CUDA-event pair around every sweep-kernel launch on the solve's stream.
 struct Run {
     int64_t launches = 0;
     int64_t push_launches = 0;
@@ -596,6 +807,103 @@ static fj_status check_opts(const fj_solve_opts *o)
     FJ_ARG(!(o->schedule == FJ_SCHED_JACOBI && o->omega > 1.0), "JACOBI rounds need omega <= 1");
     FJ_ARG(o->max_sweeps >= 1, "max_sweeps must be >= 1");
     FJ_ARG(o->max_refine >= 0, "max_refine must be >= 0");
+    FJ_ARG(o->palette >= 0 && o->palette <= 32, "palette must be 0 (unbounded) or 1..32");
+    return FJ_OK;
+}
+
+__global__ void k_gather_rp(int64_t nb, const int32_t *__restrict__ blk_row, const int64_t *__restrict__ rp,
+                            long long *__restrict__ out)
+{
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b <= nb; b += (int64_t)gridDim.x * blockDim.x)
+        out[b] = rp[blk_row[b]];
+}
+
+// Work items of a CSR in row order: every row block, with rows longer than
+// two staged tiles cut into kChunkNnz chunks.  class_row (multicolour) gives
+// each item the first row of its colour class; without it every item gets 0.
+static fj_status build_items(fj_graph *g, const DevCSR &c, const std::vector<int64_t> *class_row, ItemPlan &ip,
+                             cudaStream_t st, bool warp_tiles)
+{
+    const int64_t nb = warp_tiles ? c.nwblocks : c.nblocks;
+    const int32_t *blk_row = warp_tiles ? c.wblk_row : c.blk_row;
+    const int64_t long_row = warp_tiles ? 2 * kWarpNnz : 2 * kBlockNnz;
+    const int64_t chunk = warp_tiles ? kWarpChunk : kChunkNnz;
+    std::vector<int32_t> br((size_t)nb + 1);
+    std::vector<long long> bk((size_t)nb + 1);
+    long long *bk_d = nullptr;
+    FJ_CUDA(cudaMalloc(&bk_d, sizeof(long long) * (nb + 1)));
+    k_gather_rp<<<grid_for(nb + 1, 256), 256, 0, st>>>(nb, blk_row, c.row_ptr, bk_d);
+    FJ_CUDA(cudaGetLastError());
+    FJ_CUDA(cudaMemcpyAsync(br.data(), blk_row, sizeof(int32_t) * (nb + 1), cudaMemcpyDeviceToHost, st));
+    FJ_CUDA(cudaMemcpyAsync(bk.data(), bk_d, sizeof(long long) * (nb + 1), cudaMemcpyDeviceToHost, st));
+    FJ_CUDA(cudaStreamSynchronize(st));
+    dev_free(bk_d);
+    std::vector<Item> items;
+    std::vector<int32_t> sfirst, snch;
+    items.reserve((size_t)nb + 16);
+    int64_t nparts = 0;
+    size_t cls = 0;
+    for (int64_t b = 0; b < nb; ++b) {
+        Item it;
+        it.r0 = br[(size_t)b];
+        it.r1 = br[(size_t)b + 1];
+        it.lo = 0;
+        if (class_row) {
+            while (cls + 1 < class_row->size() && (*class_row)[cls + 1] <= it.r0) ++cls;
+            it.lo = (int32_t)(*class_row)[cls];
+        }
+        const int64_t k0 = bk[(size_t)b], k1 = bk[(size_t)b + 1];
+        if (k1 - k0 > long_row) {
+            const int64_t nch = ceil_div(k1 - k0, chunk);
+            it.slot = (int32_t)sfirst.size();
+            sfirst.push_back((int32_t)nparts);
+            snch.push_back((int32_t)nch);
+            nparts += nch;
+            for (int64_t ch = 0; ch < nch; ++ch) {
+                it.k0 = k0 + ch * chunk;
+                it.k1 = std::min(k1, it.k0 + chunk);
+                items.push_back(it);
+            }
+        } else {
+            it.slot = -1;
+            it.k0 = k0;
+            it.k1 = k1;
+            items.push_back(it);
+        }
+    }
+    ip.nitems = (int64_t)items.size();
+    ip.nslots = (int64_t)sfirst.size();
+    // first item of every colour class (the items are in row order, the rows in class order)
+    ip.class_item.clear();
+    if (class_row) {
+        size_t at = 0;
+        for (size_t k = 0; k + 1 < class_row->size(); ++k) {
+            while (at < items.size() && items[at].r0 < (*class_row)[k]) ++at;
+            ip.class_item.push_back((int64_t)at);
+        }
+    } else {
+        ip.class_item.push_back(0);
+    }
+    ip.class_item.push_back(ip.nitems);
+    ip.class_k.assign(ip.class_item.size(), bk.empty() ? 0 : bk.back());
+    for (size_t k = 0; k + 1 < ip.class_item.size(); ++k)
+        ip.class_k[k] = ip.class_item[k] < ip.nitems ? items[(size_t)ip.class_item[k]].k0 : bk.back();
+    ip.nparts = nparts;
+    FJ_CUDA(cudaMalloc(&ip.items, sizeof(Item) * std::max<size_t>(items.size(), 1)));
+    FJ_CUDA(cudaMalloc(&ip.slot_first, sizeof(int32_t) * std::max<size_t>(sfirst.size(), 1)));
+    FJ_CUDA(cudaMalloc(&ip.slot_nchunk, sizeof(int32_t) * std::max<size_t>(snch.size(), 1)));
+    FJ_CUDA(cudaMalloc(&ip.cnt, sizeof(int32_t) * std::max<size_t>(sfirst.size(), 1)));
+    FJ_CUDA(cudaMalloc(&ip.part, sizeof(double) * std::max<int64_t>(nparts, 1)));
+    FJ_CUDA(cudaMemcpyAsync(ip.items, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice, st));
+    if (!sfirst.empty()) {
+        FJ_CUDA(cudaMemcpyAsync(ip.slot_first, sfirst.data(), sizeof(int32_t) * sfirst.size(), cudaMemcpyHostToDevice,
+                                st));
+        FJ_CUDA(cudaMemcpyAsync(ip.slot_nchunk, snch.data(), sizeof(int32_t) * snch.size(), cudaMemcpyHostToDevice,
+                                st));
+    }
+    FJ_CUDA(cudaMemsetAsync(ip.cnt, 0, sizeof(int32_t) * std::max<size_t>(sfirst.size(), 1), st));
+    FJ_CUDA(cudaStreamSynchronize(st));
+    ip.built = true;
     return FJ_OK;
 }
 
@@ -604,73 +912,130 @@ static fj_status make_plan(fj_graph *g, const fj_solve_opts *o, cudaStream_t st,
     p.mc = o->schedule != FJ_SCHED_JACOBI;
     if (!p.mc) {
         p.c = &g->csr;
-        p.tail_row = g->csr.n;
+        if (!g->plan_csr.built) FJ_CHECK(build_items(g, g->csr, nullptr, g->plan_csr, st, false));
+        if (!g->wplan_csr.built) FJ_CHECK(build_items(g, g->csr, nullptr, g->wplan_csr, st, true));
+        p.ip = &g->plan_csr;
+        p.wip = &g->wplan_csr;
         return FJ_OK;
     }
-    FJ_CHECK(ensure_colouring(g, st));
-    const Colouring &cl = g->colr;
-    p.c = &cl.pcsr;
-    p.perm = cl.perm;
-    // the tail: the longest run of final classes that are each smaller than tail_rows
-    int64_t tail_rows = o->tail_rows > 0 ? o->tail_rows : 4096;
-    int k = cl.ncolours;
-    while (k > 1 && cl.class_row[k] - cl.class_row[k - 1] < tail_rows) --k;
-    if (k == cl.ncolours - 1) k = cl.ncolours;  // a single small last class is launched on its own
-    p.head_classes = k;
-    p.tail_row = cl.class_row[k];
-    p.tail_blk0 = cl.class_blk[k];
-    p.tail_blk1 = cl.pcsr.nblocks;
+    FJ_CHECK(ensure_colouring(g, o->palette, st));
+    p.c = &g->colr.pcsr;
+    p.perm = g->colr.perm;
+    if (!g->plan_pcsr.built) FJ_CHECK(build_items(g, g->colr.pcsr, &g->colr.class_row, g->plan_pcsr, st, false));
+    if (!g->wplan_pcsr.built) FJ_CHECK(build_items(g, g->colr.pcsr, &g->colr.class_row, g->wplan_pcsr, st, true));
+    p.ip = &g->plan_pcsr;
+    p.wip = &g->wplan_pcsr;
     return FJ_OK;
 }
 
+// Resident blocks of the sweep kernel on this device (persistent grid size).
 template <typename T>
-static fj_status launch_pull(const DevCSR &c, int64_t blk0, int64_t blk1, const T *din, T *dout, Workspace &ws,
-                             double omega, cudaStream_t st, Run &run)
+static int64_t sweep_blocks(bool weighted)
 {
-    if (blk1 <= blk0) return FJ_OK;
-    FJ_CHECK(run.before(st));
-    const unsigned nb = (unsigned)(blk1 - blk0);
+    static int cached[2] = {0, 0};
+    int &nres = cached[weighted ? 1 : 0];
+    if (nres == 0) {
+        int dev = 0, sms = 0, per = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return 152;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        constexpr int kSweepWarps = sweep_warps<T>();
+        if (weighted) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep<T, true>, 32 * kSweepWarps, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep<T, false>, 32 * kSweepWarps, 0);
+        nres = std::max(1, sms * std::max(1, per));
+    }
+    return nres;
+}
+
+// One sweep (multicolour: one launch per colour class, in order) or round
+// (Jacobi: one launch), then the stop test.  The two increment buffers swap
+// roles every sweep.
+template <typename T>
+static fj_status launch_sweep(fj_graph *g, const Plan &p, cudaStream_t st, Run &run, int64_t sweep)
+{
+    Workspace &ws = g->ws;
+    const DevCSR &c = *p.c;
+    const ItemPlan &wp = *p.wip;
+    T *bufs[2] = {reinterpret_cast<T *>(ws.da), reinterpret_cast<T *>(ws.db)};
+    T *dcur = bufs[sweep & 1];
+    const T *dprev = bufs[(sweep - 1) & 1];
     T *r = reinterpret_cast<T *>(ws.r);
     const T *h = reinterpret_cast<const T *>(ws.h);
     const T *inv;
     if constexpr (sizeof(T) == 4) inv = reinterpret_cast<const T *>(c.inv32);
     else inv = reinterpret_cast<const T *>(c.inv64);
-    if (c.w)
-        k_pull<T, true><<<nb, 256, 0, st>>>(c.row_ptr, c.col, c.w, c.blk_row, blk0, din, dout, r, h, inv, ws.zhat,
-                                            c.indeg, (T)omega, ws.ctr, c.n);
-    else
-        k_pull<T, false><<<nb, 256, 0, st>>>(c.row_ptr, c.col, c.w, c.blk_row, blk0, din, dout, r, h, inv, ws.zhat,
-                                             c.indeg, (T)omega, ws.ctr, c.n);
-    FJ_CUDA(cudaGetLastError());
-    return run.after(st);
-}
-
-// One sweep (multicolour) or round (Jacobi).  Jacobi alternates the two
-// increment buffers, so `parity` selects the direction.
-template <typename T>
-static fj_status launch_sweep(fj_graph *g, const Plan &p, double omega, int parity, cudaStream_t st, Run &run)
-{
-    Workspace &ws = g->ws;
-    const DevCSR &c = *p.c;
-    T *da = reinterpret_cast<T *>(ws.da), *db = reinterpret_cast<T *>(ws.db);
-    if (!p.mc) {
-        const T *din = parity ? db : da;
-        T *dout = parity ? da : db;
-        FJ_CHECK(launch_pull<T>(c, 0, c.nblocks, din, dout, ws, omega, st, run));
-    } else {
-        const Colouring &cl = g->colr;
-        for (int k = 0; k < p.head_classes; ++k)
-            FJ_CHECK(launch_pull<T>(c, cl.class_blk[k], cl.class_blk[k + 1], da, da, ws, omega, st, run));
-        if (p.tail_blk1 > p.tail_blk0) {
-            // unrelaxed Jacobi step over the merged small classes, then commit its increments
-            FJ_CHECK(launch_pull<T>(c, p.tail_blk0, p.tail_blk1, da, db, ws, std::min(omega, 1.0), st, run));
-            FJ_CUDA(cudaMemcpyAsync(da + p.tail_row, db + p.tail_row, sizeof(T) * (c.n - p.tail_row),
-                                    cudaMemcpyDeviceToDevice, st));
-        }
+    const T *om = reinterpret_cast<const T *>(ws.om);
+    T *prod = reinterpret_cast<T *>(ws.prod);
+    const int32_t *lo_of = nullptr;
+    (void)lo_of;
+    for (size_t k = 0; k + 1 < wp.class_item.size(); ++k) {
+        const int64_t i0 = wp.class_item[k], ni = wp.class_item[k + 1] - i0;
+        if (ni <= 0) continue;
+        const int64_t kk0 = wp.class_k[k], kk1 = wp.class_k[k + 1];
+        // the class's first row: every column below it belongs to an earlier class
+        const int lo = p.mc ? (int)g->colr.class_row[k] : 0;
+        const unsigned pgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(kk1 - kk0, 256 * 4), 152 * 8));
+        FJ_CHECK(run.before(st));
+        if (c.w)
+            k_products<T, true><<<pgrid, 256, 0, st>>>(kk0, kk1, c.col, c.w, lo, dcur, dprev, prod, c.n, ws.ctr);
+        else
+            k_products<T, false><<<pgrid, 256, 0, st>>>(kk0, kk1, c.col, c.w, lo, dcur, dprev, prod, c.n, ws.ctr);
+        FJ_CUDA(cudaGetLastError());
+        constexpr int kSweepWarps = sweep_warps<T>();
+        const unsigned grid =
+            (unsigned)std::min<int64_t>(ceil_div(ni, kSweepWarps), sweep_blocks<T>(c.w != nullptr));
+        if (c.w)
+            k_sweep<T, true><<<grid, 32 * kSweepWarps, 0, st>>>(wp.items, i0, ni, c.row_ptr, prod, dcur, r, h, inv,
+                                                                ws.zhat, c.indeg, om, wp.slot_first, wp.slot_nchunk,
+                                                                wp.part, wp.cnt, ws.ctr, c.n);
+        else
+            k_sweep<T, false><<<grid, 32 * kSweepWarps, 0, st>>>(wp.items, i0, ni, c.row_ptr, prod, dcur, r, h, inv,
+                                                                 ws.zhat, c.indeg, om, wp.slot_first, wp.slot_nchunk,
+                                                                 wp.part, wp.cnt, ws.ctr, c.n);
+        FJ_CUDA(cudaGetLastError());
+        FJ_CHECK(run.after(st));
+        ++run.launches;  // the products launch
     }
     k_end_sweep<<<1, 1, 0, st>>>(ws.ctr);
     FJ_CUDA(cudaGetLastError());
     ++run.launches;
+    return FJ_OK;
+}
+
+// A batch of `nsweeps` (even) sweeps captured once into a CUDA graph and
+// replayed; the buffer parity repeats every two sweeps, and a pass always
+// starts from cleared increment buffers, so every replay is exact.
+template <typename T>
+static fj_status sweep_graph(fj_graph *g, const Plan &p, int nsweeps, cudaGraphExec_t *out, int *launches)
+{
+    Workspace &ws = g->ws;
+    const int a = sizeof(T) == 8 ? 1 : 0, b = p.mc ? 1 : 0;
+    if (ws.gexec[a][b] && ws.gkey[a][b] == ws.gen && ws.gsweeps[a][b] == nsweeps) {
+        *out = ws.gexec[a][b];
+        *launches = ws.glaunch[a][b];
+        return FJ_OK;
+    }
+    if (ws.gexec[a][b]) cudaGraphExecDestroy(ws.gexec[a][b]);
+    ws.gexec[a][b] = nullptr;
+    if (!ws.cap_stream) FJ_CUDA(cudaStreamCreateWithFlags(&ws.cap_stream, cudaStreamNonBlocking));
+    Run dummy;
+    FJ_CUDA(cudaStreamBeginCapture(ws.cap_stream, cudaStreamCaptureModeThreadLocal));
+    fj_status s = FJ_OK;
+    for (int j = 0; j < nsweeps && s == FJ_OK; ++j) s = launch_sweep<T>(g, p, ws.cap_stream, dummy, j);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(ws.cap_stream, &graph);
+    if (s != FJ_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return s;
+    }
+    FJ_CUDA(e);
+    e = cudaGraphInstantiate(&ws.gexec[a][b], graph, 0);
+    cudaGraphDestroy(graph);
+    FJ_CUDA(e);
+    ws.gkey[a][b] = ws.gen;
+    ws.gsweeps[a][b] = nsweeps;
+    ws.glaunch[a][b] = (int)dummy.launches;
+    *out = ws.gexec[a][b];
+    *launches = (int)dummy.launches;
     return FJ_OK;
 }
 
@@ -680,16 +1045,31 @@ static fj_status launch_certify(fj_graph *g, const Plan &p, double epsp, cudaStr
     run.launches += 2;
     Workspace &ws = g->ws;
     const DevCSR &c = *p.c;
+    const ItemPlan &ip = *p.ip;
     k_cert_reset<<<grid_for(g->ngraphs, 256), 256, 0, st>>>(g->ngraphs, reinterpret_cast<unsigned long long *>(ws.gstat));
     T *r = reinterpret_cast<T *>(ws.r), *da = reinterpret_cast<T *>(ws.da), *db = reinterpret_cast<T *>(ws.db);
     unsigned long long *gs = reinterpret_cast<unsigned long long *>(ws.gstat);
+    const unsigned grid = (unsigned)ip.nitems;
     if (c.w)
-        k_certify<T, true><<<(unsigned)c.nblocks, 256, 0, st>>>(c.row_ptr, c.col, c.w, c.blk_row, ws.zhat, ws.sp,
-                                                                c.deg64, c.graph_of, epsp, r, da, db, gs, c.n);
+        k_certify<T, true><<<grid, 256, 0, st>>>(ip.items, c.row_ptr, c.col, c.w, ws.zhat, ws.sp, c.deg64, c.graph_of,
+                                                 epsp, r, da, db, gs, ip.slot_first, ip.slot_nchunk, ip.part, ip.cnt,
+                                                 c.n);
     else
-        k_certify<T, false><<<(unsigned)c.nblocks, 256, 0, st>>>(c.row_ptr, c.col, c.w, c.blk_row, ws.zhat, ws.sp,
-                                                                 c.deg64, c.graph_of, epsp, r, da, db, gs, c.n);
+        k_certify<T, false><<<grid, 256, 0, st>>>(ip.items, c.row_ptr, c.col, c.w, ws.zhat, ws.sp, c.deg64,
+                                                  c.graph_of, epsp, r, da, db, gs, ip.slot_first, ip.slot_nchunk,
+                                                  ip.part, ip.cnt, c.n);
     FJ_CUDA(cudaGetLastError());
+    return FJ_OK;
+}
+
+static fj_status check_index_record()
+{
+    long long dbg[4] = {0, 0, 0, 0};
+    FJ_CUDA(cudaMemcpyFromSymbol(dbg, g_fj_dbg, sizeof(dbg)));
+    if (dbg[0]) {
+        set_error("index check failed: site %lld block %lld index %lld limit %lld", dbg[0], dbg[1], dbg[2], dbg[3]);
+        return FJ_ERR_INVALID_ARG;
+    }
     return FJ_OK;
 }
 
@@ -723,45 +1103,45 @@ static fj_status solve_t(fj_graph *g, const double *s, const double *z0, const f
     k_shift<<<grid_for(ng, 256), 256, 0, st>>>(ng, gs, o->c);
     T *r = reinterpret_cast<T *>(ws.r), *h = reinterpret_cast<T *>(ws.h);
     T *da = reinterpret_cast<T *>(ws.da), *db = reinterpret_cast<T *>(ws.db);
-    k_init<T><<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(n, sd, z0d, p.perm, c.graph_of, gs, epsp, ws.sp, ws.zhat, r,
-                                                         h, da, db);
+    const double *din = p.mc ? g->colr.din_p : nullptr;
+    k_init<T><<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(n, sd, z0d, p.perm, c.graph_of, gs, epsp, o->omega, c.deg64,
+                                                         din, ws.sp, ws.zhat, r, h, da, db,
+                                                         reinterpret_cast<T *>(ws.om));
     FJ_CUDA(cudaGetLastError());
     FJ_CUDA(cudaMemsetAsync(ws.ctr, 0, sizeof(Counters), st));
     FJ_CHECK(read_dev_error(g, st));
     Run run;
     run.profile = o->profile != 0;
-    run.launches += 5;  // gstat reset, min s, shift, init, (memset)
+    run.launches += 4;  // gstat reset, min s, shift, init
     if (z0) FJ_CHECK(launch_certify<T>(g, p, epsp, st, run));  // warm start: exact FP64 residual of z0
 
-    // profiling times every push launch, so no sweep may run past the stop flag
-    const int check = run.profile ? 1 : (o->check_every > 0 ? o->check_every : 8);
+    // profiling times every sweep launch, so no sweep may run past the stop flag;
+    // otherwise sweeps run in captured batches of an even count
+    int check = run.profile ? 1 : (o->check_every > 0 ? o->check_every : 8);
+    if (!run.profile) check += check & 1;
+    cudaGraphExec_t batch = nullptr;
+    int batch_launches = 0;
+    if (!run.profile) FJ_CHECK(sweep_graph<T>(g, p, check, &batch, &batch_launches));
     int refine = 0;
     fj_status result = FJ_OK;
-    int parity = 0;
     for (;;) {
         k_pass_reset<<<1, 1, 0, st>>>(ws.ctr, o->max_sweeps);
         FJ_CUDA(cudaGetLastError());
         ++run.launches;
         for (;;) {
-            for (int j = 0; j < check; ++j) {
-                FJ_CHECK(launch_sweep<T>(g, p, o->omega, parity, st, run));
-                parity ^= 1;
+            if (batch) {
+                FJ_CUDA(cudaGraphLaunch(batch, st));
+                run.launches += batch_launches;
+                run.push_launches += batch_launches - check;
+            } else {
+                for (int j = 0; j < check; ++j) FJ_CHECK(launch_sweep<T>(g, p, st, run, ++ws.sweep_parity));
             }
             FJ_CUDA(cudaMemcpyAsync(ws.ctr_host, ws.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
             FJ_CUDA(cudaStreamSynchronize(st));
             FJ_CHECK(run.harvest());
-            {
-                long long dbg[4] = {0, 0, 0, 0};
-                FJ_CUDA(cudaMemcpyFromSymbol(dbg, g_fj_dbg, sizeof(dbg)));
-                if (dbg[0]) {
-                    set_error("index check failed: site %lld block %lld index %lld limit %lld", dbg[0], dbg[1], dbg[2],
-                              dbg[3]);
-                    return FJ_ERR_INVALID_ARG;
-                }
-            }
+            FJ_CHECK(check_index_record());
             if (ws.ctr_host->done) break;
         }
-        // Jacobi rounds that ran after the stop flag were no-ops; re-align parity
         const int done = ws.ctr_host->done;
         if (done == 3) {
             result = FJ_ERR_DIVERGED;
@@ -771,14 +1151,7 @@ static fj_status solve_t(fj_graph *g, const double *s, const double *z0, const f
         FJ_CHECK(launch_certify<T>(g, p, epsp, st, run));
         FJ_CUDA(cudaMemcpyAsync(ws.gstat_host, ws.gstat, sizeof(double) * kGs * ng, cudaMemcpyDeviceToHost, st));
         FJ_CUDA(cudaStreamSynchronize(st));
-        {
-            long long dbg[4] = {0, 0, 0, 0};
-            FJ_CUDA(cudaMemcpyFromSymbol(dbg, g_fj_dbg, sizeof(dbg)));
-            if (dbg[0]) {
-                set_error("index check failed: site %lld block %lld index %lld limit %lld", dbg[0], dbg[1], dbg[2], dbg[3]);
-                return FJ_ERR_INVALID_ARG;
-            }
-        }
+        FJ_CHECK(check_index_record());
         double viol = 0.0;
         for (int i = 0; i < ng; ++i) viol += ws.gstat_host[i * kGs + 5];
         if (viol == 0.0) break;
@@ -793,7 +1166,6 @@ static fj_status solve_t(fj_graph *g, const double *s, const double *z0, const f
             break;
         }
         ++refine;
-        parity = 0;  // certify cleared both increment buffers
     }
     // unshift into caller order
     double *zdst = mem == FJ_MEM_DEVICE ? z_out : ws.zout;

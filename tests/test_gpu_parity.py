@@ -88,6 +88,17 @@ def test_colouring_matches_greedy_oracle(capi, kind):
     assert k == kw and np.array_equal(colour, want)
 
 
+@pytest.mark.parametrize("kind,K", [("rmat_dir", 8), ("rmat_und", 4), ("ba", 3)])
+def test_palette_colouring_matches_oracle(capi, kind, K):
+    g = {"rmat_dir": lambda: W.rmat_directed(12), "rmat_und": lambda: W.rmat_undirected(12),
+         "ba": lambda: W.ba_graph(4000, 5, seed_off=43)}[kind]()
+    rp, col, w = csr_of(g)
+    G = capi.Graph.from_csr(g["n"], *to_dev(rp, col, w), directed=g["directed"])
+    colour, k = G.colour(palette=K)
+    want, kw, din = oracle.palette_colour(g["n"], rp, col, w, g["directed"], K)
+    assert k == kw and np.array_equal(colour, want)
+
+
 # ------------------------------------------------------------ solve parity
 
 @pytest.fixture(scope="module")

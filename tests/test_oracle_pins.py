@@ -411,3 +411,50 @@ def test_empty_and_edgeless_graphs():
     z, r, p, u, ok = oracle.blisor_fifo(3, rp, col, None, s, 1e-6, 1.0)
     np.testing.assert_allclose(z, s, atol=1e-15)
     assert oracle.metrics(3, rp, col, None, s, z, False)["D"] == 0.0
+
+
+# ------------------------------------------------------------ palette colouring
+
+def test_palette_colouring_reduces_to_greedy_and_constant():
+    g = W.rmat_directed(11)
+    rp, col, w = oracle.csr_from_arcs(g["n"], g["src"], g["dst"], g["w"])
+    c0, k0 = oracle.greedy_colour(g["n"], rp, col)
+    c1, k1, din = oracle.palette_colour(g["n"], rp, col, w, True, 32 if k0 <= 32 else k0)
+    assert k1 == k0 and np.array_equal(c0, c1) and np.all(din == 0)
+    c2, k2, din2 = oracle.palette_colour(g["n"], rp, col, w, True, 1)
+    assert k2 == 1 and np.all(c2 == 0)
+    # with one colour every neighbour is in class: the in-class weight is the whole symmetric degree
+    sp_, sc_, sw_, sq_ = oracle.symmetric_weights(g["n"], rp, col, w, True)
+    rows = np.repeat(np.arange(g["n"]), np.diff(sp_))
+    np.testing.assert_allclose(din2, np.bincount(rows, weights=sw_, minlength=g["n"]))
+
+
+def test_palette_colouring_least_conflict_rule_brute_force():
+    rng = np.random.default_rng(5)
+    n = 60
+    rp, col, w = random_graph(n, 0.25, True, True, seed=8)
+    K = 3
+    colour, k, din = oracle.palette_colour(n, rp, col, w, True, K)
+    sp_, sc_, sw_, sq_ = oracle.symmetric_weights(n, rp, col, w, True)
+    order = oracle.colour_priority_order(n, sp_)
+    pos = np.empty(n, np.int64)
+    pos[order] = np.arange(n)
+    for v in range(n):
+        conf = np.zeros(K, np.int64)
+        for kk in range(sp_[v], sp_[v + 1]):
+            u = sc_[kk]
+            if pos[u] < pos[v]:
+                conf[colour[u]] += sq_[kk]
+        zero = np.flatnonzero(conf == 0)
+        want = zero[0] if len(zero) else int(np.argmin(conf))
+        assert colour[v] == want
+    # fixed-point weights of a pair sum both arcs
+    assert np.all(sq_ == np.rint(sw_ * 2.0 ** 32).astype(np.int64))
+
+
+def test_safe_omega_keeps_split_diagonally_dominant():
+    d = np.array([0.0, 3.0, 10.0, 5.0])
+    din = np.array([0.0, 3.0, 2.0, 0.0])
+    om = oracle.safe_omega(1.8, d, din)
+    assert om[0] == 1.8 and om[3] == 1.8
+    assert np.all((2 / om - 1) * (1 + d) >= din - 1e-12)
