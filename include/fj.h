@@ -253,6 +253,28 @@ fj_status fj_frontier(int64_t n, const void *r, const void *h, int precision, in
                       int64_t *count, void *stream);
 
 /*
+ * fj_frontier_static - the same frontier as fj_frontier, for callers that
+ * cannot allocate device memory: a process whose device memory is all handed
+ * out by its own pool, or code that must not let a call synchronise the
+ * device, which cudaMalloc and cudaFree can do.  It makes no allocation of
+ * any kind (no cudaMalloc, cudaFree, stream-ordered or library allocation).
+ * The paper has no counterpart: this is a property of the interface only.
+ *
+ * The look-back scratch is a file-scope device array sized for n up to 2^26
+ * (67,108,864) nodes, about 256 KB, which every GPU that loads the library
+ * holds until the process exits; a larger n returns FJ_ERR_INVALID_ARG.  The
+ * array is shared by every call: the call clears what must start at zero, and
+ * calls whose work overlaps on the GPU (on different streams, or from
+ * different threads) race on it and must not be made.  The first call on each
+ * device looks up the array's device address with cudaGetSymbolAddress; make
+ * that first call before any stream capture.  Arguments, layout and errors are
+ * those of fj_frontier: r, h, list and count are device pointers, list holds
+ * n entries, *count receives |F|.
+ */
+fj_status fj_frontier_static(int64_t n, const void *r, const void *h, int precision, int32_t *list,
+                             int64_t *count, void *stream);
+
+/*
  * fj_residual - FP64 residual r[n] = s' - (I + L) zhat' with s' = s + c_eff,
  * zhat' = z + c_eff, for caller-supplied s, z (FP64) and shift c_eff; the
  * quantity of Lemma 3 used by the certificate.

@@ -25,7 +25,7 @@ EXPORTED = [
     "fj_solve_opts_default", "fj_status_string", "fj_last_error", "fj_graph_create",
     "fj_graph_create_from_arcs", "fj_graph_create_ragged", "fj_graph_destroy", "fj_graph_info",
     "fj_graph_export", "fj_graph_colour", "fj_solve", "fj_solve_warm", "fj_solve_batch",
-    "fj_metrics", "fj_frontier", "fj_residual",
+    "fj_metrics", "fj_frontier", "fj_frontier_static", "fj_residual",
 ]
 
 
@@ -90,6 +90,7 @@ def lib():
     L.fj_solve_batch.argtypes = [VP, VP, I32, ctypes.POINTER(fj_solve_opts), VP, VP, I32]
     L.fj_metrics.argtypes = [VP, VP, VP, VP, I32, VP]
     L.fj_frontier.argtypes = [I64, VP, VP, I32, VP, VP, VP]
+    L.fj_frontier_static.argtypes = [I64, VP, VP, I32, VP, VP, VP]
     L.fj_residual.argtypes = [VP, VP, VP, D, VP, I32, VP]
     for name in EXPORTED:
         if name not in ("fj_solve_opts_default", "fj_graph_destroy", "fj_status_string", "fj_last_error"):
