@@ -30,11 +30,14 @@ import numpy as np  # noqa: E402
 
 WORKLOADS = {
     # name: generator, precision, omega, schedule
-    "rmat22_dir": dict(gen="rmat_dir", scale=22, precision="fp32", omega=1.5),
+    "rmat22_dir": dict(gen="rmat_dir", scale=22, precision="fp32", omega=1.5, palette=8),
     "ba20k": dict(gen="ba", n=20000, precision="fp64", omega=1.5),
     "rmat24_und": dict(gen="rmat_und", scale=24, precision="fp32", omega=1.8),
     "rmat16_dir": dict(gen="rmat_dir", scale=16, precision="fp32", omega=1.5),
     "rmat20_dir": dict(gen="rmat_dir", scale=20, precision="fp32", omega=1.5),
+    # 64 opinion vectors (U[0,1], Beta(1/2,1/2), +-1 labels) as one multi-right-hand-side push
+    "rmat22_und_k64": dict(gen="rmat_und_multi", scale=22, nvec=64, precision="fp32", omega=1.8, cpu_scale=19),
+    "rmat16_und_k64": dict(gen="rmat_und_multi", scale=16, nvec=64, precision="fp32", omega=1.8),
 }
 EPS = 1e-6
 METRIC = "FJ solves/s to 1e-6 rel. err (GTEPS, % HBM roofline): plain vs batched/warm-start"
@@ -50,6 +53,9 @@ def make_workload(name, scale_override=None):
         src, dst, w = g["src"], g["dst"], g["w"]
     elif spec["gen"] == "rmat_und":
         g = W.rmat_undirected(spec["scale"])
+        src, dst, w = W.symmetrize_arcs(g["src"], g["dst"], None)
+    elif spec["gen"] == "rmat_und_multi":
+        g = W.rmat_multirhs(spec["scale"], spec["nvec"])
         src, dst, w = W.symmetrize_arcs(g["src"], g["dst"], None)
     else:
         g = W.ba_graph(spec["n"], 5)
@@ -191,12 +197,37 @@ def run_gpu(args):
     G = capi.Graph.from_arcs(n, src_d, dst_d, w_d, directed=g["directed"])
     del src_d, dst_d, w_d
     ginfo = G.info()
-    s_host = g["S"][0]
+    k = int(spec.get("nvec", 1))
+    s_host = g["S"][0] if k == 1 else np.ascontiguousarray(np.stack(g["S"], axis=1))
+    del g["S"]
     s_d = torch.from_numpy(s_host).to(dev)
     z_d = torch.empty_like(s_d)
     opts = dict(eps=EPS, omega=omega, precision=prec, schedule=args.schedule)
-    if args.palette is not None:
-        opts["palette"] = args.palette
+    palette = args.palette if args.palette is not None else spec.get("palette")
+    if palette is not None:
+        opts["palette"] = palette
+
+    cols = None
+    if k > 1 and args.plain_loop:
+        # the same k vectors, solved one fj_solve call each (the plain method)
+        cols = [s_d[:, j].contiguous() for j in range(k)]
+        zcol = torch.empty_like(cols[0])
+
+    def solve(s, out, **kw):
+        if k == 1:
+            return G.solve(s, out=out, **kw)
+        if cols is not None:
+            infos_ = []
+            if s is s_d:
+                for c in cols:
+                    infos_.extend(G.solve(c, out=zcol, **kw)[1])
+            else:  # host buffers: one column at a time through the C ABI
+                for j in range(k):
+                    zj = np.empty(s.shape[0])
+                    infos_.extend(G.solve(np.ascontiguousarray(s[:, j]), out=zj, **kw)[1])
+                    out[:, j] = zj
+            return out, infos_, 0
+        return G.solve_batch(s, out=out, **kw)
     if args.check_every:
         opts["check_every"] = args.check_every
 
@@ -207,15 +238,15 @@ def run_gpu(args):
         torch.cuda.synchronize()
 
     for _ in range(args.warmup):
-        G.solve(s_d, out=z_d, **opts)
+        solve(s_d, z_d, **opts)
     barrier()
     clk, clk_path = clocks_start() if rank == 0 else (None, None)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     infos = []
     ev0.record(stream)
     for _ in range(args.steps):
-        _, info, _ = G.solve(s_d, out=z_d, **opts)
-        infos.append(info[0])
+        _, info, _ = solve(s_d, z_d, **opts)
+        infos.extend(info)
     ev1.record(stream)
     barrier()
     clocks = clocks_stop(clk, clk_path, local) if rank == 0 else None
@@ -226,17 +257,17 @@ def run_gpu(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     ms_per_step = ms / args.steps
-    value = world * args.steps / (ms / 1e3)
+    value = world * args.steps * k / (ms / 1e3)
     assert all(i["converged"] == 1 for i in infos), "a timed solve did not certify"
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     s_pin = torch.from_numpy(s_host).pin_memory().numpy()
-    z_pin = torch.empty(n, dtype=torch.float64).pin_memory().numpy()
-    G.solve(s_pin, out=z_pin, **opts)
+    z_pin = torch.empty(s_host.shape, dtype=torch.float64).pin_memory().numpy()
+    solve(s_pin, z_pin, **opts)
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        G.solve(s_pin, out=z_pin, **opts)
+        solve(s_pin, z_pin, **opts)
     barrier()
     e2e_s = time.perf_counter() - t0
     if world > 1:
@@ -244,32 +275,37 @@ def run_gpu(args):
         t = torch.tensor([e2e_s], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
-    e2e_value = world * args.steps / e2e_s
+    e2e_value = world * args.steps * k / e2e_s
 
     # roofline of the push kernel: algorithmic bytes over CUDA-event time of its launches
-    _, pinfo, _ = G.solve(s_d, out=z_d, profile=1, **opts)
+    if cols is not None:
+        _, pinfo, _ = G.solve(cols[0], out=zcol, profile=1, **opts)
+    else:
+        _, pinfo, _ = solve(s_d, z_d, profile=1, **opts)
     p = pinfo[0]
     peak, peak_kind = measured_peak_hbm()
     achieved = p["push_bytes"] / (p["push_ms"] / 1e3) / 1e9 if p["push_ms"] > 0 else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "traffic": None,
-                "kernel": "k_pull (push round)", "peak_source": peak_kind,
+                "kernel": ("k_products + k_sweep (one colour class)" if (k == 1 or cols is not None) else
+                           "k_sweep_batch (one colour class, %d vectors)" % k), "peak_source": peak_kind,
                 "bytes_per_launch": p["push_bytes"] / max(1, p["push_launches"]),
                 "avg_launch_us": 1e3 * p["push_ms"] / max(1, p["push_launches"])}
     info0 = infos[-1]
     detail = {"sweeps": info0["sweeps"], "pushes": info0["pushes"], "edges": info0["edges"],
               "refine_passes": info0["refine_passes"], "resid_rel_max": info0["resid_rel_max"],
               "eps_prime": info0["eps_prime"], "gteps": info0["edges"] / (ms_per_step / 1e3) / 1e9,
-              "ncolours": G.info()["ncolours"]}
+              "ncolours": G.info()["ncolours"], "vectors_per_step": k}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        dt, nnz_c, ok = oracle_solve_time(args.workload, args.cpu_scale, omega)
+        cpu_scale = args.cpu_scale if args.cpu_scale is not None else spec.get("cpu_scale")
+        dt, nnz_c, ok = oracle_solve_time(args.workload, cpu_scale, omega)
         scale_f = nnz_c / ginfo["nnz"]
         cpu = {"value": scale_f / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
                "sample": (f"one FIFO ImprovedBLISOR solve (omega={omega}, eps={EPS}, FP64, one host thread) of "
-                          + ("the full workload" if args.cpu_scale is None else
-                             f"the same generator at scale {args.cpu_scale}, rate scaled by nnz "
+                          + ("the full workload" if cpu_scale is None else
+                             f"the same generator at scale {cpu_scale}, rate scaled by nnz "
                              f"{nnz_c}/{ginfo['nnz']}") + f", {dt:.1f} s")}
 
     if rank == 0:
@@ -278,13 +314,17 @@ def run_gpu(args):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if prec == capi.FJ_PREC_FP32 else "f64", "data": "synthetic",
             "config": {"workload": args.workload, "n": n, "nnz": ginfo["nnz"], "directed": g["directed"],
+                       "vectors": k, "palette": palette,
+                       "mode": ("batched (fj_solve_batch)" if k > 1 and cols is None else
+                                "plain (one fj_solve per vector)"),
                        "omega": omega, "eps": EPS, "schedule": "multicolour" if args.schedule != 1 else "jacobi",
                        "precision": "FP32 push, FP64 estimate and certificate" if prec == capi.FJ_PREC_FP32
                        else "FP64", "l2": "inputs larger than L2 (CSR %.2f GB)" % (
                            ginfo["nnz"] * (8 if w is not None else 4) / 1e9),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
-            "gpu_launches": int(sum(i["launches"] for i in infos)),
+            "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": 8 * n * k,
+                    "d2h_bytes_per_step": 8 * n * k},
+            "gpu_launches": int(sum(i["launches"] for i in (infos if cols is not None else infos[::k]))),
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "detail": detail,
         }
         print(json.dumps(line), flush=True)
@@ -309,6 +349,8 @@ def main():
                     help="R-MAT scale of the CPU-baseline sample (default: the full workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--palette", type=int, default=None)
+    ap.add_argument("--plain-loop", action="store_true",
+                    help="multi-vector workloads: solve the vectors one fj_solve call each")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

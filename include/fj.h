@@ -109,7 +109,8 @@ typedef struct {
     double c_eff;            /* shift used: c + max(0, -min s) */
     double eps_prime;        /* sigma * eps / (c + sigma) (Alg. 2) */
     double resid_inf;        /* max_v |r_v|, r = s' - (I + L) zhat' in FP64 */
-    double resid_rel_max;    /* max_v |r_v| / s'_v; certificate holds when <= eps_prime */
+    double resid_rel_max;    /* max_v |r_v| / s'_v; <= eps_prime unless the FP64 resolution
+                                term of the certificate (see fj_solve) binds somewhere */
     double z_inf;            /* max_v |z_v| */
     double err_bound;        /* max_v |z_v - z*_v| <= resid_inf (Lemma 5 with a
                                 row-stochastic nonnegative (I + L)^{-1}) */
@@ -120,6 +121,9 @@ typedef struct {
                                 weight and gathered increment; per row the offsets, residual
                                 read/write, threshold, 1/(1+d) and increment write; per push
                                 the in-degree and the FP64 estimate read/write */
+    int64_t frontier_rounds; /* FP64 frontier push rounds (scatter form) run on the few
+                                entries the certificate left above threshold */
+    int64_t frontier_pushes; /* entries pushed by those rounds */
 } fj_solve_info;
 
 /* The measures of Table 1 (Section 3.4). */
@@ -206,11 +210,16 @@ fj_status fj_graph_colour(fj_graph *g, int palette, int32_t *colour, int *ncolou
 /*
  * fj_solve - ImprovedBLISOR (Alg. 3 with the shift of Alg. 2) on the GPU.
  * s[n] (FP64) innate opinions; z_out[n] (FP64) receives
- * zhat = (push estimate of (I+L)^{-1}(s + c_eff)) - c_eff.  On FJ_OK the FP64
- * certificate |r_v| <= eps' s'_v holds for every node, which gives
- * |z_v - zhat_v| <= eps' (z_v + c_eff) (Lemma 5).  info (may be NULL) gets
- * one record per graph.  FJ_ERR_NOT_CONVERGED / FJ_ERR_DIVERGED still write
- * z_out and info.
+ * zhat = (push estimate of (I+L)^{-1}(s + c_eff)) - c_eff.  On FJ_OK every
+ * node meets the FP64 certificate |r_v| <= max(eps' s'_v, 2^-51 (1 + d_v)
+ * |zhat'_v|), where r = s' - (I + L) zhat' is evaluated with compensated
+ * (twice-working-precision) sums.  The second term is the FP64 resolution of
+ * row v (one ulp of zhat'_v moves r_v by (1 + d_v) ulp); it binds only where
+ * eps' s'_v is finer than that (high degree, s'_v near c).  Where the first
+ * term binds everywhere, |z_v - zhat_v| <= eps' (z_v + c_eff) (Lemma 5); in
+ * all cases max_v |z_v - zhat_v| <= max_v |r_v| = info.err_bound, since
+ * ||(I + L)^{-1}||_inf <= 1.  info (may be NULL) gets one record per graph.
+ * FJ_ERR_NOT_CONVERGED / FJ_ERR_DIVERGED still write z_out and info.
  */
 fj_status fj_solve(fj_graph *g, const double *s, const fj_solve_opts *opts, double *z_out,
                    fj_solve_info *info, int mem);
@@ -227,9 +236,13 @@ fj_status fj_solve_warm(fj_graph *g, const double *s, const double *z0, const fj
 /*
  * fj_solve_batch - k opinion vectors on one graph as one multi-right-hand-side
  * push.  S and Z_out are node-major [n][k] FP64 (element (v, j) at v*k + j);
- * 1 <= k <= 64.  A node is visited when any of its k residuals is above its
- * threshold; each vector keeps its own shift, thresholds and certificate.
- * info (may be NULL) gets k records.
+ * 1 <= k <= 64.  Every (node, vector) pair keeps its own shift c_eff,
+ * threshold, residual and FP64 certificate, and pushes by the test of Alg. 3
+ * on its own residual; the sweeps are shared, so a node's column indices and
+ * weights are read once per sweep for all k vectors.  The result of each
+ * vector meets the same bound as fj_solve.  info (may be NULL) gets k
+ * records (sweeps, pushes and launches are batch totals).  A ragged handle is
+ * rejected with FJ_ERR_INVALID_ARG.  S must not alias Z_out.
  */
 fj_status fj_solve_batch(fj_graph *g, const double *S, int k, const fj_solve_opts *opts,
                          double *Z_out, fj_solve_info *info, int mem);

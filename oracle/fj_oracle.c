@@ -343,6 +343,48 @@ void oracle_residual(int64_t n, const int64_t *row_ptr, const int32_t *col, cons
 }
 
 /*
+ * The same residual r = s - (I + L) z, evaluated as if in twice the working
+ * precision and then rounded: the dot product of row v's terms
+ * (s_v, -(1 + d_v) z_v, a_vj z_j ...) is accumulated by Ogita, Rump and
+ * Oishi's Dot2 (SIAM J. Sci. Comput. 26, 2005), i.e. Knuth's error-free sum
+ * of each term into the running total and fma's exact product error, with
+ * the errors summed on the side.  d_v is summed the same way.  Used where a
+ * plain FP64 row sum would lose the residual to cancellation (rows whose
+ * terms are many orders of magnitude larger than the residual).
+ */
+static void dot2_add(double *hi, double *lo, double x)
+{
+    double s = *hi + x;
+    double bp = s - *hi;
+    double e = (*hi - (s - bp)) + (x - bp);
+    *hi = s;
+    *lo += e;
+}
+
+static void dot2_mul_add(double *hi, double *lo, double a, double b)
+{
+    double p = a * b;
+    double pe = fma(a, b, -p);
+    dot2_add(hi, lo, p);
+    *lo += pe;
+}
+
+void oracle_residual_dot2(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *w,
+                          const double *s, const double *z, double *r)
+{
+    for (int64_t v = 0; v < n; ++v) {
+        double dh = 1.0, dl = 0.0; /* 1 + d_v */
+        for (int64_t k = row_ptr[v]; k < row_ptr[v + 1]; ++k) dot2_add(&dh, &dl, w ? w[k] : 1.0);
+        double hi = s[v], lo = 0.0;
+        /* -(1 + d_v) z_v with 1 + d_v = dh + dl */
+        dot2_mul_add(&hi, &lo, -dh, z[v]);
+        dot2_mul_add(&hi, &lo, -dl, z[v]);
+        for (int64_t k = row_ptr[v]; k < row_ptr[v + 1]; ++k) dot2_mul_add(&hi, &lo, w ? w[k] : 1.0, z[col[k]]);
+        r[v] = hi + lo;
+    }
+}
+
+/*
  * Dense LU with partial pivoting (Doolittle, row interchanges), then forward
  * and back substitution: solves M x = b for a dense row-major n x n M, which
  * is overwritten.  Returns 0, or 1 for an exactly singular pivot.

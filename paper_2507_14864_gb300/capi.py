@@ -42,7 +42,8 @@ class fj_solve_info(ctypes.Structure):
                 ("c_eff", ctypes.c_double), ("eps_prime", ctypes.c_double), ("resid_inf", ctypes.c_double),
                 ("resid_rel_max", ctypes.c_double), ("z_inf", ctypes.c_double), ("err_bound", ctypes.c_double),
                 ("launches", ctypes.c_int64), ("push_launches", ctypes.c_int64), ("push_ms", ctypes.c_double),
-                ("push_bytes", ctypes.c_double)]
+                ("push_bytes", ctypes.c_double), ("frontier_rounds", ctypes.c_int64),
+                ("frontier_pushes", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -123,6 +123,71 @@ __device__ __forceinline__ void atomic_max_nonneg(double *addr, double v)
               static_cast<unsigned long long>(__double_as_longlong(v)));
 }
 
+// ------------------------------------------------------------------ compensated FP64
+
+// A sum carried as an unevaluated pair hi + lo.  two_sum is Knuth's
+// error-free addition (s + e = a + b exactly); a product's rounding error is
+// fma(a, b, -p).  Accumulating a dot product this way is Ogita, Rump and
+// Oishi's Dot2 (SIAM J. Sci. Comput. 26, 2005): the result is as accurate as
+// if computed in twice the working precision, then rounded.  The _rn
+// intrinsics keep the compiler from contracting these steps into FMAs.
+struct DD {
+    double hi, lo;
+};
+
+__device__ __forceinline__ void two_sum(double a, double b, double &s, double &e)
+{
+    s = __dadd_rn(a, b);
+    const double bp = __dsub_rn(s, a);
+    e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bp)), __dsub_rn(b, bp));
+}
+
+__device__ __forceinline__ void dd_add(DD &acc, double x)
+{
+    double s, e;
+    two_sum(acc.hi, x, s, e);
+    acc.hi = s;
+    acc.lo = __dadd_rn(acc.lo, e);
+}
+
+// acc += a * b
+__device__ __forceinline__ void dd_fma(DD &acc, double a, double b)
+{
+    const double p = __dmul_rn(a, b);
+    const double pe = fma(a, b, -p);
+    dd_add(acc, p);
+    acc.lo = __dadd_rn(acc.lo, pe);
+}
+
+__device__ __forceinline__ DD dd_merge(DD a, DD b)
+{
+    double s, e;
+    two_sum(a.hi, b.hi, s, e);
+    return DD{s, __dadd_rn(__dadd_rn(a.lo, b.lo), e)};
+}
+
+__device__ __forceinline__ DD warp_dd_sum(DD v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        DD u;
+        u.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+        u.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+        v = dd_merge(v, u);
+    }
+    return v;
+}
+
+__device__ __forceinline__ double dd_value(DD v) { return __dadd_rn(v.hi, v.lo); }
+
+// FP64 resolution of row x's residual: moving zhat'_x by one ulp moves r_x by
+// (1 + d_x) ulp(zhat'_x) <= 2^-52 (1 + d_x) |zhat'_x|, so a threshold below
+// this may be unreachable.  The certificate test takes the larger of the two.
+__device__ __forceinline__ double resid_floor(double deg, double zp)
+{
+    return 0x1p-51 * (1.0 + deg) * fabs(zp);
+}
+
 __device__ __forceinline__ unsigned lanemask_lt()
 {
     unsigned m;

@@ -688,7 +688,7 @@ void fj_graph_destroy(fj_graph *g)
     }
     Workspace &ws = g->ws;
     dev_free(ws.r); dev_free(ws.h); dev_free(ws.da); dev_free(ws.db); dev_free(ws.om); dev_free(ws.prod);
-    dev_free(ws.zhat); dev_free(ws.sp); dev_free(ws.sin); dev_free(ws.zout);
+    dev_free(ws.zhat); dev_free(ws.sp); dev_free(ws.sin); dev_free(ws.zout); dev_free(ws.r64);
     dev_free(ws.gstat); dev_free(ws.ctr); dev_free(ws.status); dev_free(ws.tile_ctr);
     dev_free(ws.list); dev_free(ws.count); dev_free(ws.partial);
     for (int a = 0; a < 2; ++a)
@@ -696,6 +696,11 @@ void fj_graph_destroy(fj_graph *g)
             if (ws.gexec[a][b]) cudaGraphExecDestroy(ws.gexec[a][b]);
     if (ws.cap_stream) cudaStreamDestroy(ws.cap_stream);
     if (ws.ctr_host) cudaFreeHost(ws.ctr_host);
+    BatchWorkspace &b = g->bws;
+    dev_free(b.r); dev_free(b.h); dev_free(b.da); dev_free(b.db); dev_free(b.zhat); dev_free(b.sp);
+    dev_free(b.sin); dev_free(b.zout); dev_free(b.om); dev_free(b.gstat); dev_free(b.partk);
+    dev_free(b.r64); dev_free(b.list);
+    if (b.gstat_host) cudaFreeHost(b.gstat_host);
     if (ws.gstat_host) cudaFreeHost(ws.gstat_host);
     sort_scratch_free(g->sort);
     dev_free(g->err);
@@ -1088,11 +1093,73 @@ static void colouring_free(fj_graph *g)
     dev_free(cl.perm);
     dev_free(cl.iperm);
     dev_free(cl.din_p);
+    dev_free(cl.tptr);
+    dev_free(cl.tcol);
+    dev_free(cl.tw);
     csr_free(cl.pcsr);
     cl = Colouring();
     item_plan_free(g->plan_pcsr);
     item_plan_free(g->wplan_pcsr);
     g->ws.gen++;
+}
+
+// In-neighbour list lengths in the permuted order: row i of the permuted
+// transpose is row perm[i] of the transpose.
+struct PermRowLen {
+    const int64_t *tptr;
+    const int32_t *perm;
+    __device__ long long operator()(int64_t i) const
+    {
+        const int64_t v = perm[i];
+        return (long long)(tptr[v + 1] - tptr[v]);
+    }
+};
+
+// One warp per new row i: copy transposed row perm[i] with its columns
+// renumbered into the permuted order.
+__global__ void k_permute_transpose(int64_t n, const int32_t *__restrict__ perm, const int32_t *__restrict__ iperm,
+                                    const int64_t *__restrict__ tptr, const int32_t *__restrict__ tcol,
+                                    const float *__restrict__ tw, const int64_t *__restrict__ pptr,
+                                    int32_t *__restrict__ pcol, float *__restrict__ pw)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = warp; i < n; i += nwarps) {
+        const int64_t v = perm[i];
+        const int64_t a = tptr[v], len = tptr[v + 1] - a, d = pptr[i];
+        for (int64_t t = lane; t < len; t += 32) {
+            pcol[d + t] = iperm[tcol[a + t]];
+            if (tw) pw[d + t] = tw[a + t];
+        }
+    }
+}
+
+fj_status ensure_ptranspose(fj_graph *g, cudaStream_t st)
+{
+    Colouring &cl = g->colr;
+    if (cl.tptr) return FJ_OK;
+    if (!cl.built || !g->directed || !g->tptr) {
+        set_error("internal: permuted transpose needs a colouring of a directed graph");
+        return FJ_ERR_INVALID_ARG;
+    }
+    const int64_t n = g->csr.n, nnz = g->csr.nnz;
+    long long *excl = nullptr;
+    FJ_CUDA(dalloc(&cl.tptr, n + 1));
+    FJ_CUDA(dalloc(&cl.tcol, std::max<int64_t>(nnz, 1)));
+    if (g->tw) FJ_CUDA(dalloc(&cl.tw, std::max<int64_t>(nnz, 1)));
+    FJ_CUDA(dalloc(&excl, n + 1));
+    FJ_CHECK(ws_status(g->ws, scan_tiles(n, 256 * 8)));
+    FJ_CUDA(scan<256, 8>(n, PermRowLen{g->tptr, cl.perm}, excl, g->ws.count, g->ws.status, g->ws.tile_ctr, g->err,
+                         st));
+    k_finish_ptr_dev<<<grid_for(n + 1, 256), 256, 0, st>>>(n, excl, g->ws.count, cl.tptr);
+    FJ_CUDA(cudaGetLastError());
+    k_permute_transpose<<<grid_for(n * 32, 256), 256, 0, st>>>(n, cl.perm, cl.iperm, g->tptr, g->tcol, g->tw,
+                                                               cl.tptr, cl.tcol, cl.tw);
+    FJ_CUDA(cudaGetLastError());
+    FJ_CUDA(cudaStreamSynchronize(st));
+    dev_free(excl);
+    return read_dev_error(g, st);
 }
 
 fj_status ensure_colouring(fj_graph *g, int palette, cudaStream_t st)

@@ -55,6 +55,11 @@ struct Colouring {
     std::vector<int64_t> class_row;  // host: rows of class c are [class_row[c], class_row[c+1])
     DevCSR pcsr;                     // permuted CSR, blocks never straddle a class
     std::vector<int64_t> class_blk;  // host: blocks of class c are [class_blk[c], class_blk[c+1])
+    // directed graphs, built on first use: in-neighbour lists in the permuted
+    // order (row i lists the new ids of the nodes that listen to perm[i])
+    int64_t *tptr = nullptr;
+    int32_t *tcol = nullptr;
+    float *tw = nullptr;
 };
 
 // Work items of a sweep, in the order of the sweep (colour order for the
@@ -77,7 +82,7 @@ struct ItemPlan {
     int64_t nslots = 0;          // long rows
     int32_t *slot_first = nullptr;  // device: first chunk index of each long row into part[]
     int32_t *slot_nchunk = nullptr; // device
-    double *part = nullptr;         // device: one partial sum per chunk
+    double *part = nullptr;         // device: one partial sum per chunk (two words: hi, lo)
     int32_t *cnt = nullptr;         // device: chunks finished per long row
     int64_t nparts = 0;
     std::vector<int64_t> class_item;  // host: items of class c are [class_item[c], class_item[c+1])
@@ -99,6 +104,7 @@ struct Workspace {
     double *sp = nullptr;   // s' = s + c_eff (FP64)
     double *sin = nullptr;  // caller's s, z0 or z staged on the device
     double *zout = nullptr; // unshifted result staged on the device
+    double *r64 = nullptr;  // FP64 residual written by the certificate (frontier push state)
     double *gstat = nullptr;  // per graph/RHS: [c_eff, min s, resid_inf, resid_rel, z_inf, violators]
     Counters *ctr = nullptr;
     Counters *ctr_host = nullptr;  // pinned mirror
@@ -120,6 +126,21 @@ struct Workspace {
     int64_t gen = 0;            // bumped whenever buffers or work-item plans change
 };
 
+// Scratch of a multi-right-hand-side solve: node-major [n][k] arrays.
+struct BatchWorkspace {
+    int64_t cap = 0;   // n * k entries held
+    int cap_k = 0;
+    void *r = nullptr, *h = nullptr, *da = nullptr, *db = nullptr;
+    double *zhat = nullptr, *sp = nullptr, *sin = nullptr, *zout = nullptr;
+    double *r64 = nullptr;     // FP64 residual written by the certificate
+    int32_t *list = nullptr;   // frontier of (node, vector) entries, n * k capacity
+    void *om = nullptr;        // per node
+    double *gstat = nullptr;   // per right-hand side, kGs words
+    double *gstat_host = nullptr;
+    double *partk = nullptr;   // per long-row chunk and right-hand side (two words: hi, lo)
+    int64_t cap_partk = 0;
+};
+
 }  // namespace fj
 
 struct fj_graph {
@@ -137,6 +158,7 @@ struct fj_graph {
     fj::ItemPlan plan_csr, plan_pcsr;    // block-tile items (certificate)
     fj::ItemPlan wplan_csr, wplan_pcsr;  // warp-tile items (sweep)
     fj::Workspace ws;
+    fj::BatchWorkspace bws;
     fj::SortScratch sort;
     int *err = nullptr;      // device error word
     int *err_host = nullptr; // pinned mirror
@@ -149,6 +171,7 @@ fj_status graph_finish(fj_graph *g, cudaStream_t st);
 fj_status build_blocks(DevCSR &c, const std::vector<int64_t> &seg_rows, Workspace &ws, int *err,
                        cudaStream_t st, bool warp_tiles);
 fj_status ensure_colouring(fj_graph *g, int palette, cudaStream_t st);
+fj_status ensure_ptranspose(fj_graph *g, cudaStream_t st);
 fj_status ws_status(Workspace &ws, int64_t tiles);
 fj_status read_dev_error(fj_graph *g, cudaStream_t st);
 void dev_free(void *p);

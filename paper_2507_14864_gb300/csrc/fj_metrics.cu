@@ -173,10 +173,3 @@ extern "C" fj_status fj_metrics(fj_graph *g, const double *s, const double *z, f
     return FJ_OK;
 }
 
-extern "C" fj_status fj_solve_batch(fj_graph *g, const double *S, int k, const fj_solve_opts *opts, double *Z_out,
-                                    fj_solve_info *info, int mem)
-{
-    (void)g; (void)S; (void)k; (void)opts; (void)Z_out; (void)info; (void)mem;
-    set_error("fj_solve_batch is not built yet");
-    return FJ_ERR_UNSUPPORTED;
-}

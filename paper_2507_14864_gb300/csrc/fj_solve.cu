@@ -103,7 +103,6 @@ __device__ __forceinline__ float resid_store<float>(double x)
 template <>
 __device__ __forceinline__ double resid_store<double>(double x) { return x; }
 
-// Initial state over new ids i (o = perm[i] the caller's id): s', zhat, r, h.
 // Initial state over new ids i (o = perm[i] the caller's id): s', zhat, r, h,
 // and the relaxation factor of node i: omega, lowered for a node with weight
 // din_i to neighbours of its own colour class so that
@@ -174,41 +173,43 @@ __global__ void k_end_sweep(Counters *c)
     c->ticket = 0;
 }
 
-// ============================================================== row-block machinery
+// ============================================================== helpers
 
-// Segmented inclusive scan of prod[0, nz) in place (segments start where
-// head[i] != 0), by 8 warps over contiguous chunks.  Afterwards the last
-// element of every row holds that row's sum.
-template <typename T>
-__device__ __forceinline__ void block_segscan(T *prod, const unsigned char *head, int nz, T *wcarry, int *whas)
+// Segmented inclusive scan of compensated pairs p[0, nz) in shared memory
+// (segments start where head[i] != 0), by 8 warps over contiguous chunks:
+// afterwards the last element of every row holds that row's sum.
+__device__ __forceinline__ void block_segscan_dd(DD *p, const unsigned char *head, int nz, DD *wcarry, int *whas)
 {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int C = (((nz + 7) >> 3) + 31) & ~31;
     const int beg = wid * C;
     const int end = min(beg + C, nz);
-    T carry = T(0);
+    DD carry{0.0, 0.0};
     int seen = 0;
     int first_head = end;
     for (int base = beg; base < end; base += 32) {
-        int i = base + lane;
-        bool valid = i < end;
-        T v = valid ? prod[i] : T(0);
+        const int i = base + lane;
+        const bool valid = i < end;
+        DD v = valid ? p[i] : DD{0.0, 0.0};
         int f = valid ? (int)head[i] : 0;
-        unsigned hb = __ballot_sync(0xffffffffu, f != 0);
+        const unsigned hb = __ballot_sync(0xffffffffu, f != 0);
         if (hb && !seen) first_head = base + __ffs(hb) - 1;
         seen |= (hb != 0u);
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            T vu = __shfl_up_sync(0xffffffffu, v, o);
-            int fu = __shfl_up_sync(0xffffffffu, f, o);
+            DD u;
+            u.hi = __shfl_up_sync(0xffffffffu, v.hi, o);
+            u.lo = __shfl_up_sync(0xffffffffu, v.lo, o);
+            const int fu = __shfl_up_sync(0xffffffffu, f, o);
             if (lane >= o) {
-                if (!f) v += vu;
+                if (!f) v = dd_merge(u, v);
                 f |= fu;
             }
         }
-        if (!f) v += carry;
-        if (valid) prod[i] = v;
-        carry = __shfl_sync(0xffffffffu, v, 31);
+        if (!f) v = dd_merge(carry, v);
+        if (valid) p[i] = v;
+        carry.hi = __shfl_sync(0xffffffffu, v.hi, 31);
+        carry.lo = __shfl_sync(0xffffffffu, v.lo, 31);
     }
     if (lane == 0) {
         wcarry[wid] = carry;
@@ -216,16 +217,16 @@ __device__ __forceinline__ void block_segscan(T *prod, const unsigned char *head
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        T cin = T(0);
+        DD cin{0.0, 0.0};
         for (int w = 0; w < 8; ++w) {
-            T out = whas[w] ? wcarry[w] : cin + wcarry[w];
+            const DD out = whas[w] ? wcarry[w] : dd_merge(cin, wcarry[w]);
             wcarry[w] = cin;  // becomes the carry-in of warp w
             cin = out;
         }
     }
     __syncthreads();
-    const T cin = wcarry[wid];
-    for (int i = beg + lane; i < first_head; i += 32) prod[i] += cin;
+    const DD cin = wcarry[wid];
+    for (int i = beg + lane; i < first_head; i += 32) p[i] = dd_merge(cin, p[i]);
 }
 
 template <typename T, bool W>
@@ -533,23 +534,28 @@ k_sweep(const Item *__restrict__ items, int64_t item0, int64_t nitems, const int
 
 // ============================================================== FP64 certificate
 
-// r64_x = s'_x - (1 + d_x) zhat_x + sum_j a_xj zhat_j  (= s' - (I + L) zhat'; a
-// long row sums a_xj (zhat_j - zhat_x) chunk by chunk instead, which cancels
-// less), per graph: max |r64|, max |r64| / s', max |zhat - c_eff|, number of
-// nodes with |r64| > eps' s'.  Stores r64 into the push residual (magnitude
-// rounded up for FP32) and clears both increment buffers: the push restarts
-// from an exact residual (a refinement pass).
+// r64_x = s'_x - (1 + d_x) zhat_x + sum_j a_xj zhat_j  (= s' - (I + L) zhat'),
+// accumulated with compensated FP64 arithmetic (Dot2), so the value is the
+// residual of the stored zhat' to about one rounding, at any degree.  Per
+// graph: max |r64|, max |r64| / s', max |zhat - c_eff|, and the number of
+// nodes with |r64| > max(eps' s', resid_floor).  Stores r64 into the push
+// residual (magnitude rounded up for FP32) and clears both increment buffers:
+// the push restarts from an exact residual (a refinement pass).  A block item
+// forms each product a_xj zhat_j with its rounding error in shared memory and
+// sums rows by a segmented scan of the pairs; a chunk of a long row is summed
+// by the whole block and the last chunk to finish completes the row.
 template <typename T, bool W>
 __global__ void __launch_bounds__(256)
 k_certify(const Item *__restrict__ items, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
           const float *__restrict__ w, const double *__restrict__ zhat, const double *__restrict__ sp,
           const double *__restrict__ deg, const int32_t *__restrict__ graph_of, double epsp, T *__restrict__ r,
           T *__restrict__ da, T *__restrict__ db, unsigned long long *gs, const int32_t *__restrict__ slot_first,
-          const int32_t *__restrict__ slot_nchunk, double *part, int32_t *cnt, int64_t n_rows)
+          const int32_t *__restrict__ slot_nchunk, double *part, int32_t *cnt, double *__restrict__ r64,
+          int64_t n_rows)
 {
-    __shared__ double prod[2 * kBlockNnz];
+    __shared__ DD prod[2 * kBlockNnz];
     __shared__ unsigned char head[2 * kBlockNnz];
-    __shared__ double wcarry[8];
+    __shared__ DD wcarry[8];
     __shared__ int whas[8];
     __shared__ double red[4][8];
     const Item it = items[blockIdx.x];
@@ -561,82 +567,91 @@ k_certify(const Item *__restrict__ items, const int64_t *__restrict__ rp, const 
     if (!FJ_IDX_OK(6, gph, 1 << 20)) return;
     const double ce = reinterpret_cast<const double *>(gs)[(int64_t)gph * kGs + 1];
     double m_abs = 0.0, m_rel = 0.0, m_z = 0.0, viol = 0.0;
-    bool any = false;
 
-    auto epilogue = [&](int64_t x, double rx) {
-        double zx = zhat[x];
+    // completes row x from acc = sum_j a_xj zhat_j (compensated)
+    auto epilogue = [&](int64_t x, DD acc) {
+        const double zx = zhat[x];
+        dd_add(acc, sp[x]);
+        dd_fma(acc, -(1.0 + deg[x]), zx);
+        const double rx = dd_value(acc);
         double ax = fabs(rx);
         if (!(ax <= 1e300)) ax = INFINITY;
         m_abs = fmax(m_abs, ax);
         m_rel = fmax(m_rel, ax / sp[x]);
         m_z = fmax(m_z, fabs(zx - ce));
-        if (ax > epsp * sp[x]) viol += 1.0;
+        if (ax > fmax(epsp * sp[x], resid_floor(deg[x], zx))) viol += 1.0;
         r[x] = resid_store<T>(rx);
+        r64[x] = rx;
         da[x] = T(0);
         db[x] = T(0);
-        any = true;
     };
 
     if (it.slot >= 0) {
-        const double zx = zhat[r0];
-        double acc = 0.0;
+        DD acc{0.0, 0.0};
         for (int64_t k = k0 + threadIdx.x; k < k1; k += 256) {
             int32_t cj = __ldg(col + k);
-            if (FJ_IDX_OK(7, cj, n_rows)) acc += arc_w<double, W>(w, k) * (zhat[cj] - zx);
+            if (FJ_IDX_OK(7, cj, n_rows)) dd_fma(acc, arc_w<double, W>(w, k), zhat[cj]);
         }
-        acc = warp_sum(acc);
+        acc = warp_dd_sum(acc);
         if (lane == 0) wcarry[wid] = acc;
         __syncthreads();
         if (threadIdx.x == 0) {
-            double t = 0.0;
-            for (int i = 0; i < 8; ++i) t += wcarry[i];
+            DD t = wcarry[0];
+            for (int i = 1; i < 8; ++i) t = dd_merge(t, wcarry[i]);
             const int slot = it.slot;
             const int first = slot_first[slot], nch = slot_nchunk[slot];
             const int ci = (int)((k0 - rp[r0]) / kChunkNnz);
-            part[first + ci] = t;
+            part[2 * (first + ci)] = t.hi;
+            part[2 * (first + ci) + 1] = t.lo;
             __threadfence();
             if (atomicAdd(&cnt[slot], 1) == nch - 1) {
                 __threadfence();
-                double s = 0.0;
-                for (int c = 0; c < nch; ++c) s += __ldcg(part + first + c);
+                DD sum{0.0, 0.0};
+                for (int c = 0; c < nch; ++c)
+                    sum = dd_merge(sum, DD{__ldcg(part + 2 * (first + c)), __ldcg(part + 2 * (first + c) + 1)});
                 cnt[slot] = 0;
-                epilogue(r0, sp[r0] - zx + s);
+                epilogue(r0, sum);
             }
         }
     } else {
         const int nzi = (int)(k1 - k0);
+        if (!FJ_IDX_OK(8, nzi, 2 * kBlockNnz + 1)) return;
         for (int i = threadIdx.x; i < nzi; i += 256) head[i] = 0;
         __syncthreads();
         for (int64_t x = r0 + threadIdx.x; x < r1; x += 256) {
-            int64_t a = rp[x];
+            const int64_t a = rp[x];
             if (rp[x + 1] > a && FJ_IDX_OK(5, a - k0, nzi)) head[a - k0] = 1;
         }
         __syncthreads();
         for (int i = threadIdx.x; i < nzi; i += 256) {
-            int64_t k = k0 + i;
-            int32_t cj = __ldg(col + k);
-            prod[i] = FJ_IDX_OK(4, cj, n_rows) ? arc_w<double, W>(w, k) * zhat[cj] : 0.0;
+            const int64_t k = k0 + i;
+            const int32_t cj = __ldg(col + k);
+            DD t{0.0, 0.0};
+            if (FJ_IDX_OK(4, cj, n_rows)) {
+                const double a = arc_w<double, W>(w, k), z = zhat[cj];
+                t.hi = __dmul_rn(a, z);
+                t.lo = fma(a, z, -t.hi);
+            }
+            prod[i] = t;
         }
         __syncthreads();
-        block_segscan<double>(prod, head, nzi, wcarry, whas);
+        block_segscan_dd(prod, head, nzi, wcarry, whas);
         __syncthreads();
         for (int64_t x = r0 + threadIdx.x; x < r1; x += 256) {
-            int64_t a = rp[x], e = rp[x + 1];
-            const double zx = zhat[x];
-            // sum_j a_xj zhat_j - d_x zhat_x
-            epilogue(x, sp[x] - zx + (e > a ? prod[e - 1 - k0] : 0.0) - deg[x] * zx);
+            const int64_t a = rp[x], e = rp[x + 1];
+            epilogue(x, e > a ? prod[e - 1 - k0] : DD{0.0, 0.0});
         }
     }
+    (void)k1;
     m_abs = warp_max(m_abs);
     m_rel = warp_max(m_rel);
     m_z = warp_max(m_z);
     viol = warp_sum(viol);
-    unsigned anyw = __ballot_sync(0xffffffffu, any);
     if (lane == 0) {
         red[0][wid] = m_abs;
         red[1][wid] = m_rel;
         red[2][wid] = m_z;
-        red[3][wid] = anyw ? viol : 0.0;
+        red[3][wid] = viol;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -660,6 +675,71 @@ __global__ void k_cert_reset(int ng, unsigned long long *gs)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ng; i += gridDim.x * blockDim.x)
         for (int j = 2; j < kGs; ++j) gs[(int64_t)i * kGs + j] = 0ULL;
+}
+
+// ============================================================== FP64 frontier push
+
+// Entries e = v k + j (node v, vector j; k = 1 for one vector) whose FP64
+// residual, as left by the certificate and the frontier pushes since, is
+// above the certificate's threshold.
+struct CleanPred {
+    const double *r64, *sp, *zhat, *deg;
+    double epsp;
+    int k;
+    __device__ bool operator()(int64_t e) const
+    {
+        const int64_t v = k == 1 ? e : e / k;
+        return fabs(r64[e]) > fmax(epsp * sp[e], resid_floor(deg[v], zhat[e]));
+    }
+};
+
+// One round of the scatter-form push (Alg. 1, omega = 1) over the frontier
+// list, one warp per entry: zhat_e moves by r_e / (1 + d_v), and the change
+// zhat actually took (exact, a difference of neighbouring doubles) is taken out
+// of r_e and added, times a_uv, to r_u j for every in-neighbour u of v.
+// Pushes of one round run concurrently, so every residual update is an
+// atomic addition; an entry's own residual is read once and what was read is
+// what is moved (asynchronous relaxation of the diagonally dominant I + L).
+template <bool W>
+__global__ void __launch_bounds__(256)
+k_frontier_push(const int32_t *__restrict__ list, const long long *__restrict__ count, int k,
+                const int64_t *__restrict__ tp, const int32_t *__restrict__ tc, const float *__restrict__ tw,
+                const double *__restrict__ deg, double *r64, double *__restrict__ zhat, Counters *ctr,
+                int64_t n_rows)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const long long cnt = *count;
+    const int64_t n_ent = n_rows * k;
+    unsigned long long my_edges = 0;
+    for (int64_t i = warp; i < cnt; i += nwarps) {
+        const int64_t e = list[i];
+        if (!FJ_IDX_OK(20, e, n_ent)) continue;
+        const int64_t v = e / k;
+        const int j = (int)(e - v * k);
+        double dz = 0.0;
+        if (lane == 0) {
+            const double rv = __ldcg(r64 + e);
+            const double dpl = 1.0 + deg[v];
+            const double z0 = zhat[e];
+            const double z1 = __dadd_rn(z0, rv / dpl);
+            zhat[e] = z1;
+            dz = __dsub_rn(z1, z0);
+            atomicAdd(r64 + e, -__dmul_rn(dpl, dz));
+        }
+        dz = __shfl_sync(0xffffffffu, dz, 0);
+        const int64_t a0 = tp[v], a1 = tp[v + 1];
+        for (int64_t kk = a0 + lane; kk < a1; kk += 32) {
+            const int32_t u = tc[kk];
+            if (!FJ_IDX_OK(21, u, n_rows)) continue;
+            const double a = W ? (double)tw[kk] : 1.0;
+            atomicAdd(r64 + (int64_t)u * k + j, __dmul_rn(a, dz));
+        }
+        if (lane == 0) my_edges += (unsigned long long)(a1 - a0);
+    }
+    my_edges = warp_sum(my_edges);
+    if (lane == 0 && my_edges) atomicAdd(&ctr->edges, my_edges);
 }
 
 // ============================================================== frontier
@@ -702,7 +782,7 @@ static fj_status ws_grow(fj_graph *g, int64_t entries, int ngraphs)
             *p = nullptr;
             FJ_CUDA(cudaMalloc(p, sizeof(double) * (size_t)entries));
         }
-        double **dbufs[] = {&ws.zhat, &ws.sp, &ws.sin, &ws.zout};
+        double **dbufs[] = {&ws.zhat, &ws.sp, &ws.sin, &ws.zout, &ws.r64};
         for (double **p : dbufs) {
             dev_free(*p);
             *p = nullptr;
@@ -893,7 +973,7 @@ static fj_status build_items(fj_graph *g, const DevCSR &c, const std::vector<int
     FJ_CUDA(cudaMalloc(&ip.slot_first, sizeof(int32_t) * std::max<size_t>(sfirst.size(), 1)));
     FJ_CUDA(cudaMalloc(&ip.slot_nchunk, sizeof(int32_t) * std::max<size_t>(snch.size(), 1)));
     FJ_CUDA(cudaMalloc(&ip.cnt, sizeof(int32_t) * std::max<size_t>(sfirst.size(), 1)));
-    FJ_CUDA(cudaMalloc(&ip.part, sizeof(double) * std::max<int64_t>(nparts, 1)));
+    FJ_CUDA(cudaMalloc(&ip.part, 2 * sizeof(double) * std::max<int64_t>(nparts, 1)));
     FJ_CUDA(cudaMemcpyAsync(ip.items, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice, st));
     if (!sfirst.empty()) {
         FJ_CUDA(cudaMemcpyAsync(ip.slot_first, sfirst.data(), sizeof(int32_t) * sfirst.size(), cudaMemcpyHostToDevice,
@@ -1053,11 +1133,11 @@ static fj_status launch_certify(fj_graph *g, const Plan &p, double epsp, cudaStr
     if (c.w)
         k_certify<T, true><<<grid, 256, 0, st>>>(ip.items, c.row_ptr, c.col, c.w, ws.zhat, ws.sp, c.deg64, c.graph_of,
                                                  epsp, r, da, db, gs, ip.slot_first, ip.slot_nchunk, ip.part, ip.cnt,
-                                                 c.n);
+                                                 ws.r64, c.n);
     else
         k_certify<T, false><<<grid, 256, 0, st>>>(ip.items, c.row_ptr, c.col, c.w, ws.zhat, ws.sp, c.deg64,
                                                   c.graph_of, epsp, r, da, db, gs, ip.slot_first, ip.slot_nchunk,
-                                                  ip.part, ip.cnt, c.n);
+                                                  ip.part, ip.cnt, ws.r64, c.n);
     FJ_CUDA(cudaGetLastError());
     return FJ_OK;
 }
@@ -1071,6 +1151,82 @@ static fj_status check_index_record()
         return FJ_ERR_INVALID_ARG;
     }
     return FJ_OK;
+}
+
+// In-neighbour lists of the solve's row order: the CSR itself for an
+// undirected graph (symmetric), the transposed CSR for a directed one
+// (renumbered into the colour order for the multicolour schedule).
+struct InLists {
+    const int64_t *tp = nullptr;
+    const int32_t *tc = nullptr;
+    const float *tw = nullptr;
+};
+
+static fj_status in_lists(fj_graph *g, const Plan &p, cudaStream_t st, InLists &out)
+{
+    if (!g->directed) {
+        out.tp = p.c->row_ptr;
+        out.tc = p.c->col;
+        out.tw = p.c->w;
+    } else if (p.mc) {
+        FJ_CHECK(ensure_ptranspose(g, st));
+        out.tp = g->colr.tptr;
+        out.tc = g->colr.tcol;
+        out.tw = g->colr.tw;
+    } else {
+        out.tp = g->tptr;
+        out.tc = g->tcol;
+        out.tw = g->tw;
+    }
+    return FJ_OK;
+}
+
+// Largest frontier the FP64 push takes on (entries); beyond it another pass
+// of sweeps is cheaper.
+static int64_t frontier_limit(int64_t entries) { return std::max<int64_t>(1024, entries / 64); }
+constexpr int kMaxCleanups = 4;     // frontier-push episodes per solve
+constexpr int kCleanupRounds = 64;  // rounds per episode
+
+// FP64 frontier push rounds on the entries above threshold, until the
+// frontier is empty (*cleared), grows past frontier_limit, or max_rounds.
+static fj_status frontier_cleanup(fj_graph *g, const Plan &p, int k, double *r64, double *zhat, const double *sp,
+                                  double epsp, int32_t *list, int max_rounds, cudaStream_t st, Run &run,
+                                  int64_t *rounds, int64_t *pushes, bool *cleared)
+{
+    Workspace &ws = g->ws;
+    const DevCSR &c = *p.c;
+    const int64_t ne = c.n * k;
+    const int64_t limit = frontier_limit(ne);
+    InLists L;
+    FJ_CHECK(in_lists(g, p, st, L));
+    FJ_CHECK(ws_status(ws, scan_tiles(ne, 256 * 8)));
+    *cleared = false;
+    for (int it = 0; it < max_rounds; ++it) {
+        FJ_CUDA(compact<256, 8>(ne, CleanPred{r64, sp, zhat, c.deg64, epsp, k}, list, ws.count, ws.status,
+                                ws.tile_ctr, g->err, st));
+        long long cnt = 0;
+        FJ_CUDA(cudaMemcpyAsync(&cnt, ws.count, sizeof(long long), cudaMemcpyDeviceToHost, st));
+        FJ_CUDA(cudaStreamSynchronize(st));
+        ++run.launches;
+        if (cnt == 0) {
+            *cleared = true;
+            break;
+        }
+        if (cnt > limit) break;
+        const unsigned grid = grid_for(cnt * 32, 256, 152 * 16);
+        if (L.tw)
+            k_frontier_push<true><<<grid, 256, 0, st>>>(list, ws.count, k, L.tp, L.tc, L.tw, c.deg64, r64, zhat,
+                                                        ws.ctr, c.n);
+        else
+            k_frontier_push<false><<<grid, 256, 0, st>>>(list, ws.count, k, L.tp, L.tc, L.tw, c.deg64, r64, zhat,
+                                                         ws.ctr, c.n);
+        FJ_CUDA(cudaGetLastError());
+        ++run.launches;
+        ++*rounds;
+        *pushes += cnt;
+    }
+    FJ_CHECK(check_index_record());
+    return read_dev_error(g, st);
 }
 
 template <typename T>
@@ -1122,7 +1278,8 @@ static fj_status solve_t(fj_graph *g, const double *s, const double *z0, const f
     cudaGraphExec_t batch = nullptr;
     int batch_launches = 0;
     if (!run.profile) FJ_CHECK(sweep_graph<T>(g, p, check, &batch, &batch_launches));
-    int refine = 0;
+    int refine = 0, cleanups = 0;
+    int64_t f_rounds = 0, f_pushes = 0;
     fj_status result = FJ_OK;
     for (;;) {
         k_pass_reset<<<1, 1, 0, st>>>(ws.ctr, o->max_sweeps);
@@ -1148,12 +1305,27 @@ static fj_status solve_t(fj_graph *g, const double *s, const double *z0, const f
             set_error("residual became non-finite (omega %.3f)", o->omega);
             break;
         }
-        FJ_CHECK(launch_certify<T>(g, p, epsp, st, run));
-        FJ_CUDA(cudaMemcpyAsync(ws.gstat_host, ws.gstat, sizeof(double) * kGs * ng, cudaMemcpyDeviceToHost, st));
-        FJ_CUDA(cudaStreamSynchronize(st));
-        FJ_CHECK(check_index_record());
+        auto certify_count = [&](double &viol) -> fj_status {
+            FJ_CHECK(launch_certify<T>(g, p, epsp, st, run));
+            FJ_CUDA(cudaMemcpyAsync(ws.gstat_host, ws.gstat, sizeof(double) * kGs * ng, cudaMemcpyDeviceToHost, st));
+            FJ_CUDA(cudaStreamSynchronize(st));
+            FJ_CHECK(check_index_record());
+            viol = 0.0;
+            for (int i = 0; i < ng; ++i) viol += ws.gstat_host[i * kGs + 5];
+            return FJ_OK;
+        };
         double viol = 0.0;
-        for (int i = 0; i < ng; ++i) viol += ws.gstat_host[i * kGs + 5];
+        FJ_CHECK(certify_count(viol));
+        // few nodes left above threshold: FP64 frontier pushes on them, then
+        // the exact certificate again (it also re-syncs the push residual)
+        while (viol > 0.0 && viol <= (double)frontier_limit(n) && cleanups < kMaxCleanups) {
+            bool cleared = false;
+            ++cleanups;
+            FJ_CHECK(frontier_cleanup(g, p, 1, ws.r64, ws.zhat, ws.sp, epsp, ws.list, kCleanupRounds, st, run,
+                                      &f_rounds, &f_pushes, &cleared));
+            FJ_CHECK(certify_count(viol));
+            if (!cleared) break;
+        }
         if (viol == 0.0) break;
         if (done == 2) {
             result = FJ_ERR_NOT_CONVERGED;
@@ -1201,6 +1373,8 @@ static fj_status solve_t(fj_graph *g, const double *s, const double *z0, const f
             const double tb = (double)sizeof(T);
             const double per_sweep = (double)c.nnz * (4.0 + (c.w ? 4.0 : 0.0) + tb) + (double)c.n * (8.0 + 5.0 * tb);
             f.push_bytes = (double)ws.ctr_host->sweeps * per_sweep + (double)ws.ctr_host->pushes * 20.0;
+            f.frontier_rounds = f_rounds;
+            f.frontier_pushes = f_pushes;
         }
     }
     return result;
@@ -1303,3 +1477,626 @@ fj_status fj_residual(fj_graph *g, const double *s, const double *z, double c_ef
 }
 
 }  // extern "C"
+
+// ============================================================== multi-RHS batch
+
+namespace fj {
+
+// Per right-hand side: minimum of s (column j of the node-major [n][k] S).
+__global__ void k_min_s_batch(int64_t n, int k, const double *__restrict__ S, unsigned long long *gs, int *err)
+{
+    __shared__ unsigned long long sm[8];
+    const int j = blockIdx.y;
+    unsigned long long best = ~0ULL;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const double x = S[v * k + j];
+        if (!isfinite(x)) dev_error(err, DEV_BAD_OPINION);
+        const unsigned long long key = order_key(x);
+        best = key < best ? key : best;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long u = __shfl_xor_sync(0xffffffffu, best, o);
+        best = u < best ? u : best;
+    }
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < 8; ++i) best = sm[i] < best ? sm[i] : best;
+        atomicMin(&gs[(int64_t)j * kGs], best);
+    }
+}
+
+// Node-major initial state: s', zhat, r, h per (node, right-hand side); omega per node.
+template <typename T>
+__global__ void k_init_batch(int64_t n, int k, const double *__restrict__ S, const double *__restrict__ Z0,
+                             const int32_t *__restrict__ perm, const unsigned long long *__restrict__ gs,
+                             double epsp, double omega, const double *__restrict__ deg,
+                             const double *__restrict__ din, double *__restrict__ sp, double *__restrict__ zhat,
+                             T *__restrict__ r, T *__restrict__ h, T *__restrict__ da, T *__restrict__ db,
+                             T *__restrict__ om)
+{
+    const double *gsd = reinterpret_cast<const double *>(gs);
+    const int64_t total = n * k;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = idx / k;
+        const int j = (int)(idx - i * k);
+        const int64_t o = perm ? perm[i] : i;
+        const double ce = gsd[(int64_t)j * kGs + 1];
+        const double spv = S[o * k + j] + ce;
+        sp[idx] = spv;
+        zhat[idx] = Z0 ? Z0[o * k + j] + ce : 0.0;
+        r[idx] = (T)spv;
+        h[idx] = threshold_of<T>(epsp * spv);
+        da[idx] = T(0);
+        db[idx] = T(0);
+        if (j == 0) {
+            double oi = omega;
+            if (din && din[i] > 0.0) oi = fmin(omega, 0.98 * 2.0 * (1.0 + deg[i]) / (1.0 + deg[i] + din[i]));
+            om[i] = (T)oi;
+        }
+    }
+}
+
+template <typename T>
+__global__ void k_unshift_batch(int64_t n, int k, const double *__restrict__ zhat, const int32_t *__restrict__ perm,
+                                const unsigned long long *__restrict__ gs, double *__restrict__ Z)
+{
+    const double *gsd = reinterpret_cast<const double *>(gs);
+    const int64_t total = n * k;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = idx / k;
+        const int j = (int)(idx - i * k);
+        const int64_t o = perm ? perm[i] : i;
+        Z[o * k + j] = zhat[idx] - gsd[(int64_t)j * kGs + 1];
+    }
+}
+
+// Walk of one warp tile for k right-hand sides.  Lane j owns vectors j and
+// j + 32.  Columns and weights are read 32 nonzeros at a time (one coalesced
+// load per lane) and broadcast by shuffles; D gathers of the neighbours'
+// k-vectors (contiguous in the node-major layout) are issued before any is
+// consumed.  Rows are finished as the walk passes their ends, so short rows
+// share load batches.  begin(x) is called when row x becomes current (to
+// start its own loads early); src(c) gives the k-vector read for column c;
+// add(acc, a, v) accumulates a * v; apply(x, acc1, acc2) receives row x's
+// sums.  A chunk of a long row (chunk = true) sums [k0, k1) of row r0 and
+// calls apply once.
+template <typename Acc, typename V, bool W, int D, typename Begin, typename Src, typename Add, typename Apply>
+__device__ __forceinline__ void warp_tile_k(int64_t r0, int64_t r1, int64_t k0, int64_t k1, bool chunk,
+                                            const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                            const float *__restrict__ w, Begin begin, Src src, Add add, Apply apply,
+                                            int lane, bool has1, bool has2, int64_t n_rows)
+{
+    constexpr unsigned FULL = 0xffffffffu;
+    static_assert(32 % D == 0, "gather depth divides the load batch");
+    // row ends of the tile (at most kWarpRows = 64 rows): lane i holds the ends of rows r0+i and r0+32+i
+    int64_t e_lo = k1, e_hi = k1;
+    if (!chunk) {
+        if (r0 + lane < r1) e_lo = rp[r0 + lane + 1];
+        if (r0 + 32 + lane < r1) e_hi = rp[r0 + 33 + lane];
+    } else {
+        r1 = r0 + 1;
+    }
+    int64_t x = r0;
+    auto row_end = [&](int64_t xx) -> int64_t {
+        const int i = (int)(xx - r0);
+        return __shfl_sync(FULL, i < 32 ? e_lo : e_hi, i & 31);
+    };
+    int64_t xe = x < r1 ? row_end(x) : k1;
+    if (x < r1) begin(x);
+    Acc a1{}, a2{};
+    auto flush_until = [&](int64_t pos) {
+        while (x < r1 && xe <= pos) {
+            apply(x, a1, a2);
+            a1 = Acc{};
+            a2 = Acc{};
+            ++x;
+            if (x < r1) {
+                xe = row_end(x);
+                begin(x);
+            }
+        }
+    };
+    for (int64_t base = k0; base < k1; base += 32) {
+        const int64_t kk = base + lane;
+        int32_t cl = 0;
+        float al = 0.f;
+        if (kk < k1) {
+            cl = __ldg(col + kk);
+            al = W ? __ldg(w + kk) : 1.f;
+            if (!FJ_IDX_OK(15, cl, n_rows)) {
+                cl = 0;
+                al = 0.f;
+            }
+        }
+        const int m = (int)(k1 - base < 32 ? k1 - base : 32);
+        for (int t = 0; t < m; t += D) {
+            V v1[D], v2[D];
+            float aa[D];
+#pragma unroll
+            for (int u = 0; u < D; ++u) {
+                const int32_t c = __shfl_sync(FULL, cl, (t + u) & 31);
+                aa[u] = __shfl_sync(FULL, al, (t + u) & 31);
+                const V *p = src(c);
+                const bool in = t + u < m;
+                v1[u] = (in && has1) ? __ldg(p + lane) : V(0);
+                v2[u] = (in && has2) ? __ldg(p + lane + 32) : V(0);
+            }
+#pragma unroll
+            for (int u = 0; u < D; ++u) {
+                if (t + u < m) {
+                    flush_until(base + t + u);
+                    add(a1, aa[u], v1[u]);
+                    add(a2, aa[u], v2[u]);
+                }
+            }
+        }
+    }
+    flush_until(k1);
+}
+
+// One colour class of a multi-RHS sweep: the update of k_sweep applied to k
+// opinion vectors at once, one warp per warp tile.  A long row's chunks keep
+// k partial sums each and the last chunk to finish applies the update.
+template <typename T, bool W>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
+k_sweep_batch(const Item *__restrict__ items, int64_t item0, int64_t nitems, const int64_t *__restrict__ rp,
+              const int32_t *__restrict__ col, const float *__restrict__ w, int k, T *dcur,
+              const T *__restrict__ dprev, T *__restrict__ r, const T *__restrict__ h, const T *__restrict__ inv,
+              double *__restrict__ zhat, const T *__restrict__ om, const int32_t *__restrict__ indeg,
+              const int32_t *__restrict__ slot_first, const int32_t *__restrict__ slot_nchunk, double *partk,
+              int32_t *cnt, Counters *ctr, int64_t n_rows)
+{
+    __shared__ unsigned long long red[2][8];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    if (*reinterpret_cast<volatile int *>(&ctr->done)) return;
+    const int64_t nwarps = (int64_t)gridDim.x * 8;
+    const bool has1 = lane < k, has2 = lane + 32 < k;
+    unsigned long long my_push = 0, my_edges = 0;
+    bool bad = false;
+
+    // row state loaded when the row becomes current, used when it completes
+    T pr[2] = {T(0), T(0)}, ph[2] = {T(0), T(0)}, pom = T(0), pinv = T(0);
+    int32_t pdeg = 0;
+    auto begin = [&](int64_t x) {
+        const int64_t q = x * k + lane;
+        if (has1) {
+            pr[0] = r[q];
+            ph[0] = h[q];
+        }
+        if (has2) {
+            pr[1] = r[q + 32];
+            ph[1] = h[q + 32];
+        }
+        pom = om[x];
+        pinv = inv[x];
+        pdeg = indeg[x];
+    };
+    auto upd = [&](int64_t x, int hh, T acc) {
+        const int64_t q = x * k + lane + 32 * hh;
+        T rx = pr[hh] + acc;
+        T dx = T(0);
+        if (abs_t(rx) > ph[hh]) {
+            dx = pom * rx * pinv;
+            zhat[q] += (double)dx;
+            rx = (T(1) - pom) * rx;
+            my_push += 1;
+            my_edges += (unsigned long long)pdeg;
+        }
+        if (!isfinite(rx)) bad = true;
+        r[q] = rx;
+        dcur[q] = dx;
+    };
+    auto apply_row = [&](int64_t x, T s1, T s2) {
+        if (has1) upd(x, 0, s1);
+        if (has2) upd(x, 1, s2);
+    };
+    auto no_begin = [](int64_t) {};
+    constexpr int D = 8;
+
+    for (int64_t ii = item0 + (int64_t)blockIdx.x * 8 + wl; ii < item0 + nitems; ii += nwarps) {
+        const Item it = items[ii];
+        const int64_t r0 = it.r0, r1 = it.r1;
+        if (!FJ_IDX_OK(11, r0, n_rows) || !FJ_IDX_OK(12, r1, n_rows + 1) ||
+            (it.slot < 0 && !FJ_IDX_OK(13, r1 - r0, kWarpRows + 1)))
+            continue;
+        const int32_t lo = it.lo;
+        auto src = [&](int32_t c) -> const T * { return (c < lo ? (const T *)dcur : dprev) + (int64_t)c * k; };
+        auto add = [](T &acc, float a, T v) { acc += (T)a * v; };
+        if (it.slot < 0) {
+            warp_tile_k<T, T, W, D>(r0, r1, it.k0, it.k1, false, rp, col, w, begin, src, add, apply_row, lane,
+                                    has1, has2, n_rows);
+        } else {
+            const int slot = it.slot;
+            const int first = slot_first[slot], nch = slot_nchunk[slot];
+            const int ci = (int)((it.k0 - rp[r0]) / kWarpChunk);
+            auto store_part = [&](int64_t, T s1, T s2) {
+                if (has1) partk[(int64_t)(first + ci) * k + lane] = (double)s1;
+                if (has2) partk[(int64_t)(first + ci) * k + lane + 32] = (double)s2;
+            };
+            warp_tile_k<T, T, W, D>(r0, r1, it.k0, it.k1, true, rp, col, w, no_begin, src, add, store_part, lane,
+                                    has1, has2, n_rows);
+            __threadfence();
+            __syncwarp();
+            int last = 0;
+            if (lane == 0) last = atomicAdd(&cnt[slot], 1) == nch - 1;
+            last = __shfl_sync(0xffffffffu, last, 0);
+            if (last) {
+                __threadfence();
+                double a1 = 0.0, a2 = 0.0;
+                for (int c = 0; c < nch; ++c) {
+                    if (has1) a1 += __ldcg(partk + (int64_t)(first + c) * k + lane);
+                    if (has2) a2 += __ldcg(partk + (int64_t)(first + c) * k + lane + 32);
+                }
+                if (lane == 0) cnt[slot] = 0;
+                begin(r0);
+                apply_row(r0, (T)a1, (T)a2);
+            }
+        }
+    }
+    my_push = warp_sum(my_push);
+    my_edges = warp_sum(my_edges);
+    const unsigned anybad = __ballot_sync(0xffffffffu, bad);
+    if (lane == 0) {
+        red[0][wl] = my_push;
+        red[1][wl] = my_edges;
+        if (anybad) ctr->nonfinite = 1.0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long pp = 0, ee = 0;
+        for (int i = 0; i < 8; ++i) {
+            pp += red[0][i];
+            ee += red[1][i];
+        }
+        if (pp) {
+            atomicAdd(&ctr->pushes, pp);
+            atomicAdd(&ctr->sweep_pushes, pp);
+            atomicAdd(&ctr->edges, ee);
+        }
+    }
+}
+
+// FP64 certificate of every (node, right-hand side), as k_certify: the
+// residual of each vector accumulated with compensated arithmetic (Dot2).
+// Per-vector statistics are reduced per block in shared memory (maxima of
+// non-negative doubles compare as integers) and added with one atomic per
+// vector and field.
+template <typename T, bool W>
+__global__ void __launch_bounds__(256)
+k_certify_batch(const Item *__restrict__ items, int64_t nitems, const int64_t *__restrict__ rp,
+                const int32_t *__restrict__ col, const float *__restrict__ w, int k, const double *__restrict__ zhat,
+                const double *__restrict__ sp, const double *__restrict__ deg, double epsp, T *__restrict__ r,
+                T *__restrict__ da, T *__restrict__ db, unsigned long long *gs, const int32_t *__restrict__ slot_first,
+                const int32_t *__restrict__ slot_nchunk, double *partk, int32_t *cnt, double *__restrict__ r64,
+                int64_t n_rows)
+{
+    __shared__ unsigned long long sred[4][64];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < 4 * 64; i += 256) (&sred[0][0])[i] = 0ULL;
+    __syncthreads();
+    const int64_t nwarps = (int64_t)gridDim.x * 8;
+    const bool has1 = lane < k, has2 = lane + 32 < k;
+    double m_abs[2] = {0, 0}, m_rel[2] = {0, 0}, m_z[2] = {0, 0}, viol[2] = {0, 0};
+    const double *gsd = reinterpret_cast<const double *>(gs);
+
+    // row x, vector lane + 32 hh, from acc = sum_c a_xc zhat_c
+    auto finish = [&](int64_t x, int hh, DD acc) {
+        const int j = lane + 32 * hh;
+        const int64_t q = x * k + j;
+        const double zx = zhat[q], spx = sp[q];
+        dd_add(acc, spx);
+        dd_fma(acc, -(1.0 + deg[x]), zx);
+        const double rx = dd_value(acc);
+        const double ce = gsd[(int64_t)j * kGs + 1];
+        const double ax = fabs(rx) <= 1e300 ? fabs(rx) : INFINITY;
+        m_abs[hh] = fmax(m_abs[hh], ax);
+        m_rel[hh] = fmax(m_rel[hh], ax / spx);
+        m_z[hh] = fmax(m_z[hh], fabs(zx - ce));
+        if (ax > fmax(epsp * spx, resid_floor(deg[x], zx))) viol[hh] += 1.0;
+        r[q] = resid_store<T>(rx);
+        r64[q] = rx;
+        da[q] = T(0);
+        db[q] = T(0);
+    };
+    auto src = [&](int32_t c) -> const double * { return zhat + (int64_t)c * k; };
+    auto add = [](DD &acc, float a, double v) { dd_fma(acc, (double)a, v); };
+    auto no_begin = [](int64_t) {};
+    auto short_row = [&](int64_t x, DD s1, DD s2) {
+        if (has1) finish(x, 0, s1);
+        if (has2) finish(x, 1, s2);
+    };
+
+    for (int64_t ii = (int64_t)blockIdx.x * 8 + wl; ii < nitems; ii += nwarps) {
+        const Item it = items[ii];
+        const int64_t r0 = it.r0, r1 = it.r1;
+        if (!FJ_IDX_OK(1, r0, n_rows) || !FJ_IDX_OK(2, r1, n_rows + 1) ||
+            (it.slot < 0 && !FJ_IDX_OK(13, r1 - r0, kWarpRows + 1)))
+            continue;
+        if (it.slot < 0) {
+            warp_tile_k<DD, double, W, 8>(r0, r1, it.k0, it.k1, false, rp, col, w, no_begin, src, add, short_row,
+                                          lane, has1, has2, n_rows);
+        } else {
+            const int slot = it.slot;
+            const int first = slot_first[slot], nch = slot_nchunk[slot];
+            const int ci = (int)((it.k0 - rp[r0]) / kWarpChunk);
+            double *pc = partk + 2 * ((int64_t)(first + ci) * k + lane);
+            auto store_part = [&](int64_t, DD s1, DD s2) {
+                if (has1) {
+                    pc[0] = s1.hi;
+                    pc[1] = s1.lo;
+                }
+                if (has2) {
+                    pc[64] = s2.hi;
+                    pc[65] = s2.lo;
+                }
+            };
+            warp_tile_k<DD, double, W, 8>(r0, r1, it.k0, it.k1, true, rp, col, w, no_begin, src, add, store_part,
+                                          lane, has1, has2, n_rows);
+            __threadfence();
+            __syncwarp();
+            int last = 0;
+            if (lane == 0) last = atomicAdd(&cnt[slot], 1) == nch - 1;
+            last = __shfl_sync(0xffffffffu, last, 0);
+            if (last) {
+                __threadfence();
+                DD a1{0.0, 0.0}, a2{0.0, 0.0};
+                for (int c = 0; c < nch; ++c) {
+                    const double *q = partk + 2 * ((int64_t)(first + c) * k + lane);
+                    if (has1) a1 = dd_merge(a1, DD{__ldcg(q), __ldcg(q + 1)});
+                    if (has2) a2 = dd_merge(a2, DD{__ldcg(q + 64), __ldcg(q + 65)});
+                }
+                if (lane == 0) cnt[slot] = 0;
+                if (has1) finish(r0, 0, a1);
+                if (has2) finish(r0, 1, a2);
+            }
+        }
+    }
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+        if (!(hh == 0 ? has1 : has2)) continue;
+        const int j = lane + 32 * hh;
+        atomicMax(&sred[0][j], (unsigned long long)__double_as_longlong(m_abs[hh]));
+        atomicMax(&sred[1][j], (unsigned long long)__double_as_longlong(m_rel[hh]));
+        atomicMax(&sred[2][j], (unsigned long long)__double_as_longlong(m_z[hh]));
+        atomicAdd(&sred[3][j], (unsigned long long)viol[hh]);
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < k; j += 256) {
+        unsigned long long *gj = gs + (int64_t)j * kGs;
+        atomic_max_nonneg(reinterpret_cast<double *>(gj + 2), __longlong_as_double((long long)sred[0][j]));
+        atomic_max_nonneg(reinterpret_cast<double *>(gj + 3), __longlong_as_double((long long)sred[1][j]));
+        atomic_max_nonneg(reinterpret_cast<double *>(gj + 4), __longlong_as_double((long long)sred[2][j]));
+        if (sred[3][j]) atomicAdd(reinterpret_cast<double *>(gj + 5), (double)sred[3][j]);
+    }
+}
+
+static fj_status bws_grow(fj_graph *g, int k, int64_t nparts)
+{
+    BatchWorkspace &b = g->bws;
+    const int64_t need = g->csr.n * k;
+    if (need > b.cap) {
+        void **vb[] = {&b.r, &b.h, &b.da, &b.db};
+        for (void **p : vb) {
+            dev_free(*p);
+            *p = nullptr;
+            FJ_CUDA(cudaMalloc(p, sizeof(double) * (size_t)need));
+        }
+        double **db_[] = {&b.zhat, &b.sp, &b.sin, &b.zout, &b.r64};
+        for (double **p : db_) {
+            dev_free(*p);
+            *p = nullptr;
+            FJ_CUDA(cudaMalloc(p, sizeof(double) * (size_t)need));
+        }
+        dev_free(b.list);
+        b.list = nullptr;
+        FJ_CUDA(cudaMalloc(&b.list, sizeof(int32_t) * (size_t)need));
+        b.cap = need;
+    }
+    if (!b.om) FJ_CUDA(cudaMalloc(&b.om, sizeof(double) * (size_t)g->csr.n));
+    if (k > b.cap_k) {
+        dev_free(b.gstat);
+        if (b.gstat_host) cudaFreeHost(b.gstat_host);
+        FJ_CUDA(cudaMalloc(&b.gstat, sizeof(double) * kGs * k));
+        FJ_CUDA(cudaMallocHost(&b.gstat_host, sizeof(double) * kGs * k));
+        b.cap_k = k;
+    }
+    const int64_t np = 2 * std::max<int64_t>(nparts, 1) * k;
+    if (np > b.cap_partk) {
+        dev_free(b.partk);
+        FJ_CUDA(cudaMalloc(&b.partk, sizeof(double) * (size_t)np));
+        b.cap_partk = np;
+    }
+    return FJ_OK;
+}
+
+template <typename T>
+static fj_status solve_batch_t(fj_graph *g, const double *S, const double *Z0, int k, const fj_solve_opts *o,
+                               double *Z, fj_solve_info *info, int mem)
+{
+    cudaStream_t st = (cudaStream_t)o->stream;
+    const int64_t n = g->csr.n;
+    Workspace &ws = g->ws;
+    if (!ws.ctr) {
+        FJ_CUDA(cudaMalloc(&ws.ctr, sizeof(Counters)));
+        FJ_CUDA(cudaMallocHost(&ws.ctr_host, sizeof(Counters)));
+    }
+    Plan p;
+    FJ_CHECK(make_plan(g, o, st, p));
+    const DevCSR &c = *p.c;
+    const ItemPlan &wp = *p.wip;
+    FJ_CHECK(bws_grow(g, k, wp.nparts));
+    BatchWorkspace &b = g->bws;
+    const double epsp = o->sigma * o->eps / (o->c + o->sigma);
+    const double *Sd = S, *Z0d = Z0;
+    if (mem == FJ_MEM_HOST) {
+        FJ_CUDA(cudaMemcpyAsync(b.sin, S, sizeof(double) * n * k, cudaMemcpyHostToDevice, st));
+        Sd = b.sin;
+        if (Z0) {
+            FJ_CUDA(cudaMemcpyAsync(b.zout, Z0, sizeof(double) * n * k, cudaMemcpyHostToDevice, st));
+            Z0d = b.zout;
+        }
+    }
+    unsigned long long *gs = reinterpret_cast<unsigned long long *>(b.gstat);
+    k_gstat_reset<<<1, 256, 0, st>>>(k, gs);
+    k_min_s_batch<<<dim3(grid_for(n, 256, 64), k), 256, 0, st>>>(n, k, Sd, gs, g->err);
+    k_shift<<<1, 64, 0, st>>>(k, gs, o->c);
+    T *r = reinterpret_cast<T *>(b.r), *h = reinterpret_cast<T *>(b.h);
+    T *da = reinterpret_cast<T *>(b.da), *db = reinterpret_cast<T *>(b.db);
+    T *om = reinterpret_cast<T *>(b.om);
+    const double *din = p.mc ? g->colr.din_p : nullptr;
+    k_init_batch<T><<<grid_for(n * k, 256, 152 * 16), 256, 0, st>>>(n, k, Sd, Z0d, p.perm, gs, epsp, o->omega,
+                                                                    c.deg64, din, b.sp, b.zhat, r, h, da, db, om);
+    FJ_CUDA(cudaGetLastError());
+    FJ_CUDA(cudaMemsetAsync(ws.ctr, 0, sizeof(Counters), st));
+    FJ_CHECK(read_dev_error(g, st));
+    const T *inv;
+    if constexpr (sizeof(T) == 4) inv = reinterpret_cast<const T *>(c.inv32);
+    else inv = reinterpret_cast<const T *>(c.inv64);
+    const unsigned cgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(wp.nitems, 8), 152 * 8));
+    auto certify = [&]() -> fj_status {
+        k_cert_reset<<<1, 64, 0, st>>>(k, gs);
+        if (c.w)
+            k_certify_batch<T, true><<<cgrid, 256, 0, st>>>(wp.items, wp.nitems, c.row_ptr, c.col, c.w, k, b.zhat,
+                                                            b.sp, c.deg64, epsp, r, da, db, gs, wp.slot_first,
+                                                            wp.slot_nchunk, b.partk, wp.cnt, b.r64, c.n);
+        else
+            k_certify_batch<T, false><<<cgrid, 256, 0, st>>>(wp.items, wp.nitems, c.row_ptr, c.col, c.w, k, b.zhat,
+                                                             b.sp, c.deg64, epsp, r, da, db, gs, wp.slot_first,
+                                                             wp.slot_nchunk, b.partk, wp.cnt, b.r64, c.n);
+        FJ_CUDA(cudaGetLastError());
+        return FJ_OK;
+    };
+    if (Z0) FJ_CHECK(certify());
+    Run run;
+    run.profile = o->profile != 0;
+    run.launches = 6;
+    int64_t sweep = 0;
+    const int check = o->check_every > 0 ? o->check_every : 8;
+    int refine = 0, cleanups = 0;
+    int64_t f_rounds = 0, f_pushes = 0;
+    fj_status result = FJ_OK;
+    for (;;) {
+        k_pass_reset<<<1, 1, 0, st>>>(ws.ctr, o->max_sweeps);
+        for (;;) {
+            for (int jj = 0; jj < check; ++jj) {
+                ++sweep;
+                T *dcur = (sweep & 1) ? db : da;
+                const T *dprev = (sweep & 1) ? da : db;
+                for (size_t cl = 0; cl + 1 < wp.class_item.size(); ++cl) {
+                    const int64_t i0 = wp.class_item[cl], ni = wp.class_item[cl + 1] - i0;
+                    if (ni <= 0) continue;
+                    const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(ni, 8), 152 * 8);
+                    FJ_CHECK(run.before(st));
+                    if (c.w)
+                        k_sweep_batch<T, true><<<grid, 256, 0, st>>>(wp.items, i0, ni, c.row_ptr, c.col, c.w, k, dcur,
+                                                                     dprev, r, h, inv, b.zhat, om, c.indeg,
+                                                                     wp.slot_first, wp.slot_nchunk, b.partk, wp.cnt,
+                                                                     ws.ctr, c.n);
+                    else
+                        k_sweep_batch<T, false><<<grid, 256, 0, st>>>(wp.items, i0, ni, c.row_ptr, c.col, c.w, k,
+                                                                      dcur, dprev, r, h, inv, b.zhat, om, c.indeg,
+                                                                      wp.slot_first, wp.slot_nchunk, b.partk, wp.cnt,
+                                                                      ws.ctr, c.n);
+                    FJ_CUDA(cudaGetLastError());
+                    FJ_CHECK(run.after(st));
+                }
+                k_end_sweep<<<1, 1, 0, st>>>(ws.ctr);
+                ++run.launches;
+            }
+            FJ_CUDA(cudaMemcpyAsync(ws.ctr_host, ws.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+            FJ_CUDA(cudaStreamSynchronize(st));
+            FJ_CHECK(run.harvest());
+            FJ_CHECK(check_index_record());
+            if (ws.ctr_host->done) break;
+        }
+        const int done = ws.ctr_host->done;
+        if (done == 3) {
+            result = FJ_ERR_DIVERGED;
+            set_error("residual became non-finite (omega %.3f)", o->omega);
+            break;
+        }
+        auto certify_count = [&](double &viol) -> fj_status {
+            FJ_CHECK(certify());
+            run.launches += 2;
+            FJ_CUDA(cudaMemcpyAsync(b.gstat_host, b.gstat, sizeof(double) * kGs * k, cudaMemcpyDeviceToHost, st));
+            FJ_CUDA(cudaStreamSynchronize(st));
+            FJ_CHECK(check_index_record());
+            viol = 0.0;
+            for (int j = 0; j < k; ++j) viol += b.gstat_host[j * kGs + 5];
+            return FJ_OK;
+        };
+        double viol = 0.0;
+        FJ_CHECK(certify_count(viol));
+        while (viol > 0.0 && viol <= (double)frontier_limit(n * k) && cleanups < kMaxCleanups) {
+            bool cleared = false;
+            ++cleanups;
+            FJ_CHECK(frontier_cleanup(g, p, k, b.r64, b.zhat, b.sp, epsp, b.list, kCleanupRounds, st, run, &f_rounds,
+                                      &f_pushes, &cleared));
+            FJ_CHECK(certify_count(viol));
+            if (!cleared) break;
+        }
+        if (viol == 0.0) break;
+        if (done == 2 || refine >= o->max_refine) {
+            result = FJ_ERR_NOT_CONVERGED;
+            set_error("batch did not certify (%.0f entries above threshold)", viol);
+            break;
+        }
+        ++refine;
+        sweep = 0;
+    }
+    double *Zd = mem == FJ_MEM_DEVICE ? Z : b.zout;
+    k_unshift_batch<T><<<grid_for(n * k, 256, 152 * 16), 256, 0, st>>>(n, k, b.zhat, p.perm, gs, Zd);
+    FJ_CUDA(cudaGetLastError());
+    if (mem == FJ_MEM_HOST) FJ_CUDA(cudaMemcpyAsync(Z, b.zout, sizeof(double) * n * k, cudaMemcpyDeviceToHost, st));
+    FJ_CUDA(cudaMemcpyAsync(b.gstat_host, b.gstat, sizeof(double) * kGs * k, cudaMemcpyDeviceToHost, st));
+    FJ_CUDA(cudaMemcpyAsync(ws.ctr_host, ws.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+    FJ_CUDA(cudaStreamSynchronize(st));
+    FJ_CHECK(read_dev_error(g, st));
+    if (info) {
+        for (int j = 0; j < k; ++j) {
+            const double *q = b.gstat_host + (size_t)j * kGs;
+            fj_solve_info &f = info[j];
+            std::memset(&f, 0, sizeof(f));
+            f.sweeps = ws.ctr_host->sweeps;
+            f.pushes = (int64_t)ws.ctr_host->pushes;
+            f.edges = (int64_t)ws.ctr_host->edges;
+            f.refine_passes = refine;
+            f.c_eff = q[1];
+            f.eps_prime = epsp;
+            f.resid_inf = q[2];
+            f.resid_rel_max = q[3];
+            f.z_inf = q[4];
+            f.err_bound = q[2];
+            f.converged = (q[5] == 0.0 && result == FJ_OK) ? 1 : 0;
+            f.launches = run.launches + 1;
+            f.push_launches = run.push_launches;
+            f.push_ms = run.push_ms;
+            f.frontier_rounds = f_rounds;
+            f.frontier_pushes = f_pushes;
+            const double tb = (double)sizeof(T);
+            // per sweep: columns and weights once, k increments per nonzero, k row records per row
+            f.push_bytes = (double)ws.ctr_host->sweeps *
+                           ((double)c.nnz * (4.0 + (c.w ? 4.0 : 0.0) + tb * k) + (double)c.n * (8.0 + 5.0 * tb * k));
+        }
+    }
+    return result;
+}
+
+}  // namespace fj
+
+extern "C" fj_status fj_solve_batch(fj_graph *g, const double *S, int k, const fj_solve_opts *opts, double *Z_out,
+                                    fj_solve_info *info, int mem)
+{
+    FJ_ARG(g != nullptr, "graph is NULL");
+    FJ_ARG(S != nullptr && Z_out != nullptr, "S or Z_out is NULL");
+    FJ_ARG(k >= 1 && k <= 64, "k must be in 1..64");
+    FJ_ARG(mem == FJ_MEM_HOST || mem == FJ_MEM_DEVICE, "mem must be FJ_MEM_HOST or FJ_MEM_DEVICE");
+    FJ_ARG(g->ngraphs == 1, "a ragged handle takes one opinion vector per graph (use fj_solve)");
+    FJ_CHECK(fj::check_opts(opts));
+    if (opts->precision == FJ_PREC_FP32) return fj::solve_batch_t<float>(g, S, nullptr, k, opts, Z_out, info, mem);
+    return fj::solve_batch_t<double>(g, S, nullptr, k, opts, Z_out, info, mem);
+}

@@ -30,7 +30,28 @@ def to_dev(*arrays):
     return out
 
 
+U64 = 2.0 ** -53  # unit roundoff of FP64
+
+
 def certificate_holds(n, rp, col, w, s, z, c_eff, epsp, slack=1.0):
-    """Recompute the FP64 residual of the GPU result on the CPU (Lemma 5's premise)."""
-    r = oracle.residual(n, rp, col, w, s + c_eff, z + c_eff)
-    return bool(np.all(np.abs(r) <= slack * epsp * (s + c_eff) * (1 + 1e-9) + 1e-300)), r
+    """Recompute the certificate of the GPU result on the CPU (Lemma 5's premise).
+
+    The shifted system's residual s' - (I + L)(z + c_eff) equals s - (I + L) z
+    (rows of L sum to zero), so it is evaluated on the returned z, with
+    compensated sums (exact to a few ulp).  Allowed per node: the solver's test
+    max(eps' s'_v, 2^-51 (1 + d_v) |z'_v|) (the second term is the FP64
+    resolution of row v: one ulp of z'_v moves r_v by (1 + d_v) ulp), plus
+    what rounding z' - c_eff and s + c_eff once per entry can change:
+    u ((1 + d_v)|z_v| + sum_c a_vc |z_c| + |s'_v|).
+    """
+    r = oracle.residual_accurate(n, rp, col, w, s, z)
+    d = oracle.out_degree(n, rp, w)
+    sp = s + c_eff
+    zp = z + c_eff
+    wa = np.ones(col.shape[0]) if w is None else np.asarray(w, np.float64)
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    nb = np.bincount(rows, weights=wa * np.abs(z[col]), minlength=n)
+    thr = np.maximum(epsp * sp, 2.0 ** -51 * (1.0 + d) * np.abs(zp))
+    rnd = U64 * ((1.0 + d) * np.abs(z) + nb + np.abs(sp))
+    ok = bool(np.all(np.abs(r) <= slack * thr * (1 + 1e-9) + 2.0 * rnd + 1e-300))
+    return ok, r

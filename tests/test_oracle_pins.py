@@ -404,6 +404,56 @@ def test_degree_sums_are_exact_in_fp64():
     assert np.array_equal(rev, d[::97])
 
 
+def _exact_residual(n, rp, col, w, s, z):
+    """s - (I + L) z over the rationals (every FP64 input is an exact rational)."""
+    out = []
+    for v in range(n):
+        acc = Fraction(float(s[v])) - Fraction(float(z[v]))
+        for k in range(int(rp[v]), int(rp[v + 1])):
+            a = Fraction(float(w[k])) if w is not None else Fraction(1)
+            acc += a * (Fraction(float(z[int(col[k])])) - Fraction(float(z[v])))
+        out.append(acc)
+    return out
+
+
+@pytest.mark.parametrize("weighted", [False, True])
+def test_accurate_residual_matches_rational_arithmetic(weighted):
+    """Dot2 residual = the exact residual rounded, within 2 ulp, even where a plain
+    FP64 row sum loses every digit (s built so that the residual is one rounding)."""
+    rng = np.random.default_rng(7)
+    n = 40
+    arcs, ws = [], []
+    for u in range(n):
+        deg = 400 if u == 0 else int(rng.integers(0, 6))  # one hub row
+        for v in rng.choice(np.arange(1, n), size=min(deg, n - 1), replace=deg > n - 1):
+            if v != u:
+                arcs.append((u, int(v)))
+                ws.append(float(np.float32(0.5 + rng.random())))
+    src = np.array([a for a, _ in arcs], np.int32)
+    dst = np.array([b for _, b in arcs], np.int32)
+    rp, col, w = oracle.csr_from_arcs(n, src, dst, np.array(ws, np.float32) if weighted else None)
+    # hub rows repeat columns only through the arc list; csr_from_arcs keeps one copy each
+    z = 1.0 + rng.random(n) * 1e-3
+    # s_v = round((I + L) z)_v: the exact residual is only s's rounding error
+    exact_lz = _exact_residual(n, rp, col, w, np.zeros(n), z)
+    s = np.array([float(-x) for x in exact_lz])
+    want = _exact_residual(n, rp, col, w, s, z)
+    got = oracle.residual_accurate(n, rp, col, w, s, z)
+    plain = oracle.residual(n, rp, col, w, s, z)
+    u = 2.0 ** -53
+    for v in range(n):
+        wv = float(want[v])
+        assert abs(got[v] - wv) <= 4 * u * abs(wv) + 1e-300, (v, got[v], wv)
+    # the plain sum is off by far more than the residual itself at the hub
+    assert abs(plain[0] - float(want[0])) > 10 * abs(float(want[0])) or float(want[0]) == 0.0
+    # generic inputs: also within 2 ulp of the rational value
+    s2 = rng.random(n)
+    want2 = _exact_residual(n, rp, col, w, s2, z)
+    got2 = oracle.residual_accurate(n, rp, col, w, s2, z)
+    for v in range(n):
+        assert abs(got2[v] - float(want2[v])) <= 4 * u * abs(float(want2[v])) + 1e-300
+
+
 def test_empty_and_edgeless_graphs():
     rp = np.zeros(4, np.int64)
     col = np.zeros(0, np.int32)
