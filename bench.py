@@ -38,6 +38,7 @@ WORKLOADS = {
     # 64 opinion vectors (U[0,1], Beta(1/2,1/2), +-1 labels) as one multi-right-hand-side push
     "rmat22_und_k64": dict(gen="rmat_und_multi", scale=22, nvec=64, precision="fp32", omega=1.8, cpu_scale=19),
     "rmat16_und_k64": dict(gen="rmat_und_multi", scale=16, nvec=64, precision="fp32", omega=1.8),
+    "rmat20_und_k64": dict(gen="rmat_und_multi", scale=20, nvec=64, precision="fp32", omega=1.8),
 }
 EPS = 1e-6
 METRIC = "FJ solves/s to 1e-6 rel. err (GTEPS, % HBM roofline): plain vs batched/warm-start"

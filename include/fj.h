@@ -295,6 +295,58 @@ fj_status fj_frontier_static(int64_t n, const void *r, const void *h, int precis
 fj_status fj_residual(fj_graph *g, const double *s, const double *z, double c_eff, double *r,
                       int mem, void *stream);
 
+/* ------------------------------------------------------------------ learned warm start
+ *
+ * A three-layer message-passing network that predicts a start z0 for
+ * fj_solve_warm.  It has no counterpart in the paper: a push from any start
+ * reaches the same certificate (Lemmas 3 and 5), so the network can only
+ * change the work, never the result.  With a_vj the CSR weights, d_v the
+ * weighted out-degree and din_v the number of nodes listening to v:
+ *   x_v  = [s_v, log(1 + d_v), log(1 + din_v), sum_j a_vj s_j / d_v]
+ *   h^l_v = relu(Ws^l^T h^{l-1}_v + Wn^l^T g^{l-1}_v + b^l),
+ *   g^{l-1}_v = sum_j a_vj h^{l-1}_j / d_v (0 when d_v = 0), h^0 = x,
+ *   l = 1, 2, 3, width 64;  z0_v = w_o . h^3_v + b_o.
+ * The dense products run on the tensor cores in BF16 with FP32 accumulation.
+ *
+ * Parameters are one FP32 vector of fj_mpnn_param_count() entries, in this
+ * order: for l = 1, 2, 3 the matrices Ws^l [F_in][64] and Wn^l [F_in][64]
+ * (row-major; F_in = 4 for l = 1, else 64) and b^l [64], then w_o [64], b_o.
+ * The handle owns the parameters, the Adam state and the activations of the
+ * last graph it saw; it is bound to the device current at creation.
+ */
+typedef struct fj_mpnn fj_mpnn;
+
+int64_t fj_mpnn_param_count(void);
+
+/* params: host FP32 vector of fj_mpnn_param_count() entries (copied). */
+fj_status fj_mpnn_create(const float *params, fj_mpnn **out);
+void fj_mpnn_destroy(fj_mpnn *m);
+fj_status fj_mpnn_get_params(const fj_mpnn *m, float *params);
+fj_status fj_mpnn_set_params(fj_mpnn *m, const float *params);
+
+/*
+ * fj_mpnn_predict - z0[n] (FP64) for opinions s[n] (FP64) on graph g, clamped
+ * to [min s, max s] (where z lies, Section 3.2).  Host or device pointers per
+ * mem.  A ragged handle is treated as one graph (clamp to the global range).
+ */
+fj_status fj_mpnn_predict(fj_mpnn *m, fj_graph *g, const double *s, double *z0, int mem, void *stream);
+
+/*
+ * fj_mpnn_grad - forward and backward pass on one (graph, s, z) triple with
+ * loss mean_v (z0_v - z_v)^2 (z0 before clamping).  *loss receives the loss
+ * (may be NULL); grad (host FP32, fj_mpnn_param_count() entries, may be NULL)
+ * receives the gradient, which the handle also keeps for fj_mpnn_adam_step.
+ */
+fj_status fj_mpnn_grad(fj_mpnn *m, fj_graph *g, const double *s, const double *z, double *loss, float *grad,
+                       int mem, void *stream);
+
+/*
+ * fj_mpnn_adam_step - one Adam update (beta1 0.9, beta2 0.999, eps 1e-8,
+ * bias-corrected; Kingma and Ba 2015) with learning rate lr in (0, 1) from
+ * the gradient of the last fj_mpnn_grad.  FJ_ERR_INVALID_ARG without one.
+ */
+fj_status fj_mpnn_adam_step(fj_mpnn *m, double lr, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

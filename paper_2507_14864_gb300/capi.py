@@ -26,6 +26,8 @@ EXPORTED = [
     "fj_graph_create_from_arcs", "fj_graph_create_ragged", "fj_graph_destroy", "fj_graph_info",
     "fj_graph_export", "fj_graph_colour", "fj_solve", "fj_solve_warm", "fj_solve_batch",
     "fj_metrics", "fj_frontier", "fj_frontier_static", "fj_residual",
+    "fj_mpnn_param_count", "fj_mpnn_create", "fj_mpnn_destroy", "fj_mpnn_get_params", "fj_mpnn_set_params",
+    "fj_mpnn_predict", "fj_mpnn_grad", "fj_mpnn_adam_step",
 ]
 
 
@@ -93,8 +95,19 @@ def lib():
     L.fj_frontier.argtypes = [I64, VP, VP, I32, VP, VP, VP]
     L.fj_frontier_static.argtypes = [I64, VP, VP, I32, VP, VP, VP]
     L.fj_residual.argtypes = [VP, VP, VP, D, VP, I32, VP]
+    L.fj_mpnn_param_count.argtypes = []
+    L.fj_mpnn_param_count.restype = I64
+    L.fj_mpnn_create.argtypes = [VP, ctypes.POINTER(VP)]
+    L.fj_mpnn_destroy.argtypes = [VP]
+    L.fj_mpnn_destroy.restype = None
+    L.fj_mpnn_get_params.argtypes = [VP, VP]
+    L.fj_mpnn_set_params.argtypes = [VP, VP]
+    L.fj_mpnn_predict.argtypes = [VP, VP, VP, VP, I32, VP]
+    L.fj_mpnn_grad.argtypes = [VP, VP, VP, VP, ctypes.POINTER(D), VP, I32, VP]
+    L.fj_mpnn_adam_step.argtypes = [VP, D, VP]
     for name in EXPORTED:
-        if name not in ("fj_solve_opts_default", "fj_graph_destroy", "fj_status_string", "fj_last_error"):
+        if name not in ("fj_solve_opts_default", "fj_graph_destroy", "fj_status_string", "fj_last_error",
+                        "fj_mpnn_param_count", "fj_mpnn_destroy"):
             getattr(L, name).restype = st
     _lib = L
     return L
@@ -328,3 +341,70 @@ def frontier(r, h):
                              current_stream()), "fj_frontier")
     c = int(cnt.item())
     return lst[:c], c
+
+
+class MPNN:
+    """Owns an ``fj_mpnn`` handle: the learned warm-start network (parameters,
+    Adam state, activations) on the current device."""
+
+    def __init__(self, params):
+        p = np.ascontiguousarray(params, np.float32)
+        if p.shape != (self.param_count(),):
+            raise ValueError(f"expected {self.param_count()} parameters, got {p.shape}")
+        h = ctypes.c_void_p()
+        _check(lib().fj_mpnn_create(p.ctypes.data, ctypes.byref(h)), "fj_mpnn_create")
+        self._h = h
+
+    @staticmethod
+    def param_count() -> int:
+        return int(lib().fj_mpnn_param_count())
+
+    def close(self):
+        if self._h and self._h.value:
+            lib().fj_mpnn_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self) -> np.ndarray:
+        out = np.empty(self.param_count(), np.float32)
+        _check(lib().fj_mpnn_get_params(self._h, out.ctypes.data), "fj_mpnn_get_params")
+        return out
+
+    def set_params(self, params):
+        p = np.ascontiguousarray(params, np.float32)
+        _check(lib().fj_mpnn_set_params(self._h, p.ctypes.data), "fj_mpnn_set_params")
+
+    def predict(self, graph: "Graph", s, out=None):
+        mem = _mem_of(s, out)
+        if out is None:
+            if mem == FJ_MEM_DEVICE:
+                import torch
+                out = torch.empty_like(s)
+            else:
+                out = np.empty(np.asarray(s).shape[0], np.float64)
+        _check(lib().fj_mpnn_predict(self._h, graph.handle, _ptr(s, np.float64), _ptr(out, np.float64), mem,
+                                     current_stream()), "fj_mpnn_predict")
+        return out
+
+    def grad(self, graph: "Graph", s, z, want_grad=True):
+        """Loss and (optionally) the gradient (host FP32) on one triple; keeps it for adam_step."""
+        mem = _mem_of(s, z)
+        loss = ctypes.c_double()
+        g = np.empty(self.param_count(), np.float32) if want_grad else None
+        _check(lib().fj_mpnn_grad(self._h, graph.handle, _ptr(s, np.float64), _ptr(z, np.float64),
+                                  ctypes.byref(loss), None if g is None else g.ctypes.data, mem,
+                                  current_stream()), "fj_mpnn_grad")
+        return loss.value, g
+
+    def adam_step(self, lr: float):
+        _check(lib().fj_mpnn_adam_step(self._h, float(lr), current_stream()), "fj_mpnn_adam_step")
+
+    def train_step(self, graph: "Graph", s, z, lr: float) -> float:
+        loss, _ = self.grad(graph, s, z, want_grad=False)
+        self.adam_step(lr)
+        return loss

@@ -678,8 +678,11 @@ void fj_graph_destroy(fj_graph *g)
     dev_free(g->colr.perm);
     dev_free(g->colr.iperm);
     dev_free(g->colr.din_p);
+    dev_free(g->colr.tptr);
+    dev_free(g->colr.tcol);
+    dev_free(g->colr.tw);
     csr_free(g->colr.pcsr);
-    for (ItemPlan *ip : {&g->plan_csr, &g->plan_pcsr, &g->wplan_csr, &g->wplan_pcsr}) {
+    for (ItemPlan *ip : {&g->wplan_csr, &g->wplan_pcsr}) {
         dev_free(ip->items);
         dev_free(ip->slot_first);
         dev_free(ip->slot_nchunk);
@@ -699,7 +702,7 @@ void fj_graph_destroy(fj_graph *g)
     BatchWorkspace &b = g->bws;
     dev_free(b.r); dev_free(b.h); dev_free(b.da); dev_free(b.db); dev_free(b.zhat); dev_free(b.sp);
     dev_free(b.sin); dev_free(b.zout); dev_free(b.om); dev_free(b.gstat); dev_free(b.partk);
-    dev_free(b.r64); dev_free(b.list);
+    dev_free(b.r64); dev_free(b.list); dev_free(b.tick);
     if (b.gstat_host) cudaFreeHost(b.gstat_host);
     if (ws.gstat_host) cudaFreeHost(ws.gstat_host);
     sort_scratch_free(g->sort);
@@ -1098,7 +1101,6 @@ static void colouring_free(fj_graph *g)
     dev_free(cl.tw);
     csr_free(cl.pcsr);
     cl = Colouring();
-    item_plan_free(g->plan_pcsr);
     item_plan_free(g->wplan_pcsr);
     g->ws.gen++;
 }

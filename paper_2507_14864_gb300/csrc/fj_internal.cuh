@@ -139,6 +139,8 @@ struct BatchWorkspace {
     double *gstat_host = nullptr;
     double *partk = nullptr;   // per long-row chunk and right-hand side (two words: hi, lo)
     int64_t cap_partk = 0;
+    unsigned int *tick = nullptr;  // per colour class: next tile, retired warps
+    int64_t cap_tick = 0;
 };
 
 }  // namespace fj
@@ -155,8 +157,7 @@ struct fj_graph {
     std::vector<int64_t> node_off;     // host, ngraphs + 1
     int64_t *node_off_d = nullptr;
     fj::Colouring colr;
-    fj::ItemPlan plan_csr, plan_pcsr;    // block-tile items (certificate)
-    fj::ItemPlan wplan_csr, wplan_pcsr;  // warp-tile items (sweep)
+    fj::ItemPlan wplan_csr, wplan_pcsr;  // warp-tile items (sweep and certificate)
     fj::Workspace ws;
     fj::BatchWorkspace bws;
     fj::SortScratch sort;

@@ -175,60 +175,6 @@ __global__ void k_end_sweep(Counters *c)
 
 // ============================================================== helpers
 
-// Segmented inclusive scan of compensated pairs p[0, nz) in shared memory
-// (segments start where head[i] != 0), by 8 warps over contiguous chunks:
-// afterwards the last element of every row holds that row's sum.
-__device__ __forceinline__ void block_segscan_dd(DD *p, const unsigned char *head, int nz, DD *wcarry, int *whas)
-{
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int C = (((nz + 7) >> 3) + 31) & ~31;
-    const int beg = wid * C;
-    const int end = min(beg + C, nz);
-    DD carry{0.0, 0.0};
-    int seen = 0;
-    int first_head = end;
-    for (int base = beg; base < end; base += 32) {
-        const int i = base + lane;
-        const bool valid = i < end;
-        DD v = valid ? p[i] : DD{0.0, 0.0};
-        int f = valid ? (int)head[i] : 0;
-        const unsigned hb = __ballot_sync(0xffffffffu, f != 0);
-        if (hb && !seen) first_head = base + __ffs(hb) - 1;
-        seen |= (hb != 0u);
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            DD u;
-            u.hi = __shfl_up_sync(0xffffffffu, v.hi, o);
-            u.lo = __shfl_up_sync(0xffffffffu, v.lo, o);
-            const int fu = __shfl_up_sync(0xffffffffu, f, o);
-            if (lane >= o) {
-                if (!f) v = dd_merge(u, v);
-                f |= fu;
-            }
-        }
-        if (!f) v = dd_merge(carry, v);
-        if (valid) p[i] = v;
-        carry.hi = __shfl_sync(0xffffffffu, v.hi, 31);
-        carry.lo = __shfl_sync(0xffffffffu, v.lo, 31);
-    }
-    if (lane == 0) {
-        wcarry[wid] = carry;
-        whas[wid] = seen;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        DD cin{0.0, 0.0};
-        for (int w = 0; w < 8; ++w) {
-            const DD out = whas[w] ? wcarry[w] : dd_merge(cin, wcarry[w]);
-            wcarry[w] = cin;  // becomes the carry-in of warp w
-            cin = out;
-        }
-    }
-    __syncthreads();
-    const DD cin = wcarry[wid];
-    for (int i = beg + lane; i < first_head; i += 32) p[i] = dd_merge(cin, p[i]);
-}
-
 template <typename T, bool W>
 __device__ __forceinline__ T arc_w(const float *__restrict__ w, int64_t k)
 {
@@ -539,37 +485,46 @@ k_sweep(const Item *__restrict__ items, int64_t item0, int64_t nitems, const int
 // residual of the stored zhat' to about one rounding, at any degree.  Per
 // graph: max |r64|, max |r64| / s', max |zhat - c_eff|, and the number of
 // nodes with |r64| > max(eps' s', resid_floor).  Stores r64 into the push
-// residual (magnitude rounded up for FP32) and clears both increment buffers:
-// the push restarts from an exact residual (a refinement pass).  A block item
-// forms each product a_xj zhat_j with its rounding error in shared memory and
-// sums rows by a segmented scan of the pairs; a chunk of a long row is summed
-// by the whole block and the last chunk to finish completes the row.
+// residual (magnitude rounded up for FP32) and the FP64 residual, and clears
+// both increment buffers: the push restarts from an exact residual (a
+// refinement pass).
+//
+// One warp per warp tile (grid-strided): a row of at most kShortRow nonzeros
+// is summed by one lane, a longer row by the whole warp (lanes stride the row,
+// then a warp reduction of the compensated pairs); a chunk of a long row is
+// summed by the warp and the last chunk to finish completes the row.
+constexpr int kShortRow = 8;
+
 template <typename T, bool W>
 __global__ void __launch_bounds__(256)
-k_certify(const Item *__restrict__ items, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
-          const float *__restrict__ w, const double *__restrict__ zhat, const double *__restrict__ sp,
-          const double *__restrict__ deg, const int32_t *__restrict__ graph_of, double epsp, T *__restrict__ r,
-          T *__restrict__ da, T *__restrict__ db, unsigned long long *gs, const int32_t *__restrict__ slot_first,
-          const int32_t *__restrict__ slot_nchunk, double *part, int32_t *cnt, double *__restrict__ r64,
-          int64_t n_rows)
+k_certify(const Item *__restrict__ items, int64_t nitems, const int64_t *__restrict__ rp,
+          const int32_t *__restrict__ col, const float *__restrict__ w, const double *__restrict__ zhat,
+          const double *__restrict__ sp, const double *__restrict__ deg, const int32_t *__restrict__ graph_of,
+          double epsp, T *__restrict__ r, T *__restrict__ da, T *__restrict__ db, unsigned long long *gs,
+          const int32_t *__restrict__ slot_first, const int32_t *__restrict__ slot_nchunk, double *part, int32_t *cnt,
+          double *__restrict__ r64, int64_t n_rows)
 {
-    __shared__ DD prod[2 * kBlockNnz];
-    __shared__ unsigned char head[2 * kBlockNnz];
-    __shared__ DD wcarry[8];
-    __shared__ int whas[8];
-    __shared__ double red[4][8];
-    const Item it = items[blockIdx.x];
-    const int64_t r0 = it.r0, r1 = it.r1;
-    if (!FJ_IDX_OK(1, r0, n_rows) || !FJ_IDX_OK(2, r1, n_rows + 1) || !FJ_IDX_OK(3, r1 - r0, kBlockRows + 1)) return;
-    const int64_t k0 = it.k0, k1 = it.k1;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int gph = graph_of ? graph_of[r0] : 0;
-    if (!FJ_IDX_OK(6, gph, 1 << 20)) return;
-    const double ce = reinterpret_cast<const double *>(gs)[(int64_t)gph * kGs + 1];
-    double m_abs = 0.0, m_rel = 0.0, m_z = 0.0, viol = 0.0;
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const double *gsd = reinterpret_cast<const double *>(gs);
+    int cur_g = -1;
+    double ce = 0.0, m_abs = 0.0, m_rel = 0.0, m_z = 0.0, viol = 0.0;
 
+    auto flush = [&]() {  // warp-uniform
+        const double a = warp_max(m_abs), rl = warp_max(m_rel), zz = warp_max(m_z), v = warp_sum(viol);
+        if (lane == 0 && cur_g >= 0) {
+            unsigned long long *g = gs + (int64_t)cur_g * kGs;
+            atomic_max_nonneg(reinterpret_cast<double *>(g + 2), a);
+            atomic_max_nonneg(reinterpret_cast<double *>(g + 3), rl);
+            atomic_max_nonneg(reinterpret_cast<double *>(g + 4), zz);
+            if (v > 0) atomicAdd(reinterpret_cast<double *>(g + 5), v);
+        }
+        m_abs = m_rel = m_z = viol = 0.0;
+    };
     // completes row x from acc = sum_j a_xj zhat_j (compensated)
-    auto epilogue = [&](int64_t x, DD acc) {
+    auto finish = [&](int64_t x, DD acc) {
         const double zx = zhat[x];
         dd_add(acc, sp[x]);
         dd_fma(acc, -(1.0 + deg[x]), zx);
@@ -585,89 +540,77 @@ k_certify(const Item *__restrict__ items, const int64_t *__restrict__ rp, const 
         da[x] = T(0);
         db[x] = T(0);
     };
+    auto gather = [&](int64_t k, DD &acc) {
+        const int32_t cj = __ldg(col + k);
+        if (FJ_IDX_OK(4, cj, n_rows)) dd_fma(acc, arc_w<double, W>(w, k), zhat[cj]);
+    };
 
-    if (it.slot >= 0) {
-        DD acc{0.0, 0.0};
-        for (int64_t k = k0 + threadIdx.x; k < k1; k += 256) {
-            int32_t cj = __ldg(col + k);
-            if (FJ_IDX_OK(7, cj, n_rows)) dd_fma(acc, arc_w<double, W>(w, k), zhat[cj]);
+    for (int64_t ii = warp; ii < nitems; ii += nwarps) {
+        const Item it = items[ii];
+        const int64_t r0 = it.r0, r1 = it.r1;
+        if (!FJ_IDX_OK(1, r0, n_rows) || !FJ_IDX_OK(2, r1, n_rows + 1) ||
+            (it.slot < 0 && !FJ_IDX_OK(3, r1 - r0, kWarpRows + 1)))
+            continue;
+        const int gph = graph_of ? graph_of[r0] : 0;
+        if (!FJ_IDX_OK(6, gph, 1 << 20)) continue;
+        if (gph != cur_g) {
+            flush();
+            cur_g = gph;
+            ce = gsd[(int64_t)gph * kGs + 1];
         }
-        acc = warp_dd_sum(acc);
-        if (lane == 0) wcarry[wid] = acc;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            DD t = wcarry[0];
-            for (int i = 1; i < 8; ++i) t = dd_merge(t, wcarry[i]);
+        if (it.slot < 0) {
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                const int64_t x = r0 + lane + 32 * half;
+                const bool mine = x < r1;
+                int64_t a = 0, e = 0;
+                if (mine) {
+                    a = rp[x];
+                    e = rp[x + 1];
+                }
+                const bool shortrow = mine && e - a <= kShortRow;
+                if (shortrow) {
+                    DD acc{0.0, 0.0};
+                    for (int64_t k = a; k < e; ++k) gather(k, acc);
+                    finish(x, acc);
+                }
+                unsigned longs = __ballot_sync(FULL, mine && !shortrow);
+                while (longs) {
+                    const int src = __ffs(longs) - 1;
+                    longs &= longs - 1;
+                    const int64_t al = __shfl_sync(FULL, a, src), el = __shfl_sync(FULL, e, src);
+                    DD acc{0.0, 0.0};
+                    for (int64_t k = al + lane; k < el; k += 32) gather(k, acc);
+                    acc = warp_dd_sum(acc);
+                    if (lane == 0) finish(r0 + src + 32 * half, acc);
+                }
+            }
+        } else {
+            DD acc{0.0, 0.0};
+            for (int64_t k = it.k0 + lane; k < it.k1; k += 32) gather(k, acc);
+            acc = warp_dd_sum(acc);
             const int slot = it.slot;
             const int first = slot_first[slot], nch = slot_nchunk[slot];
-            const int ci = (int)((k0 - rp[r0]) / kChunkNnz);
-            part[2 * (first + ci)] = t.hi;
-            part[2 * (first + ci) + 1] = t.lo;
-            __threadfence();
-            if (atomicAdd(&cnt[slot], 1) == nch - 1) {
+            const int ci = (int)((it.k0 - rp[r0]) / kWarpChunk);
+            int last = 0;
+            if (lane == 0) {
+                part[2 * (first + ci)] = acc.hi;
+                part[2 * (first + ci) + 1] = acc.lo;
+                __threadfence();
+                last = atomicAdd(&cnt[slot], 1) == nch - 1;
+            }
+            last = __shfl_sync(FULL, last, 0);
+            if (last && lane == 0) {
                 __threadfence();
                 DD sum{0.0, 0.0};
                 for (int c = 0; c < nch; ++c)
                     sum = dd_merge(sum, DD{__ldcg(part + 2 * (first + c)), __ldcg(part + 2 * (first + c) + 1)});
                 cnt[slot] = 0;
-                epilogue(r0, sum);
+                finish(r0, sum);
             }
         }
-    } else {
-        const int nzi = (int)(k1 - k0);
-        if (!FJ_IDX_OK(8, nzi, 2 * kBlockNnz + 1)) return;
-        for (int i = threadIdx.x; i < nzi; i += 256) head[i] = 0;
-        __syncthreads();
-        for (int64_t x = r0 + threadIdx.x; x < r1; x += 256) {
-            const int64_t a = rp[x];
-            if (rp[x + 1] > a && FJ_IDX_OK(5, a - k0, nzi)) head[a - k0] = 1;
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < nzi; i += 256) {
-            const int64_t k = k0 + i;
-            const int32_t cj = __ldg(col + k);
-            DD t{0.0, 0.0};
-            if (FJ_IDX_OK(4, cj, n_rows)) {
-                const double a = arc_w<double, W>(w, k), z = zhat[cj];
-                t.hi = __dmul_rn(a, z);
-                t.lo = fma(a, z, -t.hi);
-            }
-            prod[i] = t;
-        }
-        __syncthreads();
-        block_segscan_dd(prod, head, nzi, wcarry, whas);
-        __syncthreads();
-        for (int64_t x = r0 + threadIdx.x; x < r1; x += 256) {
-            const int64_t a = rp[x], e = rp[x + 1];
-            epilogue(x, e > a ? prod[e - 1 - k0] : DD{0.0, 0.0});
-        }
     }
-    (void)k1;
-    m_abs = warp_max(m_abs);
-    m_rel = warp_max(m_rel);
-    m_z = warp_max(m_z);
-    viol = warp_sum(viol);
-    if (lane == 0) {
-        red[0][wid] = m_abs;
-        red[1][wid] = m_rel;
-        red[2][wid] = m_z;
-        red[3][wid] = viol;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double a = 0, rl = 0, zz = 0, v = 0;
-        for (int i = 0; i < 8; ++i) {
-            a = fmax(a, red[0][i]);
-            rl = fmax(rl, red[1][i]);
-            zz = fmax(zz, red[2][i]);
-            v += red[3][i];
-        }
-        unsigned long long *g = gs + (int64_t)gph * kGs;
-        atomic_max_nonneg(reinterpret_cast<double *>(g + 2), a);
-        atomic_max_nonneg(reinterpret_cast<double *>(g + 3), rl);
-        atomic_max_nonneg(reinterpret_cast<double *>(g + 4), zz);
-        if (v > 0) atomicAdd(reinterpret_cast<double *>(g + 5), v);
-    }
+    flush();
 }
 
 // Clears the per-graph certificate slots (2..6) before a certify pass.
@@ -821,8 +764,7 @@ static fj_status ws_grow(fj_graph *g, int64_t entries, int ngraphs)
 struct Plan {
     const DevCSR *c = nullptr;  // CSR the push runs on
     const int32_t *perm = nullptr;
-    const ItemPlan *ip = nullptr;   // block-tile items (certificate)
-    const ItemPlan *wip = nullptr;  // warp-tile items (sweep)
+    const ItemPlan *wip = nullptr;  // warp-tile items (sweep, certificate)
     bool mc = false;
 };
 
@@ -992,18 +934,14 @@ static fj_status make_plan(fj_graph *g, const fj_solve_opts *o, cudaStream_t st,
     p.mc = o->schedule != FJ_SCHED_JACOBI;
     if (!p.mc) {
         p.c = &g->csr;
-        if (!g->plan_csr.built) FJ_CHECK(build_items(g, g->csr, nullptr, g->plan_csr, st, false));
         if (!g->wplan_csr.built) FJ_CHECK(build_items(g, g->csr, nullptr, g->wplan_csr, st, true));
-        p.ip = &g->plan_csr;
         p.wip = &g->wplan_csr;
         return FJ_OK;
     }
     FJ_CHECK(ensure_colouring(g, o->palette, st));
     p.c = &g->colr.pcsr;
     p.perm = g->colr.perm;
-    if (!g->plan_pcsr.built) FJ_CHECK(build_items(g, g->colr.pcsr, &g->colr.class_row, g->plan_pcsr, st, false));
     if (!g->wplan_pcsr.built) FJ_CHECK(build_items(g, g->colr.pcsr, &g->colr.class_row, g->wplan_pcsr, st, true));
-    p.ip = &g->plan_pcsr;
     p.wip = &g->wplan_pcsr;
     return FJ_OK;
 }
@@ -1125,19 +1063,19 @@ static fj_status launch_certify(fj_graph *g, const Plan &p, double epsp, cudaStr
     run.launches += 2;
     Workspace &ws = g->ws;
     const DevCSR &c = *p.c;
-    const ItemPlan &ip = *p.ip;
+    const ItemPlan &ip = *p.wip;
     k_cert_reset<<<grid_for(g->ngraphs, 256), 256, 0, st>>>(g->ngraphs, reinterpret_cast<unsigned long long *>(ws.gstat));
     T *r = reinterpret_cast<T *>(ws.r), *da = reinterpret_cast<T *>(ws.da), *db = reinterpret_cast<T *>(ws.db);
     unsigned long long *gs = reinterpret_cast<unsigned long long *>(ws.gstat);
-    const unsigned grid = (unsigned)ip.nitems;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ip.nitems, 8), 152 * 8));
     if (c.w)
-        k_certify<T, true><<<grid, 256, 0, st>>>(ip.items, c.row_ptr, c.col, c.w, ws.zhat, ws.sp, c.deg64, c.graph_of,
-                                                 epsp, r, da, db, gs, ip.slot_first, ip.slot_nchunk, ip.part, ip.cnt,
-                                                 ws.r64, c.n);
+        k_certify<T, true><<<grid, 256, 0, st>>>(ip.items, ip.nitems, c.row_ptr, c.col, c.w, ws.zhat, ws.sp, c.deg64,
+                                                 c.graph_of, epsp, r, da, db, gs, ip.slot_first, ip.slot_nchunk,
+                                                 ip.part, ip.cnt, ws.r64, c.n);
     else
-        k_certify<T, false><<<grid, 256, 0, st>>>(ip.items, c.row_ptr, c.col, c.w, ws.zhat, ws.sp, c.deg64,
-                                                  c.graph_of, epsp, r, da, db, gs, ip.slot_first, ip.slot_nchunk,
-                                                  ip.part, ip.cnt, ws.r64, c.n);
+        k_certify<T, false><<<grid, 256, 0, st>>>(ip.items, ip.nitems, c.row_ptr, c.col, c.w, ws.zhat, ws.sp,
+                                                  c.deg64, c.graph_of, epsp, r, da, db, gs, ip.slot_first,
+                                                  ip.slot_nchunk, ip.part, ip.cnt, ws.r64, c.n);
     FJ_CUDA(cudaGetLastError());
     return FJ_OK;
 }
@@ -1648,12 +1586,11 @@ k_sweep_batch(const Item *__restrict__ items, int64_t item0, int64_t nitems, con
               const T *__restrict__ dprev, T *__restrict__ r, const T *__restrict__ h, const T *__restrict__ inv,
               double *__restrict__ zhat, const T *__restrict__ om, const int32_t *__restrict__ indeg,
               const int32_t *__restrict__ slot_first, const int32_t *__restrict__ slot_nchunk, double *partk,
-              int32_t *cnt, Counters *ctr, int64_t n_rows)
+              int32_t *cnt, Counters *ctr, unsigned int *tick, int64_t n_rows)
 {
     __shared__ unsigned long long red[2][8];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     if (*reinterpret_cast<volatile int *>(&ctr->done)) return;
-    const int64_t nwarps = (int64_t)gridDim.x * 8;
     const bool has1 = lane < k, has2 = lane + 32 < k;
     unsigned long long my_push = 0, my_edges = 0;
     bool bad = false;
@@ -1697,8 +1634,14 @@ k_sweep_batch(const Item *__restrict__ items, int64_t item0, int64_t nitems, con
     auto no_begin = [](int64_t) {};
     constexpr int D = 8;
 
-    for (int64_t ii = item0 + (int64_t)blockIdx.x * 8 + wl; ii < item0 + nitems; ii += nwarps) {
-        const Item it = items[ii];
+    // tiles are drawn from tick[0] one at a time (dynamic balance across warps);
+    // the last warp to retire resets tick[0..1] for the next launch
+    for (;;) {
+        unsigned int got = 0;
+        if (lane == 0) got = atomicAdd(&tick[0], 1u);
+        got = __shfl_sync(0xffffffffu, got, 0);
+        if ((int64_t)got >= nitems) break;
+        const Item it = items[item0 + got];
         const int64_t r0 = it.r0, r1 = it.r1;
         if (!FJ_IDX_OK(11, r0, n_rows) || !FJ_IDX_OK(12, r1, n_rows + 1) ||
             (it.slot < 0 && !FJ_IDX_OK(13, r1 - r0, kWarpRows + 1)))
@@ -1735,6 +1678,13 @@ k_sweep_batch(const Item *__restrict__ items, int64_t item0, int64_t nitems, con
                 begin(r0);
                 apply_row(r0, (T)a1, (T)a2);
             }
+        }
+    }
+    if (lane == 0) {
+        __threadfence();
+        if (atomicAdd(&tick[1], 1u) == gridDim.x * 8u - 1u) {
+            tick[0] = 0u;
+            tick[1] = 0u;
         }
     }
     my_push = warp_sum(my_push);
@@ -1874,9 +1824,33 @@ k_certify_batch(const Item *__restrict__ items, int64_t nitems, const int64_t *_
     }
 }
 
-static fj_status bws_grow(fj_graph *g, int k, int64_t nparts)
+// Resident blocks of the batch sweep kernel (its persistent grid).
+template <typename T>
+static int64_t batch_sweep_blocks(bool weighted)
+{
+    static int cached[2] = {0, 0};
+    int &nres = cached[weighted ? 1 : 0];
+    if (nres == 0) {
+        int dev = 0, sms = 0, per = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return 152;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (weighted) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep_batch<T, true>, 256, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep_batch<T, false>, 256, 0);
+        nres = std::max(1, sms * std::max(1, per));
+    }
+    return nres;
+}
+
+static fj_status bws_grow(fj_graph *g, int k, int64_t nparts, int64_t nclasses)
 {
     BatchWorkspace &b = g->bws;
+    if (nclasses > b.cap_tick) {
+        dev_free(b.tick);
+        b.tick = nullptr;
+        FJ_CUDA(cudaMalloc(&b.tick, sizeof(unsigned int) * 2 * (size_t)nclasses));
+        FJ_CUDA(cudaMemset(b.tick, 0, sizeof(unsigned int) * 2 * (size_t)nclasses));
+        b.cap_tick = nclasses;
+    }
     const int64_t need = g->csr.n * k;
     if (need > b.cap) {
         void **vb[] = {&b.r, &b.h, &b.da, &b.db};
@@ -1928,7 +1902,7 @@ static fj_status solve_batch_t(fj_graph *g, const double *S, const double *Z0, i
     FJ_CHECK(make_plan(g, o, st, p));
     const DevCSR &c = *p.c;
     const ItemPlan &wp = *p.wip;
-    FJ_CHECK(bws_grow(g, k, wp.nparts));
+    FJ_CHECK(bws_grow(g, k, wp.nparts, (int64_t)wp.class_item.size()));
     BatchWorkspace &b = g->bws;
     const double epsp = o->sigma * o->eps / (o->c + o->sigma);
     const double *Sd = S, *Z0d = Z0;
@@ -1989,18 +1963,20 @@ static fj_status solve_batch_t(fj_graph *g, const double *S, const double *Z0, i
                 for (size_t cl = 0; cl + 1 < wp.class_item.size(); ++cl) {
                     const int64_t i0 = wp.class_item[cl], ni = wp.class_item[cl + 1] - i0;
                     if (ni <= 0) continue;
-                    const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(ni, 8), 152 * 8);
+                    const unsigned grid =
+                        (unsigned)std::min<int64_t>(ceil_div(ni, 8), batch_sweep_blocks<T>(c.w != nullptr));
+                    unsigned int *tk = b.tick + 2 * cl;
                     FJ_CHECK(run.before(st));
                     if (c.w)
                         k_sweep_batch<T, true><<<grid, 256, 0, st>>>(wp.items, i0, ni, c.row_ptr, c.col, c.w, k, dcur,
                                                                      dprev, r, h, inv, b.zhat, om, c.indeg,
                                                                      wp.slot_first, wp.slot_nchunk, b.partk, wp.cnt,
-                                                                     ws.ctr, c.n);
+                                                                     ws.ctr, tk, c.n);
                     else
                         k_sweep_batch<T, false><<<grid, 256, 0, st>>>(wp.items, i0, ni, c.row_ptr, c.col, c.w, k,
                                                                       dcur, dprev, r, h, inv, b.zhat, om, c.indeg,
                                                                       wp.slot_first, wp.slot_nchunk, b.partk, wp.cnt,
-                                                                      ws.ctr, c.n);
+                                                                      ws.ctr, tk, c.n);
                     FJ_CUDA(cudaGetLastError());
                     FJ_CHECK(run.after(st));
                 }
