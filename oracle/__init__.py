@@ -63,6 +63,8 @@ def _lib():
     lib.oracle_sor_ordered.restype = ctypes.c_int
     lib.oracle_residual.argtypes = [I64, VP, VP, VP, VP, VP, VP]
     lib.oracle_residual.restype = None
+    lib.oracle_csr_build.argtypes = [I64, I64, VP, VP, VP, VP, VP, VP]
+    lib.oracle_csr_build.restype = I64
     lib.oracle_residual_dot2.argtypes = [I64, VP, VP, VP, VP, VP, VP]
     lib.oracle_residual_dot2.restype = None
     lib.oracle_lu_solve.argtypes = [I64, VP, VP, VP]
@@ -96,7 +98,24 @@ def csr_from_arcs(n: int, src, dst, w=None):
     Drops self-loops, orders arcs by (src, dst) keeping generation order among
     repeats (stable), keeps the first arc of every repeated (src, dst) pair.
     Returns ``(row_ptr int64[n+1], col int32[nnz], w float32[nnz] or None)``.
+    Built by the C routine ``oracle_csr_build``; ``csr_from_arcs_np`` is the
+    same definition in numpy, and the pins check the two agree.
     """
+    src = np.ascontiguousarray(src, np.int32)
+    dst = np.ascontiguousarray(dst, np.int32)
+    m = int(src.shape[0])
+    wf = None if w is None else np.ascontiguousarray(w, np.float32)
+    row_ptr = np.empty(n + 1, np.int64)
+    col = np.empty(max(m, 1), np.int32)
+    wout = None if w is None else np.empty(max(m, 1), np.float32)
+    nnz = _lib().oracle_csr_build(n, m, _p(src), _p(dst), _p(wf), _p(row_ptr), _p(col), _p(wout))
+    if nnz < 0:
+        raise ValueError("arc list names a node outside [0, n)")
+    return row_ptr, col[:nnz].copy(), None if wout is None else wout[:nnz].copy()
+
+
+def csr_from_arcs_np(n: int, src, dst, w=None):
+    """csr_from_arcs by a stable lexicographic sort in numpy (the pins' second route)."""
     src = np.asarray(src, np.int64)
     dst = np.asarray(dst, np.int64)
     keep = src != dst

@@ -20,6 +20,80 @@
 #include <stdlib.h>
 #include <string.h>
 
+/*
+ * Simple-graph CSR from an arc list (Section 3.2: simple graphs): self-loops
+ * dropped, arcs ordered by (src, dst), the first arc in generation order kept
+ * of every repeated (src, dst).  Arcs are bucketed by src in generation order
+ * (a stable counting sort), each row is sorted by (dst, arc index), and runs of
+ * equal dst keep their first element.  row_ptr has n + 1 entries; col and
+ * w_out (NULL when w is NULL) room for m.  Returns nnz, or -1 on a bad node id
+ * or allocation failure.
+ */
+typedef struct {
+    int32_t dst;
+    int64_t e;
+} arc_key;
+
+static int arc_cmp(const void *a, const void *b)
+{
+    const arc_key *x = (const arc_key *)a, *y = (const arc_key *)b;
+    if (x->dst != y->dst) return x->dst < y->dst ? -1 : 1;
+    return x->e < y->e ? -1 : (x->e > y->e ? 1 : 0);
+}
+
+int64_t oracle_csr_build(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const float *w,
+                         int64_t *row_ptr, int32_t *col, float *w_out)
+{
+    int64_t *start = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    arc_key *keys = (arc_key *)malloc(sizeof(arc_key) * (size_t)(m > 0 ? m : 1));
+    if (!start || !keys) {
+        free(start);
+        free(keys);
+        return -1;
+    }
+    for (int64_t e = 0; e < m; ++e) {
+        if (src[e] < 0 || src[e] >= n || dst[e] < 0 || dst[e] >= n) {
+            free(start);
+            free(keys);
+            return -1;
+        }
+        if (src[e] != dst[e]) start[src[e] + 1] += 1;
+    }
+    for (int64_t u = 0; u < n; ++u) start[u + 1] += start[u];
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    if (!fill) {
+        free(start);
+        free(keys);
+        return -1;
+    }
+    for (int64_t u = 0; u < n; ++u) fill[u] = start[u];
+    for (int64_t e = 0; e < m; ++e) {
+        if (src[e] == dst[e]) continue;
+        arc_key k;
+        k.dst = dst[e];
+        k.e = e;
+        keys[fill[src[e]]++] = k;
+    }
+    free(fill);
+    int64_t nnz = 0;
+    row_ptr[0] = 0;
+    for (int64_t u = 0; u < n; ++u) {
+        arc_key *row = keys + start[u];
+        int64_t len = start[u + 1] - start[u];
+        if (len > 1) qsort(row, (size_t)len, sizeof(arc_key), arc_cmp);
+        for (int64_t i = 0; i < len; ++i) {
+            if (i > 0 && row[i].dst == row[i - 1].dst) continue;
+            col[nnz] = row[i].dst;
+            if (w && w_out) w_out[nnz] = w[row[i].e];
+            ++nnz;
+        }
+        row_ptr[u + 1] = nnz;
+    }
+    free(start);
+    free(keys);
+    return nnz;
+}
+
 /* Weighted out-degree d_u = sum of row u, summed in CSR order. */
 static void out_degree(int64_t n, const int64_t *row_ptr, const double *w, double *d)
 {
