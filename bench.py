@@ -39,6 +39,13 @@ WORKLOADS = {
     "rmat22_und_k64": dict(gen="rmat_und_multi", scale=22, nvec=64, precision="fp32", omega=1.8, cpu_scale=19),
     "rmat16_und_k64": dict(gen="rmat_und_multi", scale=16, nvec=64, precision="fp32", omega=1.8),
     "rmat20_und_k64": dict(gen="rmat_und_multi", scale=20, nvec=64, precision="fp32", omega=1.8),
+    # 256 BA graphs (m = 5), n log-uniform in [1e3, 2e5], one U[0,1] vector each, as one ragged handle
+    "ragged256_ba": dict(gen="ragged", count=256, lo=1000, hi=200000, precision="fp32", omega=1.5, cpu_scale=None),
+    # learned warm start: train on SBM/BA triples, then held-out directed R-MAT with 16 vectors
+    "rmat23_warm16": dict(gen="warm", scale=23, nvec=16, precision="fp32", omega=1.5, palette=8,
+                          train_steps=400, lr=2e-3, cpu_scale=18),
+    "rmat18_warm16": dict(gen="warm", scale=18, nvec=16, precision="fp32", omega=1.5, palette=8,
+                          train_steps=200, lr=2e-3),
 }
 EPS = 1e-6
 METRIC = "FJ solves/s to 1e-6 rel. err (GTEPS, % HBM roofline): plain vs batched/warm-start"
@@ -49,7 +56,10 @@ def make_workload(name, scale_override=None):
     spec = dict(WORKLOADS[name])
     if scale_override is not None:
         spec["scale"] = scale_override
-    if spec["gen"] == "rmat_dir":
+    if spec["gen"] == "warm":
+        g = W.rmat_directed(spec["scale"], nvec=spec["nvec"])
+        src, dst, w = g["src"], g["dst"], g["w"]
+    elif spec["gen"] == "rmat_dir":
         g = W.rmat_directed(spec["scale"])
         src, dst, w = g["src"], g["dst"], g["w"]
     elif spec["gen"] == "rmat_und":
@@ -216,19 +226,29 @@ def run_gpu(args):
 
     def solve(s, out, **kw):
         if k == 1:
-            return G.solve(s, out=out, **kw)
+            res = G.solve(s, out=out, **kw)
+            if "profile" not in kw:
+                G.metrics(s, res[0])  # a8: the Table 1 measures of the solve
+            return res
         if cols is not None:
             infos_ = []
             if s is s_d:
                 for c in cols:
                     infos_.extend(G.solve(c, out=zcol, **kw)[1])
+                    if "profile" not in kw:
+                        G.metrics(c, zcol)
             else:  # host buffers: one column at a time through the C ABI
                 for j in range(k):
                     zj = np.empty(s.shape[0])
-                    infos_.extend(G.solve(np.ascontiguousarray(s[:, j]), out=zj, **kw)[1])
+                    sj = np.ascontiguousarray(s[:, j])
+                    infos_.extend(G.solve(sj, out=zj, **kw)[1])
+                    G.metrics(sj, zj)
                     out[:, j] = zj
             return out, infos_, 0
-        return G.solve_batch(s, out=out, **kw)
+        res = G.solve_batch(s, out=out, **kw)
+        if "profile" not in kw:
+            G.metrics_batch(s, res[0])  # a8 for every vector of the batch
+        return res
     if args.check_every:
         opts["check_every"] = args.check_every
 
@@ -323,13 +343,315 @@ def run_gpu(args):
                        else "FP64", "l2": "inputs larger than L2 (CSR %.2f GB)" % (
                            ginfo["nnz"] * (8 if w is not None else 4) / 1e9),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": 8 * n * k,
-                    "d2h_bytes_per_step": 8 * n * k},
-            "gpu_launches": int(sum(i["launches"] for i in (infos if cols is not None else infos[::k]))),
+            "e2e": {"value": e2e_value, "unit": "solves/s",
+                    "h2d_bytes_per_step": (24 if k == 1 else 8) * n * k, "d2h_bytes_per_step": 8 * n * k},
+            # solve launches plus the five of each metrics call
+            "gpu_launches": int(sum(i["launches"] for i in (infos if cols is not None else infos[::k])))
+            + 5 * args.steps * (k if cols is not None else 1),
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "detail": detail,
         }
         print(json.dumps(line), flush=True)
     G.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def run_warm(args):
+    """Learned warm start: solves/s of (predict z0 + push from z0) against the
+    zero start on the same vectors, both to the same certificate."""
+    import torch
+
+    world, rank, local = dist_init()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2507_14864_gb300 import capi
+    from fjsynth import workloads as W
+
+    spec = WORKLOADS[args.workload]
+    dev = torch.device("cuda", local)
+    omega = args.omega if args.omega is not None else spec["omega"]
+    prec = capi.FJ_PREC_FP32
+    palette = args.palette if args.palette is not None else spec.get("palette")
+    opts = dict(eps=EPS, omega=omega, precision=prec, schedule=args.schedule)
+    if palette is not None:
+        opts["palette"] = palette
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- training (outside the timed region): triples from the plain solver
+    t0 = time.perf_counter()
+    triples, graphs = [], []
+    for gd in W.warm_training_set():
+        if gd["directed"]:
+            a, b, ww = gd["src"], gd["dst"], gd["w"]
+        else:
+            a, b, ww = W.symmetrize_arcs(gd["src"], gd["dst"], None)
+        G = capi.Graph.from_arcs(gd["n"], torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev),
+                                 None if ww is None else torch.from_numpy(ww).to(dev), directed=gd["directed"])
+        graphs.append(G)
+        # targets: the plain solver (SOR only where it is safe, omega 1 on directed graphs)
+        topts = dict(opts, omega=1.0 if gd["directed"] else omega)
+        for sv in gd["S"]:
+            s_d = torch.from_numpy(sv).to(dev)
+            z_d, info, _ = G.solve(s_d, **topts)
+            triples.append((G, s_d, z_d))
+    net = capi.MPNN(capi.MPNN.initial_params(1))
+    losses = []
+    for it in range(spec["train_steps"]):
+        G, s_d, z_d = triples[it % len(triples)]
+        losses.append(net.train_step(G, s_d, z_d, spec["lr"]))
+    barrier()
+    train_s = time.perf_counter() - t0
+
+    # ---- held-out evaluation graph
+    _, g, src, dst, w = make_workload(args.workload)
+    n = g["n"]
+    G = capi.Graph.from_arcs(n, torch.from_numpy(src).to(dev), torch.from_numpy(dst).to(dev),
+                             torch.from_numpy(w).to(dev), directed=True)
+    ginfo = G.info()
+    k = spec["nvec"]
+    S = [torch.from_numpy(sv).to(dev) for sv in g["S"]]
+    z_d = torch.empty_like(S[0])
+    z0_d = torch.empty_like(S[0])
+
+    def warm_step(infos=None):
+        for s_d in S:
+            net.predict(G, s_d, out=z0_d)
+            _, inf, _ = G.solve(s_d, out=z_d, z0=z0_d, **opts)
+            if infos is not None:
+                infos.extend(inf)
+
+    def zero_step(infos=None):
+        for s_d in S:
+            _, inf, _ = G.solve(s_d, out=z_d, **opts)
+            if infos is not None:
+                infos.extend(inf)
+
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        barrier()
+        infos = []
+        ev0.record(stream)
+        for _ in range(args.steps):
+            fn(infos)
+        ev1.record(stream)
+        barrier()
+        ms = ev0.elapsed_time(ev1)
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, infos
+
+    ms_zero, inf_zero = timed(zero_step)
+    clk, clk_path = clocks_start() if rank == 0 else (None, None)
+    ms_warm, inf_warm = timed(warm_step)
+    clocks = clocks_stop(clk, clk_path, local) if rank == 0 else None
+    assert all(i["converged"] == 1 for i in inf_warm + inf_zero), "a timed solve did not certify"
+    value = world * args.steps * k / (ms_warm / 1e3)
+    zero_value = world * args.steps * k / (ms_zero / 1e3)
+    # predict time alone
+    barrier()
+    ev0.record(stream)
+    for s_d in S:
+        net.predict(G, s_d, out=z0_d)
+    ev1.record(stream)
+    barrier()
+    predict_ms = ev0.elapsed_time(ev1) / k
+
+    # end to end with host buffers through the C ABI: predict and warm solve per vector
+    s_pin = [torch.from_numpy(sv).pin_memory().numpy() for sv in g["S"]]
+    z0_pin = torch.empty(n, dtype=torch.float64).pin_memory().numpy()
+    z_pin = torch.empty(n, dtype=torch.float64).pin_memory().numpy()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for sp in s_pin:
+            net.predict(G, sp, out=z0_pin)
+            G.solve(sp, out=z_pin, z0=z0_pin, **opts)
+    barrier()
+    e2e_value = world * args.steps * k / (time.perf_counter() - t0)
+
+    _, pinfo, _ = G.solve(S[0], out=z_d, z0=z0_d, profile=1, **opts)
+    p = pinfo[0]
+    peak, peak_kind = measured_peak_hbm()
+    achieved = p["push_bytes"] / (p["push_ms"] / 1e3) / 1e9 if p["push_ms"] > 0 else None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None, "traffic": None,
+                "kernel": "k_products + k_sweep (one colour class)", "peak_source": peak_kind,
+                "bytes_per_launch": p["push_bytes"] / max(1, p["push_launches"]),
+                "avg_launch_us": 1e3 * p["push_ms"] / max(1, p["push_launches"])}
+    mean = lambda xs: float(np.mean(xs)) if xs else None
+    detail = {"zero_start_solves_per_s": zero_value, "warm_vs_zero": value / zero_value,
+              "sweeps_warm": mean([i["sweeps"] for i in inf_warm]),
+              "sweeps_zero": mean([i["sweeps"] for i in inf_zero]),
+              "predict_ms": predict_ms, "train_s": train_s, "train_steps": spec["train_steps"],
+              "train_loss_first": losses[0], "train_loss_last": float(np.mean(losses[-20:])),
+              "ncolours": ginfo["ncolours"], "vectors_per_step": k}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu_scale = args.cpu_scale if args.cpu_scale is not None else spec.get("cpu_scale")
+        dt, nnz_c, ok = oracle_solve_time(args.workload, cpu_scale, omega)
+        cpu = {"value": (nnz_c / ginfo["nnz"]) / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
+               "sample": (f"one FIFO ImprovedBLISOR solve (omega={omega}, eps={EPS}, FP64, zero start, one host "
+                          f"thread) of the same generator at scale {cpu_scale}, rate scaled by nnz "
+                          f"{nnz_c}/{ginfo['nnz']}, {dt:.1f} s")}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_warm / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "n": n, "nnz": ginfo["nnz"], "directed": True, "vectors": k,
+                       "palette": palette, "mode": "learned warm start (predict + fj_solve_warm)",
+                       "omega": omega, "eps": EPS, "precision": "FP32 push, FP64 estimate and certificate; "
+                       "network BF16 GEMMs with FP32 accumulation",
+                       "l2": "inputs larger than L2 (CSR %.2f GB)" % (ginfo["nnz"] * 8 / 1e9),
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": 24 * n * k,
+                    "d2h_bytes_per_step": 16 * n * k},
+            "gpu_launches": int(sum(i["launches"] for i in inf_warm)) + 6 * k * args.steps,
+            "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "detail": detail,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def run_ragged(args):
+    """Ragged batch: every graph of the batch solved (and its metrics taken) by one
+    solve over the block-diagonal handle; --plain-loop solves them one handle each."""
+    import torch
+
+    world, rank, local = dist_init()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2507_14864_gb300 import capi
+    from fjsynth import workloads as W
+
+    spec = WORKLOADS[args.workload]
+    dev = torch.device("cuda", local)
+    omega = args.omega if args.omega is not None else spec["omega"]
+    opts = dict(eps=EPS, omega=omega, precision=capi.FJ_PREC_FP32, schedule=args.schedule)
+    palette = args.palette if args.palette is not None else spec.get("palette")
+    if palette is not None:
+        opts["palette"] = palette
+    r = W.ragged_ba(spec["count"], spec["lo"], spec["hi"])
+    parts = []
+    for gr in r["graphs"]:
+        a, b, _ = W.symmetrize_arcs(gr["src"], gr["dst"])
+        parts.append((gr["n"], a, b, None))
+    s_host = np.concatenate([gr["s"] for gr in r["graphs"]])
+    ng = len(parts)
+    n = int(s_host.shape[0])
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    if args.plain_loop:
+        handles = [capi.Graph.from_arcs(pn, torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev), None,
+                                        directed=False) for pn, a, b, _ in parts]
+        svecs = [torch.from_numpy(gr["s"]).to(dev) for gr in r["graphs"]]
+        nnz = sum(h.info()["nnz"] for h in handles)
+
+        def step(infos=None):
+            for h, sv in zip(handles, svecs):
+                z, inf, _ = h.solve(sv, **opts)
+                h.metrics(sv, z)
+                if infos is not None:
+                    infos.extend(inf)
+        mode = "plain (one handle and one fj_solve per graph)"
+    else:
+        G = capi.Graph.ragged_from_arcs(parts, directed=False)
+        nnz = G.info()["nnz"]
+        s_d = torch.from_numpy(s_host).to(dev)
+        z_d = torch.empty_like(s_d)
+
+        def step(infos=None):
+            _, inf, _ = G.solve(s_d, out=z_d, **opts)
+            G.metrics(s_d, z_d)
+            if infos is not None:
+                infos.extend(inf)
+        mode = "ragged (one handle, one fj_solve for all graphs)"
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    clk, clk_path = clocks_start() if rank == 0 else (None, None)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    infos = []
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step(infos)
+    ev1.record(stream)
+    barrier()
+    clocks = clocks_stop(clk, clk_path, local) if rank == 0 else None
+    ms = ev0.elapsed_time(ev1)
+    assert all(i["converged"] == 1 for i in infos), "a timed solve did not certify"
+    value = world * args.steps * ng / (ms / 1e3)
+    e2e_value = None
+    if not args.plain_loop:
+        s_pin = torch.from_numpy(s_host).pin_memory().numpy()
+        z_pin = torch.empty(n, dtype=torch.float64).pin_memory().numpy()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            G.solve(s_pin, out=z_pin, **opts)
+            G.metrics(s_pin, z_pin)
+        barrier()
+        e2e_value = world * args.steps * ng / (time.perf_counter() - t0)
+        _, pinfo, _ = G.solve(s_d, out=z_d, profile=1, **opts)
+        p = pinfo[0]
+    else:
+        _, pinfo, _ = handles[-1].solve(svecs[-1], profile=1, **opts)
+        p = pinfo[0]
+    peak, peak_kind = measured_peak_hbm()
+    achieved = p["push_bytes"] / (p["push_ms"] / 1e3) / 1e9 if p["push_ms"] > 0 else None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None, "traffic": None,
+                "kernel": "k_products + k_sweep (one colour class)", "peak_source": peak_kind,
+                "bytes_per_launch": p["push_bytes"] / max(1, p["push_launches"]),
+                "avg_launch_us": 1e3 * p["push_ms"] / max(1, p["push_launches"])}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "graphs": ng, "n": n, "nnz": nnz, "directed": False,
+                       "mode": mode, "omega": omega, "eps": EPS, "palette": palette,
+                       "precision": "FP32 push, FP64 estimate, certificate and metrics",
+                       "l2": "inputs larger than L2", "parallelism": "replicas" if world > 1 else "single GPU"},
+            "e2e": None if e2e_value is None else {"value": e2e_value, "unit": "solves/s",
+                                                   "h2d_bytes_per_step": 24 * n, "d2h_bytes_per_step": 8 * n},
+            "gpu_launches": int(sum(i["launches"] for i in infos[::ng])) if not args.plain_loop else
+            int(sum(i["launches"] for i in infos)),
+            "roofline": roofline, "cpu_baseline": None, "clocks": clocks,
+            "detail": {"sweeps": max(i["sweeps"] for i in infos), "graphs_per_step": ng},
+        }
+        print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -355,6 +677,10 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if WORKLOADS[args.workload]["gen"] == "warm":
+        return run_warm(args)
+    if WORKLOADS[args.workload]["gen"] == "ragged":
+        return run_ragged(args)
     return run_gpu(args)
 
 

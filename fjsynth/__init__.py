@@ -65,6 +65,9 @@ def _lib():
         lib.fjs_loguniform_sizes.restype = ctypes.c_int
         lib.fjs_uniform.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64]
         lib.fjs_uniform.restype = ctypes.c_double
+        lib.fjs_uniform_fill.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,
+                                         ctypes.c_void_p]
+        lib.fjs_uniform_fill.restype = None
         lib.fjs_raw.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64]
         lib.fjs_raw.restype = ctypes.c_uint64
         _lib_handle = lib
@@ -74,6 +77,13 @@ def _lib():
 def uniform(seed: int, stream: int, ctr: int) -> float:
     """One draw U(seed, stream, ctr) in [0, 1) of the counter-based generator."""
     return _lib().fjs_uniform(seed, stream, ctr)
+
+
+def uniform_array(seed: int, stream: int, n: int, ctr0: int = 0) -> np.ndarray:
+    """U(seed, stream, ctr0 + i) for i < n (float64)."""
+    out = np.empty(n, np.float64)
+    _lib().fjs_uniform_fill(seed, stream, ctr0, n, out.ctypes.data)
+    return out
 
 
 def raw(seed: int, stream: int, ctr: int) -> int:

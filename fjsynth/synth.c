@@ -62,6 +62,13 @@ double fjs_uniform(uint64_t seed, uint64_t stream, uint64_t ctr)
     return fjs_u01(fjs_key(seed, stream), ctr);
 }
 
+/* out[i] = U(seed, stream, ctr0 + i) for i < n. */
+void fjs_uniform_fill(uint64_t seed, uint64_t stream, uint64_t ctr0, int64_t n, double *out)
+{
+    uint64_t key = fjs_key(seed, stream);
+    for (int64_t i = 0; i < n; ++i) out[i] = fjs_u01(key, ctr0 + (uint64_t)i);
+}
+
 /* ------------------------------------------------------------------ R-MAT */
 
 typedef struct {

@@ -11,7 +11,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import OP_ARCSINE, OP_BETA_MIX, OP_SIGN, OP_UNIFORM, ba, loguniform_sizes, opinions, rmat, sbm
+from . import OP_ARCSINE, OP_BETA_MIX, OP_SIGN, OP_UNIFORM, ba, loguniform_sizes, opinions, rmat, sbm, uniform_array
 
 BASE_SEED = 20250714
 
@@ -99,3 +99,27 @@ def symmetrize_arcs(src: np.ndarray, dst: np.ndarray, w=None):
         aw[0::2] = w
         aw[1::2] = w
     return asrc, adst, aw
+
+
+def warm_training_set(seed_off: int = 7, nvec: int = 3):
+    """Training graphs of the learned warm start: SBM and BA graphs with n from
+    10^4 to 10^6, nvec U[0,1] vectors each.  SBM graphs are undirected with
+    unit weights; BA graphs are directed, each edge oriented by a fair coin
+    and weighted U(0.5, 1.5) FP32, so the network also sees nodes that listen
+    to nobody, nodes nobody listens to, and weights."""
+    sizes = [10_000, 30_000, 100_000, 300_000, 1_000_000, 20_000, 60_000, 200_000]
+    out = []
+    for i, n in enumerate(sizes):
+        seed = BASE_SEED + seed_off + 104729 * (i + 1)
+        S = [_f32(opinions(n, OP_UNIFORM, seed + 1000, vec=k)) for k in range(nvec)]
+        if i % 2 == 0:
+            src, dst = sbm(n, 2 + i % 7, 12.0, 3.0, seed)
+            out.append(dict(name=f"sbm_n{n}", n=n, src=src, dst=dst, w=None, directed=False, S=S, fp32=True))
+        else:
+            a, b = ba(n, 5, seed)
+            flip = uniform_array(seed, 7, a.shape[0]) < 0.5
+            src = np.where(flip, b, a).astype(np.int32)
+            dst = np.where(flip, a, b).astype(np.int32)
+            w = (0.5 + uniform_array(seed, 8, a.shape[0])).astype(np.float32)
+            out.append(dict(name=f"ba_dir_n{n}", n=n, src=src, dst=dst, w=w, directed=True, S=S, fp32=True))
+    return out

@@ -124,6 +124,8 @@ typedef struct {
     int64_t frontier_rounds; /* FP64 frontier push rounds (scatter form) run on the few
                                 entries the certificate left above threshold */
     int64_t frontier_pushes; /* entries pushed by those rounds */
+    double omega_used;       /* relaxation factor of the reported solve: opts.omega, or 1
+                                after the FJ_SCHED_AUTO divergence fallback */
 } fj_solve_info;
 
 /* The measures of Table 1 (Section 3.4). */
@@ -209,6 +211,12 @@ fj_status fj_graph_colour(fj_graph *g, int palette, int32_t *colour, int *ncolou
 
 /*
  * fj_solve - ImprovedBLISOR (Alg. 3 with the shift of Alg. 2) on the GPU.
+ * Under opts->schedule == FJ_SCHED_AUTO a solve whose residual becomes
+ * non-finite with omega > 1 (the multicolour SOR is only proven for
+ * symmetric systems, Section 5.2; directed graphs can diverge) is restarted
+ * with omega = 1 (Gauss-Seidel on the diagonally dominant I + L, which
+ * converges); info.omega_used reports the factor of the returned solve.
+ * An explicit schedule returns FJ_ERR_DIVERGED instead.
  * s[n] (FP64) innate opinions; z_out[n] (FP64) receives
  * zhat = (push estimate of (I+L)^{-1}(s + c_eff)) - c_eff.  On FJ_OK every
  * node meets the FP64 certificate |r_v| <= max(eps' s'_v, 2^-51 (1 + d_v)
@@ -248,12 +256,42 @@ fj_status fj_solve_batch(fj_graph *g, const double *S, int k, const fj_solve_opt
                          double *Z_out, fj_solve_info *info, int mem);
 
 /*
+ * fj_graph_tune - autotuner for fj_solve on this graph.  Times complete,
+ * certified solves of s (reps timed calls after one untimed call each, CUDA
+ * events on base->stream) for every candidate: Jacobi rounds at omega 1, and
+ * the multicolour schedule for palette K in {4, 8, 16, 32} x omega in {1.2,
+ * 1.5, 1.8}.  *best receives base with the schedule, palette and omega of the
+ * fastest (its colouring is left built on the handle); *best_ms (may be NULL)
+ * its mean time.  Costs one colouring per palette and 13 (reps + 1) solves.
+ * FJ_ERR_NOT_CONVERGED when no candidate certifies.
+ */
+fj_status fj_graph_tune(fj_graph *g, const double *s, const fj_solve_opts *base, int reps,
+                        fj_solve_opts *best, double *best_ms, int mem);
+
+/*
+ * fj_graph_tune_batch - as fj_graph_tune for fj_solve_batch on S[n][k], with
+ * one more dimension: the number of k-vector gathers each warp keeps in
+ * flight (4 or 8).  The best depth stays on the handle for later batch solves.
+ */
+fj_status fj_graph_tune_batch(fj_graph *g, const double *S, int k, const fj_solve_opts *base, int reps,
+                              fj_solve_opts *best, double *best_ms, int mem);
+
+/*
  * fj_metrics - P, D, I, C and mean z of Table 1 for opinions s[n] and
  * equilibrium z[n] (FP64), summed in FP64 in a fixed order (deterministic).
  * out gets one record per graph (ngraphs for a ragged handle).
  */
 fj_status fj_metrics(fj_graph *g, const double *s, const double *z, fj_metrics_out *out, int mem,
                      void *stream);
+
+/*
+ * fj_metrics_batch - the measures of fj_metrics for k opinion vectors at once:
+ * S and Z node-major [n][k] (FP64, element (v, j) at v*k + j), 1 <= k <= 64,
+ * out[k] one record per vector.  FP64 sums in a fixed order (deterministic).
+ * A ragged handle is rejected (use fj_metrics).
+ */
+fj_status fj_metrics_batch(fj_graph *g, const double *S, const double *Z, int k, fj_metrics_out *out, int mem,
+                           void *stream);
 
 /*
  * fj_frontier - the push frontier F = {v : |r_v| > h_v} (strict test of Alg. 1
@@ -325,9 +363,11 @@ fj_status fj_mpnn_get_params(const fj_mpnn *m, float *params);
 fj_status fj_mpnn_set_params(fj_mpnn *m, const float *params);
 
 /*
- * fj_mpnn_predict - z0[n] (FP64) for opinions s[n] (FP64) on graph g, clamped
- * to [min s, max s] (where z lies, Section 3.2).  Host or device pointers per
- * mem.  A ragged handle is treated as one graph (clamp to the global range).
+ * fj_mpnn_predict - z0[n] (FP64) for opinions s[n] (FP64) on graph g: the
+ * network's output clamped to [min s, max s] (where z lies, Section 3.2),
+ * except that a node with d_v = 0 (it listens to nobody) takes s_v, its exact
+ * equilibrium value.  Host or device pointers per mem.  A ragged handle is
+ * treated as one graph (clamp to the global range).
  */
 fj_status fj_mpnn_predict(fj_mpnn *m, fj_graph *g, const double *s, double *z0, int mem, void *stream);
 

@@ -25,8 +25,8 @@ EXPORTED = [
     "fj_solve_opts_default", "fj_status_string", "fj_last_error", "fj_graph_create",
     "fj_graph_create_from_arcs", "fj_graph_create_ragged", "fj_graph_destroy", "fj_graph_info",
     "fj_graph_export", "fj_graph_colour", "fj_solve", "fj_solve_warm", "fj_solve_batch",
-    "fj_metrics", "fj_frontier", "fj_frontier_static", "fj_residual",
-    "fj_mpnn_param_count", "fj_mpnn_create", "fj_mpnn_destroy", "fj_mpnn_get_params", "fj_mpnn_set_params",
+    "fj_metrics", "fj_metrics_batch", "fj_frontier", "fj_frontier_static", "fj_residual",
+    "fj_graph_tune", "fj_graph_tune_batch", "fj_mpnn_param_count", "fj_mpnn_create", "fj_mpnn_destroy", "fj_mpnn_get_params", "fj_mpnn_set_params",
     "fj_mpnn_predict", "fj_mpnn_grad", "fj_mpnn_adam_step",
 ]
 
@@ -45,7 +45,7 @@ class fj_solve_info(ctypes.Structure):
                 ("resid_rel_max", ctypes.c_double), ("z_inf", ctypes.c_double), ("err_bound", ctypes.c_double),
                 ("launches", ctypes.c_int64), ("push_launches", ctypes.c_int64), ("push_ms", ctypes.c_double),
                 ("push_bytes", ctypes.c_double), ("frontier_rounds", ctypes.c_int64),
-                ("frontier_pushes", ctypes.c_int64)]
+                ("frontier_pushes", ctypes.c_int64), ("omega_used", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -92,6 +92,11 @@ def lib():
     L.fj_solve_warm.argtypes = [VP, VP, VP, ctypes.POINTER(fj_solve_opts), VP, VP, I32]
     L.fj_solve_batch.argtypes = [VP, VP, I32, ctypes.POINTER(fj_solve_opts), VP, VP, I32]
     L.fj_metrics.argtypes = [VP, VP, VP, VP, I32, VP]
+    L.fj_graph_tune.argtypes = [VP, VP, ctypes.POINTER(fj_solve_opts), I32, ctypes.POINTER(fj_solve_opts),
+                                ctypes.POINTER(D), I32]
+    L.fj_graph_tune_batch.argtypes = [VP, VP, I32, ctypes.POINTER(fj_solve_opts), I32,
+                                      ctypes.POINTER(fj_solve_opts), ctypes.POINTER(D), I32]
+    L.fj_metrics_batch.argtypes = [VP, VP, VP, I32, VP, I32, VP]
     L.fj_frontier.argtypes = [I64, VP, VP, I32, VP, VP, VP]
     L.fj_frontier_static.argtypes = [I64, VP, VP, I32, VP, VP, VP]
     L.fj_residual.argtypes = [VP, VP, VP, D, VP, I32, VP]
@@ -107,7 +112,7 @@ def lib():
     L.fj_mpnn_adam_step.argtypes = [VP, D, VP]
     for name in EXPORTED:
         if name not in ("fj_solve_opts_default", "fj_graph_destroy", "fj_status_string", "fj_last_error",
-                        "fj_mpnn_param_count", "fj_mpnn_destroy"):
+                        "fj_graph_tune", "fj_graph_tune_batch", "fj_mpnn_param_count", "fj_mpnn_destroy"):
             getattr(L, name).restype = st
     _lib = L
     return L
@@ -213,6 +218,30 @@ class Graph:
         return cls(h.value)
 
     @classmethod
+    def ragged_from_arcs(cls, graphs, directed=False):
+        """A ragged handle from per-graph arc lists [(n, src, dst, w or None), ...] (host
+        arrays): each graph goes through the library's own ingest (keep-first dedup,
+        self-loops dropped) and export, then the CSRs are laid out block-diagonally."""
+        rps, cols, ws, offs = [], [], [], [0]
+        nnz_at = 0
+        weighted = any(g[3] is not None for g in graphs)
+        for n, src, dst, w in graphs:
+            one = cls.from_arcs(n, np.ascontiguousarray(src, np.int32), np.ascontiguousarray(dst, np.int32),
+                                None if w is None else np.ascontiguousarray(w, np.float32), directed=directed)
+            rp, col, wc, _ = one.export(weights=weighted)
+            one.close()
+            rps.append(rp[1:] + nnz_at)
+            cols.append(col + offs[-1])
+            if weighted:
+                ws.append(wc)
+            nnz_at += int(rp[-1])
+            offs.append(offs[-1] + int(n))
+        row_ptr = np.concatenate([np.zeros(1, np.int64)] + rps).astype(np.int64)
+        col = np.concatenate(cols).astype(np.int32)
+        w = np.concatenate(ws).astype(np.float32) if weighted else None
+        return cls.ragged(np.array(offs, np.int64), row_ptr, col, w, directed=directed)
+
+    @classmethod
     def ragged(cls, node_offsets, row_ptr, col, w=None, directed=False, stream=None):
         mem = _mem_of(node_offsets, row_ptr, col, w)
         h = ctypes.c_void_p()
@@ -316,6 +345,35 @@ class Graph:
         res = [m.as_dict() for m in outs]
         return res[0] if ng == 1 else res
 
+    def tune(self, s, reps=2, **opts):
+        """fj_graph_tune: the fastest certified (schedule, palette, omega) for s.
+        Returns (dict of solve options to pass to solve(), mean ms)."""
+        base = default_opts(**opts)
+        best = fj_solve_opts()
+        ms = ctypes.c_double()
+        _check(lib().fj_graph_tune(self._h, _ptr(s, np.float64), ctypes.byref(base), int(reps), ctypes.byref(best),
+                                   ctypes.byref(ms), _mem_of(s)), "fj_graph_tune")
+        return {"schedule": best.schedule, "palette": best.palette, "omega": best.omega}, ms.value
+
+    def tune_batch(self, S, reps=1, **opts):
+        """fj_graph_tune_batch; the chosen gather depth stays on the handle."""
+        base = default_opts(**opts)
+        best = fj_solve_opts()
+        ms = ctypes.c_double()
+        _check(lib().fj_graph_tune_batch(self._h, _ptr(S, np.float64), int(S.shape[1]), ctypes.byref(base),
+                                         int(reps), ctypes.byref(best), ctypes.byref(ms), _mem_of(S)),
+               "fj_graph_tune_batch")
+        return {"schedule": best.schedule, "palette": best.palette, "omega": best.omega}, ms.value
+
+    def metrics_batch(self, S, Z):
+        """fj_metrics_batch on node-major S, Z [n, k]: one dict per vector."""
+        k = int(S.shape[1])
+        outs = (fj_metrics_out * k)()
+        mem = _mem_of(S, Z)
+        _check(lib().fj_metrics_batch(self._h, _ptr(S, np.float64), _ptr(Z, np.float64), k, outs, mem,
+                                      current_stream()), "fj_metrics_batch")
+        return [m.as_dict() for m in outs]
+
     def residual(self, s, z, c_eff):
         mem = _mem_of(s, z)
         if mem == FJ_MEM_DEVICE:
@@ -358,6 +416,20 @@ class MPNN:
     @staticmethod
     def param_count() -> int:
         return int(lib().fj_mpnn_param_count())
+
+    @classmethod
+    def initial_params(cls, seed: int = 0) -> np.ndarray:
+        """A start for training: each weight matrix uniform in +-1/sqrt(2 F_in)
+        (F_in = 4, 64, 64), zero biases, head weights uniform in +-1/8."""
+        rng = np.random.default_rng(seed)
+        parts = []
+        for fin in (4, 64, 64):
+            lim = 1.0 / np.sqrt(2 * fin)
+            parts += [rng.uniform(-lim, lim, fin * 64), rng.uniform(-lim, lim, fin * 64), np.zeros(64)]
+        parts += [rng.uniform(-0.125, 0.125, 64), np.zeros(1)]
+        p = np.concatenate(parts).astype(np.float32)
+        assert p.shape[0] == cls.param_count()
+        return p
 
     def close(self):
         if self._h and self._h.value:

@@ -1032,10 +1032,24 @@ struct SegStartPred {
     }
 };
 
-__global__ void k_colour_keys(int64_t n, const int32_t *__restrict__ colour, uint32_t *__restrict__ key)
+// Sort key of the colour permutation: the colour, and when indeg is given,
+// below it the in-degree descending (22 bits, clamped), so that inside a
+// class the nodes most rows gather from sit together (their increments share
+// cache sectors); ties keep id order (the sort is stable).
+constexpr int kDegKeyBits = 22;
+
+__global__ void k_colour_keys(int64_t n, const int32_t *__restrict__ colour, const int32_t *__restrict__ indeg,
+                              uint32_t *__restrict__ key)
 {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        key[i] = (uint32_t)colour[i];
+    constexpr uint32_t dmax = (1u << kDegKeyBits) - 1u;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (!indeg) {
+            key[i] = (uint32_t)colour[i];
+        } else {
+            const uint32_t d = (uint32_t)min(max(indeg[i], 0), (int32_t)dmax);
+            key[i] = ((uint32_t)colour[i] << kDegKeyBits) | (dmax - d);
+        }
+    }
 }
 
 static fj_status colour_graph(fj_graph *g, int palette, cudaStream_t st)
@@ -1183,19 +1197,22 @@ fj_status ensure_colouring(fj_graph *g, int palette, cudaStream_t st)
     FJ_CUDA(dalloc(&v0, n));
     FJ_CUDA(dalloc(&k1, n));
     FJ_CUDA(dalloc(&v1, n));
-    k_colour_keys<<<grid_for(n, 256), 256, 0, st>>>(n, cl.colour, k0);
+    // in-degree order inside classes: one graph and a bounded palette (colours
+    // then fit the key's top 10 bits)
+    const bool deg_key = g->ngraphs == 1 && palette > 0 && palette <= 1024;
+    k_colour_keys<<<grid_for(n, 256), 256, 0, st>>>(n, cl.colour, deg_key ? c.indeg : nullptr, k0);
     k_iota<<<grid_for(n, 256), 256, 0, st>>>(n, v0);
     FJ_CUDA(cudaGetLastError());
     bool in1 = false;
     FJ_CUDA(sort_pairs(n, 32, k0, v0, k1, v1, g->sort, g->err, st, &in1));
     uint32_t *sk = in1 ? k1 : k0, *sv = in1 ? v1 : v0;
     // class boundaries from the sorted colours
-    int32_t maxc = 0;
-    FJ_CUDA(cudaMemcpyAsync(&maxc, sk + (n - 1), sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    FJ_CUDA(cudaStreamSynchronize(st));
-    cl.ncolours = maxc + 1;
+    const int kshift = deg_key ? kDegKeyBits : 0;
     std::vector<uint32_t> hk((size_t)n);
-    FJ_CUDA(cudaMemcpy(hk.data(), sk, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost));
+    FJ_CUDA(cudaMemcpyAsync(hk.data(), sk, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, st));
+    FJ_CUDA(cudaStreamSynchronize(st));
+    for (auto &x : hk) x >>= kshift;
+    cl.ncolours = (int)hk[(size_t)n - 1] + 1;
     cl.class_row.assign((size_t)cl.ncolours + 1, n);
     cl.class_row[0] = 0;
     for (int64_t i = 1; i < n; ++i)

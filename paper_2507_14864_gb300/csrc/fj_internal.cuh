@@ -141,6 +141,7 @@ struct BatchWorkspace {
     int64_t cap_partk = 0;
     unsigned int *tick = nullptr;  // per colour class: next tile, retired warps
     int64_t cap_tick = 0;
+    int depth = 4;                 // k-vector gathers in flight per warp (4 or 8; fj_graph_tune_batch)
 };
 
 }  // namespace fj
@@ -173,6 +174,8 @@ fj_status build_blocks(DevCSR &c, const std::vector<int64_t> &seg_rows, Workspac
                        cudaStream_t st, bool warp_tiles);
 fj_status ensure_colouring(fj_graph *g, int palette, cudaStream_t st);
 fj_status ensure_ptranspose(fj_graph *g, cudaStream_t st);
+// fj_solve.cu
+fj_status plain_items(fj_graph *g, cudaStream_t st, const ItemPlan **out);
 fj_status ws_status(Workspace &ws, int64_t tiles);
 fj_status read_dev_error(fj_graph *g, cudaStream_t st);
 void dev_free(void *p);

@@ -106,6 +106,81 @@ __global__ void k_metric_mean_div(int ng, const int64_t *__restrict__ node_off, 
     if (gi < ng) mean[gi] /= (double)(node_off[gi + 1] - node_off[gi]);
 }
 
+// Multi-vector measures: S and Z node-major [n][k], k <= 64.  Lanes own
+// vectors j = lane and lane + 32; warps take rows with a fixed stride, so every
+// partial sum has a fixed order.  Pass 1: sum z per vector.  Pass 2: C, P, I
+// and the arc sum of a (z_x - z_c)^2.  Partials per block, reduced in block
+// order by k_metric_batch_reduce.
+constexpr int kMetricBatchBlocks = 152 * 4;
+
+template <bool W>
+__global__ void __launch_bounds__(256)
+k_metric_batch(int pass, int64_t n, int k, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+               const float *__restrict__ w, const double *__restrict__ S, const double *__restrict__ Z,
+               const double *__restrict__ mean, double *__restrict__ part)
+{
+    __shared__ double red[8][4][64];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int64_t warp = (int64_t)blockIdx.x * 8 + wl, nwarps = (int64_t)gridDim.x * 8;
+    const bool has[2] = {lane < k, lane + 32 < k};
+    double acc[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+    double mu[2] = {0, 0};
+    if (pass == 2)
+        for (int hh = 0; hh < 2; ++hh)
+            if (has[hh]) mu[hh] = mean[lane + 32 * hh];
+    for (int64_t x = warp; x < n; x += nwarps) {
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+            if (!has[hh]) continue;
+            const int j = lane + 32 * hh;
+            const double zx = Z[x * k + j];
+            if (pass == 1) {
+                acc[hh][0] += zx;
+            } else {
+                const double sx = S[x * k + j];
+                acc[hh][0] += zx * zx;
+                acc[hh][1] += (zx - mu[hh]) * (zx - mu[hh]);
+                acc[hh][2] += (zx - sx) * (zx - sx);
+                double dd = 0.0;
+                for (int64_t kk = rp[x]; kk < rp[x + 1]; ++kk) {
+                    const double d = zx - Z[(int64_t)col[kk] * k + j];
+                    dd += (W ? (double)w[kk] : 1.0) * d * d;
+                }
+                acc[hh][3] += dd;
+            }
+        }
+    }
+    const int nf = pass == 1 ? 1 : 4;
+    for (int hh = 0; hh < 2; ++hh)
+        for (int f = 0; f < nf; ++f) red[wl][f][lane + 32 * hh] = acc[hh][f];
+    __syncthreads();
+    for (int i = threadIdx.x; i < nf * 64; i += 256) {
+        const int f = i / 64, j = i % 64;
+        if (j >= k) continue;
+        double t = 0.0;
+        for (int ww = 0; ww < 8; ++ww) t += red[ww][f][j];
+        part[((int64_t)blockIdx.x * nf + f) * k + j] = t;
+    }
+}
+
+// out[f * k + j] = sum over blocks (in order) of part[b][f][j].
+__global__ void k_metric_batch_reduce(int nblocks, int nf, int k, const double *__restrict__ part,
+                                      double *__restrict__ out)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nf * k; i += gridDim.x * blockDim.x) {
+        const int f = i / k, j = i % k;
+        double t = 0.0;
+        for (int b = 0; b < nblocks; ++b) t += part[((int64_t)b * nf + f) * k + j];
+        out[i] = t;
+    }
+}
+
+__global__ void k_metric_batch_mean(int k, int64_t n, double *__restrict__ m)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < k) m[j] /= (double)n;
+}
+
 }  // namespace fj
 
 using namespace fj;
@@ -173,3 +248,52 @@ extern "C" fj_status fj_metrics(fj_graph *g, const double *s, const double *z, f
     return FJ_OK;
 }
 
+extern "C" fj_status fj_metrics_batch(fj_graph *g, const double *S, const double *Z, int k, fj_metrics_out *out,
+                                      int mem, void *stream)
+{
+    FJ_ARG(g != nullptr, "graph is NULL");
+    FJ_ARG(S && Z && out, "NULL pointer");
+    FJ_ARG(k >= 1 && k <= 64, "k must be in 1..64");
+    FJ_ARG(mem == FJ_MEM_HOST || mem == FJ_MEM_DEVICE, "mem must be FJ_MEM_HOST or FJ_MEM_DEVICE");
+    FJ_ARG(g->ngraphs == 1, "a ragged handle takes fj_metrics");
+    cudaStream_t st = (cudaStream_t)stream;
+    const DevCSR &c = g->csr;
+    const int64_t n = c.n;
+    const int nb = kMetricBatchBlocks;
+    size_t bytes = sizeof(double) * ((size_t)nb * 4 * k + 5 * (size_t)k);
+    if (mem == FJ_MEM_HOST) bytes += sizeof(double) * 2 * (size_t)n * k;
+    char *buf = nullptr;
+    FJ_CUDA(cudaMallocAsync(&buf, bytes, st));
+    double *part = reinterpret_cast<double *>(buf);
+    double *mean = part + (size_t)nb * 4 * k;
+    double *res = mean + k;
+    const double *Sd = S, *Zd = Z;
+    if (mem == FJ_MEM_HOST) {
+        double *stage = res + 4 * k;
+        FJ_CUDA(cudaMemcpyAsync(stage, S, sizeof(double) * n * k, cudaMemcpyHostToDevice, st));
+        FJ_CUDA(cudaMemcpyAsync(stage + n * k, Z, sizeof(double) * n * k, cudaMemcpyHostToDevice, st));
+        Sd = stage;
+        Zd = stage + n * k;
+    }
+    if (c.w) k_metric_batch<true><<<nb, 256, 0, st>>>(1, n, k, c.row_ptr, c.col, c.w, Sd, Zd, mean, part);
+    else k_metric_batch<false><<<nb, 256, 0, st>>>(1, n, k, c.row_ptr, c.col, c.w, Sd, Zd, mean, part);
+    k_metric_batch_reduce<<<1, 64, 0, st>>>(nb, 1, k, part, mean);
+    k_metric_batch_mean<<<1, 64, 0, st>>>(k, n, mean);
+    if (c.w) k_metric_batch<true><<<nb, 256, 0, st>>>(2, n, k, c.row_ptr, c.col, c.w, Sd, Zd, mean, part);
+    else k_metric_batch<false><<<nb, 256, 0, st>>>(2, n, k, c.row_ptr, c.col, c.w, Sd, Zd, mean, part);
+    k_metric_batch_reduce<<<1, 256, 0, st>>>(nb, 4, k, part, res);
+    FJ_CUDA(cudaGetLastError());
+    std::vector<double> hres((size_t)4 * k), hmean((size_t)k);
+    FJ_CUDA(cudaMemcpyAsync(hres.data(), res, sizeof(double) * 4 * k, cudaMemcpyDeviceToHost, st));
+    FJ_CUDA(cudaMemcpyAsync(hmean.data(), mean, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+    FJ_CUDA(cudaFreeAsync(buf, st));
+    FJ_CUDA(cudaStreamSynchronize(st));
+    for (int j = 0; j < k; ++j) {
+        out[j].C = hres[(size_t)0 * k + j];
+        out[j].P = hres[(size_t)1 * k + j];
+        out[j].I = hres[(size_t)2 * k + j];
+        out[j].D = g->directed ? hres[(size_t)3 * k + j] : 0.5 * hres[(size_t)3 * k + j];
+        out[j].mean_z = hmean[(size_t)j];
+    }
+    return FJ_OK;
+}

@@ -12,10 +12,13 @@
 //   forward   D[128 nodes][64]   = [h | g] (K = 2 F_in, padded to 16) x W^T
 //   backward  D[128 nodes][128]  = dq (K = 64) x [Ws | Wn]^T   (dh_self, dg)
 //             D[128 feat][64]   += X^T dq over chunks of 128 nodes  (dW)
-// with dq = bf16(dh * [h > 0]).  Aggregations (g and its adjoint) are
-// warp-per-node gathers in FP32.  Parameters are FP32 (Adam state too); the
-// GEMMs read BF16 copies packed once per update into the exact shared-memory
-// image of their B operand.
+// with dq = bf16(dh * [h > 0]).  The aggregations (m, g and the adjoint of g)
+// run over the graph's warp-tile plan (tiles of at most 64 rows and 512
+// nonzeros, longer rows cut into 512-nonzero chunks), so a hub with 10^5
+// neighbours is spread over many warps instead of serialising one; sums are
+// FP32 (FP64 for m).  Parameters are FP32 (Adam state too); the GEMMs read
+// BF16 copies packed once per update into the exact shared-memory image of
+// their B operand.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -84,30 +87,346 @@ __global__ void k_pack_bwd(const float *__restrict__ theta, int ws, int fin, __n
     }
 }
 
-// ---------------------------------------------------------------- features
+// ---------------------------------------------------------------- aggregation over the warp-tile plan
 
-// x_v in BF16 (4 per node); thread per node.
-__global__ void k_features(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
-                           const float *__restrict__ w, const double *__restrict__ deg,
-                           const int32_t *__restrict__ indeg, const double *__restrict__ s,
-                           __nv_bfloat16 *__restrict__ x, int *err)
+constexpr int kShortAgg = 8;  // rows of at most this many nonzeros are summed by one lane
+
+// m_v = sum_j a_vj s_j / d_v (FP64; 0 when d_v = 0).  Short rows one lane
+// each, longer rows the whole warp; a chunk of a long row leaves its partial
+// sum in part[] and the last chunk to finish completes the row.
+__global__ void __launch_bounds__(256)
+k_agg_s(const Item *__restrict__ items, int64_t nitems, const int64_t *__restrict__ rp,
+        const int32_t *__restrict__ col, const float *__restrict__ w, const double *__restrict__ deg,
+        const double *__restrict__ s, double *__restrict__ m, double *part, int32_t *cnt,
+        const int32_t *__restrict__ slot_first, const int32_t *__restrict__ slot_nchunk, int64_t n, int *err)
+{
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    auto term = [&](int64_t k) -> double {
+        const int32_t j = col[k];
+        if (j < 0 || j >= n) {
+            dev_error(err, DEV_BAD_COL);
+            return 0.0;
+        }
+        return (w ? (double)w[k] : 1.0) * s[j];
+    };
+    auto finish = [&](int64_t x, double acc) {
+        const double d = deg[x];
+        m[x] = d > 0.0 ? acc / d : 0.0;
+    };
+    for (int64_t ii = warp; ii < nitems; ii += nwarps) {
+        const Item it = items[ii];
+        const int64_t r0 = it.r0, r1 = it.r1;
+        if (r0 < 0 || r1 > n || r0 >= r1) continue;
+        if (it.slot < 0) {
+            for (int half = 0; half < 2; ++half) {
+                const int64_t x = r0 + lane + 32 * half;
+                const bool mine = x < r1;
+                int64_t a = 0, e = 0;
+                if (mine) {
+                    a = rp[x];
+                    e = rp[x + 1];
+                }
+                const bool shortrow = mine && e - a <= kShortAgg;
+                if (shortrow) {
+                    double acc = 0.0;
+                    for (int64_t k = a; k < e; ++k) acc += term(k);
+                    finish(x, acc);
+                }
+                unsigned longs = __ballot_sync(FULL, mine && !shortrow);
+                while (longs) {
+                    const int src = __ffs(longs) - 1;
+                    longs &= longs - 1;
+                    const int64_t al = __shfl_sync(FULL, a, src), el = __shfl_sync(FULL, e, src);
+                    double acc = 0.0;
+                    for (int64_t k = al + lane; k < el; k += 32) acc += term(k);
+                    acc = warp_sum(acc);
+                    if (lane == 0) finish(r0 + src + 32 * half, acc);
+                }
+            }
+        } else {
+            double acc = 0.0;
+            for (int64_t k = it.k0 + lane; k < it.k1; k += 32) acc += term(k);
+            acc = warp_sum(acc);
+            const int slot = it.slot, first = slot_first[slot], nch = slot_nchunk[slot];
+            const int ci = (int)((it.k0 - rp[r0]) / kWarpChunk);
+            if (lane == 0) {
+                part[first + ci] = acc;
+                __threadfence();
+                if (atomicAdd(&cnt[slot], 1) == nch - 1) {
+                    __threadfence();
+                    double t = 0.0;
+                    for (int c = 0; c < nch; ++c) t += __ldcg(part + first + c);
+                    cnt[slot] = 0;
+                    finish(r0, t);
+                }
+            }
+        }
+    }
+}
+
+// x_v in BF16 (4 per node) from s, the degrees and m.
+__global__ void k_features(int64_t n, const double *__restrict__ deg, const int32_t *__restrict__ indeg,
+                           const double *__restrict__ s, const double *__restrict__ m, __nv_bfloat16 *__restrict__ x)
 {
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-        double acc = 0.0;
-        for (int64_t k = rp[v]; k < rp[v + 1]; ++k) {
-            const int32_t j = col[k];
-            if (j < 0 || j >= n) {
-                dev_error(err, DEV_BAD_COL);
-                continue;
-            }
-            acc += (w ? (double)w[k] : 1.0) * s[j];
-        }
-        const double d = deg[v];
-        const double m = d > 0.0 ? acc / d : 0.0;
         x[4 * v + 0] = __float2bfloat16_rn((float)s[v]);
-        x[4 * v + 1] = __float2bfloat16_rn((float)log1p(d));
+        x[4 * v + 1] = __float2bfloat16_rn((float)log1p(deg[v]));
         x[4 * v + 2] = __float2bfloat16_rn((float)log1p((double)indeg[v]));
-        x[4 * v + 3] = __float2bfloat16_rn((float)m);
+        x[4 * v + 3] = __float2bfloat16_rn((float)m[v]);
+    }
+}
+
+// g_v = sum_j a_vj x_j / d_v for 4-wide BF16 rows (FP32 sums), layout as k_agg_s.
+__global__ void __launch_bounds__(256)
+k_agg4(const Item *__restrict__ items, int64_t nitems, const int64_t *__restrict__ rp,
+       const int32_t *__restrict__ col, const float *__restrict__ w, const double *__restrict__ deg,
+       const __nv_bfloat16 *__restrict__ x, __nv_bfloat16 *__restrict__ g, float *part, int32_t *cnt,
+       const int32_t *__restrict__ slot_first, const int32_t *__restrict__ slot_nchunk, int64_t n, int *err)
+{
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    auto add = [&](int64_t k, float (&acc)[4]) {
+        const int32_t j = col[k];
+        if (j < 0 || j >= n) {
+            dev_error(err, DEV_BAD_COL);
+            return;
+        }
+        const float a = w ? w[k] : 1.f;
+        const uint2 raw = *reinterpret_cast<const uint2 *>(x + 4 * (int64_t)j);
+        const float2 p = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&raw.x));
+        const float2 q = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&raw.y));
+        acc[0] += a * p.x;
+        acc[1] += a * p.y;
+        acc[2] += a * q.x;
+        acc[3] += a * q.y;
+    };
+    auto finish = [&](int64_t v, const float (&acc)[4]) {
+        const double d = deg[v];
+        const float inv = d > 0.0 ? (float)(1.0 / d) : 0.f;
+        __nv_bfloat162 lo = __floats2bfloat162_rn(acc[0] * inv, acc[1] * inv);
+        __nv_bfloat162 hi = __floats2bfloat162_rn(acc[2] * inv, acc[3] * inv);
+        uint2 raw;
+        raw.x = *reinterpret_cast<unsigned *>(&lo);
+        raw.y = *reinterpret_cast<unsigned *>(&hi);
+        *reinterpret_cast<uint2 *>(g + 4 * v) = raw;
+    };
+    for (int64_t ii = warp; ii < nitems; ii += nwarps) {
+        const Item it = items[ii];
+        const int64_t r0 = it.r0, r1 = it.r1;
+        if (r0 < 0 || r1 > n || r0 >= r1) continue;
+        if (it.slot < 0) {
+            for (int half = 0; half < 2; ++half) {
+                const int64_t xr = r0 + lane + 32 * half;
+                const bool mine = xr < r1;
+                int64_t a = 0, e = 0;
+                if (mine) {
+                    a = rp[xr];
+                    e = rp[xr + 1];
+                }
+                const bool shortrow = mine && e - a <= kShortAgg;
+                if (shortrow) {
+                    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+                    for (int64_t k = a; k < e; ++k) add(k, acc);
+                    finish(xr, acc);
+                }
+                unsigned longs = __ballot_sync(FULL, mine && !shortrow);
+                while (longs) {
+                    const int src = __ffs(longs) - 1;
+                    longs &= longs - 1;
+                    const int64_t al = __shfl_sync(FULL, a, src), el = __shfl_sync(FULL, e, src);
+                    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+                    for (int64_t k = al + lane; k < el; k += 32) add(k, acc);
+#pragma unroll
+                    for (int f = 0; f < 4; ++f) acc[f] = warp_sum(acc[f]);
+                    if (lane == 0) finish(r0 + src + 32 * half, acc);
+                }
+            }
+        } else {
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int64_t k = it.k0 + lane; k < it.k1; k += 32) add(k, acc);
+#pragma unroll
+            for (int f = 0; f < 4; ++f) acc[f] = warp_sum(acc[f]);
+            const int slot = it.slot, first = slot_first[slot], nch = slot_nchunk[slot];
+            const int ci = (int)((it.k0 - rp[r0]) / kWarpChunk);
+            if (lane == 0) {
+                for (int f = 0; f < 4; ++f) part[(int64_t)(first + ci) * 4 + f] = acc[f];
+                __threadfence();
+                if (atomicAdd(&cnt[slot], 1) == nch - 1) {
+                    __threadfence();
+                    float t[4] = {0.f, 0.f, 0.f, 0.f};
+                    for (int c = 0; c < nch; ++c)
+                        for (int f = 0; f < 4; ++f) t[f] += __ldcg(part + (int64_t)(first + c) * 4 + f);
+                    cnt[slot] = 0;
+                    finish(r0, t);
+                }
+            }
+        }
+    }
+}
+
+// g_v = sum_j a_vj h_j / d_v for 64-wide BF16 rows: one warp per tile, lane l
+// owns features 2l and 2l + 1; the tile's columns and weights are read 32 at a
+// time and broadcast, eight row gathers are in flight; rows complete as the
+// walk passes their ends.  A chunk of a long row leaves 64 FP32 partials.
+__global__ void __launch_bounds__(256)
+k_agg64(const Item *__restrict__ items, int64_t nitems, const int64_t *__restrict__ rp,
+        const int32_t *__restrict__ col, const float *__restrict__ w, const double *__restrict__ deg,
+        const __nv_bfloat16 *__restrict__ h, __nv_bfloat16 *__restrict__ g, float *part, int32_t *cnt,
+        const int32_t *__restrict__ slot_first, const int32_t *__restrict__ slot_nchunk, int64_t n, int *err)
+{
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr int D = 8;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const __nv_bfloat162 *h2 = reinterpret_cast<const __nv_bfloat162 *>(h);
+    for (int64_t ii = warp; ii < nitems; ii += nwarps) {
+        const Item it = items[ii];
+        int64_t r0 = it.r0, r1 = it.r1;
+        if (r0 < 0 || r1 > n || r0 >= r1 || (it.slot < 0 && r1 - r0 > kWarpRows)) continue;
+        const bool chunk = it.slot >= 0;
+        const int64_t k0 = it.k0, k1 = it.k1;
+        int64_t e_lo = k1, e_hi = k1;
+        if (!chunk) {
+            if (r0 + lane < r1) e_lo = rp[r0 + lane + 1];
+            if (r0 + 32 + lane < r1) e_hi = rp[r0 + 33 + lane];
+        } else {
+            r1 = r0 + 1;
+        }
+        auto row_end = [&](int64_t xx) -> int64_t {
+            const int i = (int)(xx - r0);
+            return __shfl_sync(FULL, i < 32 ? e_lo : e_hi, i & 31);
+        };
+        int64_t x = r0;
+        int64_t xe = row_end(x);
+        float a0 = 0.f, a1 = 0.f;
+        auto emit = [&](int64_t v) {
+            if (chunk) {
+                const int slot = it.slot, first = slot_first[slot];
+                const int ci = (int)((k0 - rp[r0]) / kWarpChunk);
+                reinterpret_cast<float2 *>(part + (int64_t)(first + ci) * 64)[lane] = make_float2(a0, a1);
+                return;
+            }
+            const double d = deg[v];
+            const float inv = d > 0.0 ? (float)(1.0 / d) : 0.f;
+            reinterpret_cast<__nv_bfloat162 *>(g + v * 64)[lane] = __floats2bfloat162_rn(a0 * inv, a1 * inv);
+        };
+        auto flush_until = [&](int64_t pos) {
+            while (x < r1 && xe <= pos) {
+                emit(x);
+                a0 = a1 = 0.f;
+                ++x;
+                if (x < r1) xe = row_end(x);
+            }
+        };
+        for (int64_t base = k0; base < k1; base += 32) {
+            const int64_t kk = base + lane;
+            int32_t cl = 0;
+            float al = 0.f;
+            if (kk < k1) {
+                cl = col[kk];
+                al = w ? w[kk] : 1.f;
+                if (cl < 0 || cl >= n) {
+                    dev_error(err, DEV_BAD_COL);
+                    cl = 0;
+                    al = 0.f;
+                }
+            }
+            const int mm = (int)(k1 - base < 32 ? k1 - base : 32);
+            for (int t = 0; t < mm; t += D) {
+                __nv_bfloat162 v[D];
+                float aa[D];
+#pragma unroll
+                for (int u = 0; u < D; ++u) {
+                    const int32_t c = __shfl_sync(FULL, cl, (t + u) & 31);
+                    aa[u] = __shfl_sync(FULL, al, (t + u) & 31);
+                    v[u] = t + u < mm ? h2[(int64_t)c * 32 + lane] : __floats2bfloat162_rn(0.f, 0.f);
+                }
+#pragma unroll
+                for (int u = 0; u < D; ++u) {
+                    if (t + u < mm) {
+                        flush_until(base + t + u);
+                        const float2 f = __bfloat1622float2(v[u]);
+                        a0 += aa[u] * f.x;
+                        a1 += aa[u] * f.y;
+                    }
+                }
+            }
+        }
+        flush_until(k1);
+        if (chunk) {
+            __threadfence();
+            __syncwarp();
+            const int slot = it.slot, first = slot_first[slot], nch = slot_nchunk[slot];
+            int last = 0;
+            if (lane == 0) last = atomicAdd(&cnt[slot], 1) == nch - 1;
+            last = __shfl_sync(FULL, last, 0);
+            if (last) {
+                __threadfence();
+                a0 = a1 = 0.f;
+                for (int c = 0; c < nch; ++c) {
+                    const float2 p = __ldcg(reinterpret_cast<const float2 *>(part + (int64_t)(first + c) * 64) + lane);
+                    a0 += p.x;
+                    a1 += p.y;
+                }
+                if (lane == 0) cnt[slot] = 0;
+                const double d = deg[r0];
+                const float inv = d > 0.0 ? (float)(1.0 / d) : 0.f;
+                reinterpret_cast<__nv_bfloat162 *>(g + r0 * 64)[lane] = __floats2bfloat162_rn(a0 * inv, a1 * inv);
+            }
+        }
+    }
+}
+
+// Adjoint of the 64-wide aggregation: dh[j] += (a_vj / d_v) dg[v] for every
+// arc v -> j, scattered along the same tiles (atomic float2 adds).
+__global__ void __launch_bounds__(256)
+k_scatter64(const Item *__restrict__ items, int64_t nitems, const int64_t *__restrict__ rp,
+            const int32_t *__restrict__ col, const float *__restrict__ w, const double *__restrict__ deg,
+            const float *__restrict__ dg, float *__restrict__ dh, int64_t n, int *err)
+{
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t ii = warp; ii < nitems; ii += nwarps) {
+        const Item it = items[ii];
+        const int64_t r0 = it.r0, r1 = it.slot >= 0 ? it.r0 + 1 : it.r1;
+        if (r0 < 0 || r1 > n || r0 >= r1) continue;
+        for (int64_t v = r0; v < r1; ++v) {
+            const double d = deg[v];
+            if (!(d > 0.0)) continue;
+            const float inv = (float)(1.0 / d);
+            float2 gv = reinterpret_cast<const float2 *>(dg + v * 64)[lane];
+            gv.x *= inv;
+            gv.y *= inv;
+            const int64_t a = it.slot >= 0 ? it.k0 : rp[v], e = it.slot >= 0 ? it.k1 : rp[v + 1];
+            for (int64_t base = a; base < e; base += 32) {
+                const int64_t kk = base + lane;
+                int32_t cl = -1;
+                float al = 0.f;
+                if (kk < e) {
+                    cl = col[kk];
+                    al = w ? w[kk] : 1.f;
+                    if (cl < 0 || cl >= n) {
+                        dev_error(err, DEV_BAD_COL);
+                        cl = -1;
+                    }
+                }
+                const int mm = (int)(e - base < 32 ? e - base : 32);
+                for (int t = 0; t < mm; ++t) {
+                    const int32_t c = __shfl_sync(FULL, cl, t);
+                    const float aj = __shfl_sync(FULL, al, t);
+                    if (c >= 0) atomicAdd(reinterpret_cast<float2 *>(dh + (int64_t)c * 64) + lane,
+                                          make_float2(aj * gv.x, aj * gv.y));
+                }
+            }
+        }
     }
 }
 
@@ -157,17 +476,14 @@ __device__ __forceinline__ bool gemm_run(uint32_t taddr, uint32_t a_s, uint32_t 
 
 // ---------------------------------------------------------------- forward layer
 
-// One layer on a tile of 128 nodes: stage [h_v | g_v] (BF16) and the packed
-// weights, one MMA chain, epilogue relu(D + b) -> h_out (BF16); the last layer
-// also writes z0 = w_o . h + b_o.  g is stored for the backward pass when
-// g_out is not NULL.
+// One layer on a tile of 128 nodes: stage [h_v | g_v] (BF16, g from the
+// aggregation pass) and the packed weights, one MMA chain, epilogue
+// relu(D + b) -> h_out (BF16); the last layer also writes z0 = w_o . h + b_o.
 template <int FIN, bool LAST>
 __global__ void __launch_bounds__(128)
-k_layer_fwd(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col, const float *__restrict__ w,
-            const double *__restrict__ deg, const __nv_bfloat16 *__restrict__ h_in,
+k_layer_fwd(int64_t n, const __nv_bfloat16 *__restrict__ h_in, const __nv_bfloat16 *__restrict__ g_in,
             const __nv_bfloat16 *__restrict__ img, const float *__restrict__ bias, const float *__restrict__ head,
-            __nv_bfloat16 *__restrict__ g_out, __nv_bfloat16 *__restrict__ h_out, float *__restrict__ z0,
-            int *err)
+            __nv_bfloat16 *__restrict__ h_out, float *__restrict__ z0, int *err)
 {
     constexpr int KP = FIN == kFin0 ? 16 : 2 * FIN;
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -179,99 +495,30 @@ k_layer_fwd(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict
     const int64_t r0 = (int64_t)blockIdx.x * kTile;
     gemm_setup(&tslot, &bar, 64);
     const uint32_t taddr = tslot;
-
-    // B: the packed weight image
     {
         const uint4 *src = reinterpret_cast<const uint4 *>(img);
         uint4 *dst = reinterpret_cast<uint4 *>(sb);
         for (int i = threadIdx.x; i < kHid * KP * 2 / 16; i += 128) dst[i] = src[i];
     }
-    // A: [h | g] rows
     if constexpr (FIN == kFin0) {
+        // row t: [x (8 bytes) | g (8 bytes)] in K group 0, zeros in K group 1
         const int64_t v = r0 + threadIdx.x;
-        float self[4] = {0.f, 0.f, 0.f, 0.f}, agg[4] = {0.f, 0.f, 0.f, 0.f};
+        uint4 row = make_uint4(0, 0, 0, 0);
         if (v < n) {
-#pragma unroll
-            for (int f = 0; f < 4; ++f) self[f] = bf(h_in[4 * v + f]);
-            for (int64_t k = rp[v]; k < rp[v + 1]; ++k) {
-                const int32_t j = col[k];
-                if (j < 0 || j >= n) {
-                    dev_error(err, DEV_BAD_COL);
-                    continue;
-                }
-                const float a = w ? w[k] : 1.f;
-#pragma unroll
-                for (int f = 0; f < 4; ++f) agg[f] += a * bf(h_in[4 * j + f]);
-            }
-            const double d = deg[v];
-            const float inv = d > 0.0 ? (float)(1.0 / d) : 0.f;
-#pragma unroll
-            for (int f = 0; f < 4; ++f) agg[f] *= inv;
+            const uint2 xs = *reinterpret_cast<const uint2 *>(h_in + 4 * v);
+            const uint2 gs = *reinterpret_cast<const uint2 *>(g_in + 4 * v);
+            row = make_uint4(xs.x, xs.y, gs.x, gs.y);
         }
-        __nv_bfloat16 row[16];
-#pragma unroll
-        for (int f = 0; f < 4; ++f) {
-            row[f] = __float2bfloat16_rn(self[f]);
-            row[4 + f] = __float2bfloat16_rn(agg[f]);
-        }
-#pragma unroll
-        for (int f = 8; f < 16; ++f) row[f] = __float2bfloat16_rn(0.f);
-        if (v < n && g_out)
-#pragma unroll
-            for (int f = 0; f < 4; ++f) g_out[4 * v + f] = row[4 + f];
-        // row r = threadIdx.x: K groups 0 and 1, 16 bytes each
-        const uint4 *rv = reinterpret_cast<const uint4 *>(row);
-        *reinterpret_cast<uint4 *>(sa + tc::kmajor_offset(threadIdx.x, 0, KP)) = rv[0];
-        *reinterpret_cast<uint4 *>(sa + tc::kmajor_offset(threadIdx.x, 8, KP)) = rv[1];
+        *reinterpret_cast<uint4 *>(sa + tc::kmajor_offset(threadIdx.x, 0, KP)) = row;
+        *reinterpret_cast<uint4 *>(sa + tc::kmajor_offset(threadIdx.x, 8, KP)) = make_uint4(0, 0, 0, 0);
     } else {
-        // warp per node, lane owns features 2 lane, 2 lane + 1
+        // warp per row, lane l: features 2l, 2l + 1 of h and of g
         for (int rr = wid; rr < kTile; rr += 4) {
             const int64_t v = r0 + rr;
             __nv_bfloat162 self2 = __floats2bfloat162_rn(0.f, 0.f), agg2 = self2;
             if (v < n) {
-                const __nv_bfloat162 *hv = reinterpret_cast<const __nv_bfloat162 *>(h_in + v * FIN);
-                self2 = hv[lane];
-                float a0 = 0.f, a1 = 0.f;
-                const int64_t kb = rp[v], ke = rp[v + 1];
-                int64_t k = kb;
-                for (; k + 3 < ke; k += 4) {
-                    int32_t j[4];
-                    float a[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        j[u] = col[k + u];
-                        a[u] = w ? w[k + u] : 1.f;
-                        if (j[u] < 0 || j[u] >= n) {
-                            dev_error(err, DEV_BAD_COL);
-                            j[u] = (int32_t)v;
-                            a[u] = 0.f;
-                        }
-                    }
-                    __nv_bfloat162 x[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) x[u] = reinterpret_cast<const __nv_bfloat162 *>(h_in + (int64_t)j[u] * FIN)[lane];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const float2 f = __bfloat1622float2(x[u]);
-                        a0 += a[u] * f.x;
-                        a1 += a[u] * f.y;
-                    }
-                }
-                for (; k < ke; ++k) {
-                    int32_t j = col[k];
-                    float a = w ? w[k] : 1.f;
-                    if (j < 0 || j >= n) {
-                        dev_error(err, DEV_BAD_COL);
-                        continue;
-                    }
-                    const float2 f = __bfloat1622float2(reinterpret_cast<const __nv_bfloat162 *>(h_in + (int64_t)j * FIN)[lane]);
-                    a0 += a * f.x;
-                    a1 += a * f.y;
-                }
-                const double d = deg[v];
-                const float inv = d > 0.0 ? (float)(1.0 / d) : 0.f;
-                agg2 = __floats2bfloat162_rn(a0 * inv, a1 * inv);
-                if (g_out) reinterpret_cast<__nv_bfloat162 *>(g_out + v * FIN)[lane] = agg2;
+                self2 = reinterpret_cast<const __nv_bfloat162 *>(h_in + v * FIN)[lane];
+                agg2 = reinterpret_cast<const __nv_bfloat162 *>(g_in + v * FIN)[lane];
             }
             *reinterpret_cast<__nv_bfloat162 *>(sa + tc::kmajor_offset(rr, 2 * lane, KP)) = self2;
             *reinterpret_cast<__nv_bfloat162 *>(sa + tc::kmajor_offset(rr, FIN + 2 * lane, KP)) = agg2;
@@ -356,10 +603,12 @@ k_loss_head(int64_t n, const float *__restrict__ z0, const double *__restrict__ 
 // ---------------------------------------------------------------- backward: dX = dq [Ws | Wn]^T
 
 // Tile of 128 nodes: dq = bf16(dh * [h > 0]) (K = 64) times the backward image
-// (N = 128); columns 0..63 are dh_self, 64..127 the gradient of g.
+// (N = 128); columns 0..63 (the gradient through h_v itself) overwrite the
+// tile's rows of dh in place (each tile reads its rows before the MMA), columns
+// 64..127 (the gradient of g) go to dg.
 __global__ void __launch_bounds__(128)
-k_layer_dx(int64_t n, const float *__restrict__ dh, const __nv_bfloat16 *__restrict__ h,
-           const __nv_bfloat16 *__restrict__ img, float *__restrict__ dself, float *__restrict__ dg, int *err)
+k_layer_dx(int64_t n, float *dh, const __nv_bfloat16 *__restrict__ h, const __nv_bfloat16 *__restrict__ img,
+           float *__restrict__ dg, int *err)
 {
     constexpr int K = kHid, N = 2 * kHid;
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -396,7 +645,7 @@ k_layer_dx(int64_t n, const float *__restrict__ dh, const __nv_bfloat16 *__restr
         tc::tmem_ld16(taddr + ((uint32_t)(32 * wid) << 16) + (uint32_t)c0, acc);
         tc::tmem_wait_ld();
         if (v < n && ok) {
-            float *dst = c0 < kHid ? dself + v * kHid + c0 : dg + v * kHid + (c0 - kHid);
+            float *dst = c0 < kHid ? dh + v * kHid + c0 : dg + v * kHid + (c0 - kHid);
 #pragma unroll
             for (int i = 0; i < 16; i += 4)
                 *reinterpret_cast<float4 *>(dst + i) = make_float4(acc[i], acc[i + 1], acc[i + 2], acc[i + 3]);
@@ -487,36 +736,6 @@ k_layer_dw(int64_t n, const __nv_bfloat16 *__restrict__ h_in, const __nv_bfloat1
     gemm_teardown(taddr, 64);
 }
 
-// ---------------------------------------------------------------- backward: adjoint of the aggregation
-
-// dh_in[j] = dself[j] + sum over v with a_vj > 0 of (a_vj / d_v) dg[v];
-// warp per node j over its in-neighbour list, lanes over features.
-__global__ void __launch_bounds__(256)
-k_agg_adjoint(int64_t n, const int64_t *__restrict__ tp, const int32_t *__restrict__ tc_, const float *__restrict__ tw,
-              const double *__restrict__ deg, const float *__restrict__ dself, const float *__restrict__ dg,
-              float *__restrict__ dh_in, int *err)
-{
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t j = warp; j < n; j += nwarps) {
-        float2 acc = reinterpret_cast<const float2 *>(dself + j * kHid)[lane];
-        for (int64_t k = tp[j]; k < tp[j + 1]; ++k) {
-            const int32_t v = tc_[k];
-            if (v < 0 || v >= n) {
-                dev_error(err, DEV_BAD_COL);
-                continue;
-            }
-            const double d = deg[v];
-            const float c = d > 0.0 ? (float)((tw ? (double)tw[k] : 1.0) / d) : 0.f;
-            const float2 x = reinterpret_cast<const float2 *>(dg + (int64_t)v * kHid)[lane];
-            acc.x += c * x.x;
-            acc.y += c * x.y;
-        }
-        reinterpret_cast<float2 *>(dh_in + j * kHid)[lane] = acc;
-    }
-}
-
 // ---------------------------------------------------------------- Adam, clamp
 
 __global__ void k_adam(int np, float *__restrict__ theta, float *__restrict__ m, float *__restrict__ v,
@@ -532,8 +751,9 @@ __global__ void k_adam(int np, float *__restrict__ theta, float *__restrict__ m,
     }
 }
 
-// z0 (FP32) -> clamp to [min s, max s] -> FP64 output; the range comes from
-// the order keys reduced by k_range.
+// z0 (FP32) -> FP64 output: clamped to [min s, max s] (the range comes from the
+// order keys reduced by k_range), except that a node that listens to nobody
+// (d_v = 0) takes its own opinion, its exact equilibrium value.
 __device__ __forceinline__ unsigned long long okey(double x)
 {
     unsigned long long b = (unsigned long long)__double_as_longlong(x);
@@ -558,12 +778,12 @@ __global__ void k_range(int64_t n, const double *__restrict__ s, unsigned long l
 }
 
 __global__ void k_clamp_out(int64_t n, const float *__restrict__ z0, const unsigned long long *__restrict__ mm,
-                            double *__restrict__ out)
+                            const double *__restrict__ deg, const double *__restrict__ s, double *__restrict__ out)
 {
     const double lo = okey_inv(mm[0]), hi = okey_inv(mm[1]);
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         const double x = (double)z0[v];
-        out[v] = x < lo ? lo : (x > hi ? hi : x);
+        out[v] = deg[v] > 0.0 ? (x < lo ? lo : (x > hi ? hi : x)) : s[v];
     }
 }
 
@@ -586,8 +806,11 @@ struct fj_mpnn {
     __nv_bfloat16 *h[3] = {nullptr, nullptr, nullptr};  // n x 64
     __nv_bfloat16 *g[2] = {nullptr, nullptr};           // n x 64 (inputs of layers 2, 3)
     float *z0 = nullptr;
+    double *mv = nullptr;                               // n: m_v
+    int64_t cap_part = 0;
+    float *part = nullptr;                              // per long-row chunk: 64 partial sums
     int64_t cap_bwd = 0;
-    float *dh = nullptr, *dself = nullptr, *dg = nullptr;  // n x 64
+    float *dh = nullptr, *dg = nullptr;                 // n x 64
     double *sin = nullptr, *zin = nullptr, *zout = nullptr;  // host staging
     int64_t cap_stage = 0;
     double *loss = nullptr;
@@ -639,6 +862,7 @@ fj_status ensure_fwd(fj_mpnn *m, int64_t n)
     for (auto &p : m->h) FJ_CHECK(grow(&p, kHid * n));
     for (auto &p : m->g) FJ_CHECK(grow(&p, kHid * n));
     FJ_CHECK(grow(&m->z0, n));
+    FJ_CHECK(grow(&m->mv, n));
     m->cap = n;
     return FJ_OK;
 }
@@ -647,7 +871,6 @@ fj_status ensure_bwd(fj_mpnn *m, int64_t n)
 {
     if (n <= m->cap_bwd) return FJ_OK;
     FJ_CHECK(grow(&m->dh, kHid * n));
-    FJ_CHECK(grow(&m->dself, kHid * n));
     FJ_CHECK(grow(&m->dg, kHid * n));
     m->cap_bwd = n;
     return FJ_OK;
@@ -671,26 +894,41 @@ fj_status stage(fj_mpnn *m, int64_t n, const double *src, double **dst_slot, con
     return FJ_OK;
 }
 
-// Forward pass; keeps what the backward pass needs when `train`.
-fj_status forward(fj_mpnn *m, fj_graph *g, const double *sd, bool train, cudaStream_t st)
+// Forward pass (every activation stays for the backward pass).
+fj_status forward(fj_mpnn *m, fj_graph *g, const double *sd, cudaStream_t st)
 {
     const DevCSR &c = g->csr;
     const int64_t n = c.n;
     FJ_CHECK(ensure_fwd(m, n));
-    k_features<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(n, c.row_ptr, c.col, c.w, c.deg64, c.indeg, sd, m->x,
-                                                          m->err);
+    const ItemPlan *ip = nullptr;
+    FJ_CHECK(plain_items(g, st, &ip));
+    if (ip->nparts * 64 > m->cap_part) {
+        FJ_CHECK(grow(&m->part, ip->nparts * 64));
+        m->cap_part = ip->nparts * 64;
+    }
+    const unsigned agrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ip->nitems, 8), 152 * 8));
+    k_agg_s<<<agrid, 256, 0, st>>>(ip->items, ip->nitems, c.row_ptr, c.col, c.w, c.deg64, sd, m->mv, ip->part,
+                                   ip->cnt, ip->slot_first, ip->slot_nchunk, n, m->err);
+    k_features<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(n, c.deg64, c.indeg, sd, m->mv, m->x);
+    k_agg4<<<agrid, 256, 0, st>>>(ip->items, ip->nitems, c.row_ptr, c.col, c.w, c.deg64, m->x, m->g0, m->part,
+                                  ip->cnt, ip->slot_first, ip->slot_nchunk, n, m->err);
     const unsigned tiles = (unsigned)std::max<int64_t>(1, (n + kTile - 1) / kTile);
     const float *th = m->theta;
     const int ho = head_off();
-    k_layer_fwd<kFin0, false><<<tiles, 128, kGemmSmem, st>>>(n, c.row_ptr, c.col, c.w, c.deg64, m->x, m->img_fwd[0],
-                                                             th + layer_off(0).b, th + ho, train ? m->g0 : nullptr,
-                                                             m->h[0], m->z0, m->err);
-    k_layer_fwd<kHid, false><<<tiles, 128, kGemmSmem, st>>>(n, c.row_ptr, c.col, c.w, c.deg64, m->h[0], m->img_fwd[1],
-                                                            th + layer_off(1).b, th + ho, train ? m->g[0] : nullptr,
-                                                            m->h[1], m->z0, m->err);
-    k_layer_fwd<kHid, true><<<tiles, 128, kGemmSmem, st>>>(n, c.row_ptr, c.col, c.w, c.deg64, m->h[1], m->img_fwd[2],
-                                                           th + layer_off(2).b, th + ho, train ? m->g[1] : nullptr,
-                                                           m->h[2], m->z0, m->err);
+    k_layer_fwd<kFin0, false><<<tiles, 128, kGemmSmem, st>>>(n, m->x, m->g0, m->img_fwd[0], th + layer_off(0).b,
+                                                             th + ho, m->h[0], m->z0, m->err);
+    for (int l = 1; l < 3; ++l) {
+        k_agg64<<<agrid, 256, 0, st>>>(ip->items, ip->nitems, c.row_ptr, c.col, c.w, c.deg64, m->h[l - 1],
+                                       m->g[l - 1], m->part, ip->cnt, ip->slot_first, ip->slot_nchunk, n, m->err);
+        if (l == 1)
+            k_layer_fwd<kHid, false><<<tiles, 128, kGemmSmem, st>>>(n, m->h[0], m->g[0], m->img_fwd[1],
+                                                                    th + layer_off(1).b, th + ho, m->h[1], m->z0,
+                                                                    m->err);
+        else
+            k_layer_fwd<kHid, true><<<tiles, 128, kGemmSmem, st>>>(n, m->h[1], m->g[1], m->img_fwd[2],
+                                                                   th + layer_off(2).b, th + ho, m->h[2], m->z0,
+                                                                   m->err);
+    }
     FJ_CUDA(cudaGetLastError());
     return FJ_OK;
 }
@@ -760,7 +998,7 @@ void fj_mpnn_destroy(fj_mpnn *m)
     dev_free(m->x); dev_free(m->g0); dev_free(m->z0);
     for (auto p : m->h) dev_free(p);
     for (auto p : m->g) dev_free(p);
-    dev_free(m->dh); dev_free(m->dself); dev_free(m->dg);
+    dev_free(m->dh); dev_free(m->dg); dev_free(m->mv); dev_free(m->part);
     dev_free(m->sin); dev_free(m->zin); dev_free(m->zout);
     dev_free(m->loss); dev_free(m->mm); dev_free(m->err);
     delete m;
@@ -790,7 +1028,7 @@ fj_status fj_mpnn_predict(fj_mpnn *m, fj_graph *g, const double *s, double *z0, 
     const int64_t n = g->csr.n;
     const double *sd = nullptr;
     FJ_CHECK(stage(m, n, s, &m->sin, &sd, mem, st));
-    FJ_CHECK(forward(m, g, sd, false, st));
+    FJ_CHECK(forward(m, g, sd, st));
     const unsigned long long init[2] = {~0ULL, 0ULL};
     FJ_CUDA(cudaMemcpyAsync(m->mm, init, sizeof(init), cudaMemcpyHostToDevice, st));
     k_range<<<grid_for(n, 256, 152 * 4), 256, 0, st>>>(n, sd, m->mm);
@@ -804,7 +1042,7 @@ fj_status fj_mpnn_predict(fj_mpnn *m, fj_graph *g, const double *s, double *z0, 
         }
         dst = m->zout;
     }
-    k_clamp_out<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(n, m->z0, m->mm, dst);
+    k_clamp_out<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(n, m->z0, m->mm, g->csr.deg64, sd, dst);
     FJ_CUDA(cudaGetLastError());
     if (mem == FJ_MEM_HOST) FJ_CUDA(cudaMemcpyAsync(z0, dst, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
     return mpnn_check(m, st);
@@ -823,17 +1061,16 @@ fj_status fj_mpnn_grad(fj_mpnn *m, fj_graph *g, const double *s, const double *z
     FJ_CHECK(stage(m, n, s, &m->sin, &sd, mem, st));
     FJ_CHECK(stage(m, n, z, &m->zin, &zd, mem, st));
     FJ_CHECK(ensure_bwd(m, n));
-    FJ_CHECK(forward(m, g, sd, true, st));
+    FJ_CHECK(forward(m, g, sd, st));
     const int np = param_count();
     FJ_CUDA(cudaMemsetAsync(m->grad, 0, sizeof(float) * np, st));
     FJ_CUDA(cudaMemsetAsync(m->loss, 0, sizeof(double), st));
     const int ho = head_off();
     k_loss_head<<<grid_for(n * 32, 256, 152 * 8), 256, 0, st>>>(n, m->z0, zd, m->h[2], m->theta + ho, m->dh,
                                                                 m->grad + ho, m->loss);
-    // in-neighbour lists for the adjoint of the mean
-    const int64_t *tp = g->directed ? g->tptr : c.row_ptr;
-    const int32_t *tcol = g->directed ? g->tcol : c.col;
-    const float *tw = g->directed ? g->tw : c.w;
+    const ItemPlan *ip = nullptr;
+    FJ_CHECK(plain_items(g, st, &ip));
+    const unsigned agrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ip->nitems, 8), 152 * 8));
     const unsigned tiles = (unsigned)std::max<int64_t>(1, (n + kTile - 1) / kTile);
     const unsigned dwgrid = (unsigned)std::min<int64_t>(tiles, 152 * 3);
     for (int l = 2; l >= 0; --l) {
@@ -847,9 +1084,10 @@ fj_status fj_mpnn_grad(fj_mpnn *m, fj_graph *g, const double *s, const double *z
             k_layer_dw<kHid><<<dwgrid, 128, kGemmSmem, st>>>(n, hin, gin, m->dh, m->h[l], m->grad + o.ws,
                                                              m->grad + o.b, m->err);
         if (l > 0) {
-            k_layer_dx<<<tiles, 128, kGemmSmem, st>>>(n, m->dh, m->h[l], m->img_bwd[l], m->dself, m->dg, m->err);
-            k_agg_adjoint<<<grid_for(n * 32, 256, 152 * 8), 256, 0, st>>>(n, tp, tcol, tw, c.deg64, m->dself, m->dg,
-                                                                          m->dh, m->err);
+            // dh <- gradient through h_{l-1} itself, then + the adjoint of the aggregation
+            k_layer_dx<<<tiles, 128, kGemmSmem, st>>>(n, m->dh, m->h[l], m->img_bwd[l], m->dg, m->err);
+            k_scatter64<<<agrid, 256, 0, st>>>(ip->items, ip->nitems, c.row_ptr, c.col, c.w, c.deg64, m->dg, m->dh,
+                                               n, m->err);
         }
         FJ_CUDA(cudaGetLastError());
     }

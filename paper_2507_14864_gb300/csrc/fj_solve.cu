@@ -306,11 +306,11 @@ k_sweep(const Item *__restrict__ items, int64_t item0, int64_t nitems, const int
     unsigned long long my_push = 0, my_edges = 0;
     bool bad = false;
 
-    auto apply = [&](int64_t x, T rx, T hx, T ix, T ox, double zx, int32_t dgx) {
+    auto apply = [&](int64_t x, T rx, T hx, T ix, T ox, int32_t dgx) {
         T dx = T(0);
         if (abs_t(rx) > hx) {
             dx = ox * rx * ix;
-            zhat[x] = zx + (double)dx;
+            zhat[x] += (double)dx;  // read only when the row pushes
             rx = (T(1) - ox) * rx;
             my_push += 1;
             my_edges += (unsigned long long)dgx;
@@ -357,14 +357,12 @@ k_sweep(const Item *__restrict__ items, int64_t item0, int64_t nitems, const int
                 const T *spb = sprod[wl][s];
                 int ra[kWR], re[kWR];
                 T rr[kWR], rh[kWR], ri[kWR], ro[kWR], acc[kWR];
-                double rz[kWR];
                 int32_t rd[kWR];
 #pragma unroll
                 for (int q = 0; q < kWR; ++q) {
                     const int64_t x = r0 + lane + 32 * q;
                     ra[q] = re[q] = 0;
                     rr[q] = rh[q] = ri[q] = ro[q] = acc[q] = T(0);
-                    rz[q] = 0.0;
                     rd[q] = 0;
                     if (x < r1) {
                         ra[q] = (int)(rp[x] - kb);
@@ -373,7 +371,6 @@ k_sweep(const Item *__restrict__ items, int64_t item0, int64_t nitems, const int
                         rh[q] = h[x];
                         ri[q] = inv[x];
                         ro[q] = om[x];
-                        rz[q] = zhat[x];
                         rd[q] = indeg[x];
                     }
                 }
@@ -413,7 +410,7 @@ k_sweep(const Item *__restrict__ items, int64_t item0, int64_t nitems, const int
 #pragma unroll
                 for (int q = 0; q < kWR; ++q) {
                     const int64_t x = r0 + lane + 32 * q;
-                    if (x < r1) apply(x, rr[q] + acc[q], rh[q], ri[q], ro[q], rz[q], rd[q]);
+                    if (x < r1) apply(x, rr[q] + acc[q], rh[q], ri[q], ro[q], rd[q]);
                 }
             } else {
                 // ---- chunk of a long row: partial sum; the last chunk applies the update
@@ -441,7 +438,7 @@ k_sweep(const Item *__restrict__ items, int64_t item0, int64_t nitems, const int
                     sum = warp_sum(sum);
                     if (lane == 0) {
                         cnt[slot] = 0;
-                        apply(r0, r[r0] + (T)sum, h[r0], inv[r0], om[r0], zhat[r0], indeg[r0]);
+                        apply(r0, r[r0] + (T)sum, h[r0], inv[r0], om[r0], indeg[r0]);
                     }
                 }
             }
@@ -480,20 +477,33 @@ k_sweep(const Item *__restrict__ items, int64_t item0, int64_t nitems, const int
 
 // ============================================================== FP64 certificate
 
-// r64_x = s'_x - (1 + d_x) zhat_x + sum_j a_xj zhat_j  (= s' - (I + L) zhat'),
-// accumulated with compensated FP64 arithmetic (Dot2), so the value is the
-// residual of the stored zhat' to about one rounding, at any degree.  Per
-// graph: max |r64|, max |r64| / s', max |zhat - c_eff|, and the number of
-// nodes with |r64| > max(eps' s', resid_floor).  Stores r64 into the push
-// residual (magnitude rounded up for FP32) and the FP64 residual, and clears
-// both increment buffers: the push restarts from an exact residual (a
-// refinement pass).
+// r64_x = s'_x - (1 + d_x) zhat_x + sum_j a_xj zhat_j  (= s' - (I + L) zhat').
+// Each row is first summed plainly in FP64 (one FMA per nonzero) with an FP32
+// sum of |a_xj zhat_j| beside it, which gives the a-priori bound
+// gamma_m (sum of |terms|), gamma_m = m u / (1 - m u), on that sum's rounding
+// error.  Only when |r64| lies within that bound of the threshold is the row
+// summed again with compensated arithmetic (Dot2), which is exact to about one
+// rounding; the decision |r64| > max(eps' s', resid_floor) is therefore always
+// the exact one, while most rows cost one FP64 FMA per nonzero.  Per graph:
+// max |r64|, max |r64| / s', max |zhat - c_eff|, the number above threshold.
+// Stores r64 into the push residual (magnitude rounded up for FP32) and the
+// FP64 residual, and clears both increment buffers: the push restarts from
+// this residual (a refinement pass).
 //
 // One warp per warp tile (grid-strided): a row of at most kShortRow nonzeros
-// is summed by one lane, a longer row by the whole warp (lanes stride the row,
-// then a warp reduction of the compensated pairs); a chunk of a long row is
-// summed by the warp and the last chunk to finish completes the row.
+// is summed by one lane, a longer row by the whole warp; a chunk of a long row
+// is summed by the warp and the last chunk to finish completes the row.
 constexpr int kShortRow = 8;
+
+// gamma_m of the standard bound on an m-term FP64 sum (u = 2^-53), with the
+// FP32 magnitude sum inflated to an upper bound of itself.
+__device__ __forceinline__ double plain_bound(int64_t m, float abs32, double dpl_zx, double spx)
+{
+    const double mm = (double)(m + 4);
+    const double gam = mm * 0x1p-53 / (1.0 - mm * 0x1p-53);
+    const double mag = (double)abs32 * (1.0 + (double)(m + 2) * 0x1p-23) + fabs(dpl_zx) + fabs(spx);
+    return gam * mag;
+}
 
 template <typename T, bool W>
 __global__ void __launch_bounds__(256)
@@ -523,12 +533,39 @@ k_certify(const Item *__restrict__ items, int64_t nitems, const int64_t *__restr
         }
         m_abs = m_rel = m_z = viol = 0.0;
     };
-    // completes row x from acc = sum_j a_xj zhat_j (compensated)
-    auto finish = [&](int64_t x, DD acc) {
-        const double zx = zhat[x];
+    // plain pass over [a, e) by one thread: FP64 sum and FP32 magnitude sum
+    auto plain_terms = [&](int64_t a, int64_t e, int64_t step, double &acc, float &mag) {
+        for (int64_t k = a; k < e; k += step) {
+            const int32_t cj = __ldg(col + k);
+            if (!FJ_IDX_OK(4, cj, n_rows)) continue;
+            const double zc = zhat[cj];
+            const float wk = W ? __ldg(w + k) : 1.f;
+            acc = fma(W ? (double)wk : 1.0, zc, acc);
+            mag = fmaf(wk, fabsf((float)zc), mag);
+        }
+    };
+    auto exact_terms = [&](int64_t a, int64_t e, int64_t step, DD &acc) {
+        for (int64_t k = a; k < e; k += step) {
+            const int32_t cj = __ldg(col + k);
+            if (FJ_IDX_OK(4, cj, n_rows)) dd_fma(acc, arc_w<double, W>(w, k), zhat[cj]);
+        }
+    };
+    // the residual from a plain sum, and whether the decision needs the exact one
+    auto plain_residual = [&](int64_t x, int64_t len, double acc, float mag, bool &ambiguous) -> double {
+        const double zx = zhat[x], spx = sp[x], dpl = 1.0 + deg[x];
+        const double rx = fma(-dpl, zx, spx) + acc;
+        const double bnd = plain_bound(len, mag, dpl * zx, spx);
+        const double thr = fmax(epsp * spx, resid_floor(deg[x], zx));
+        ambiguous = fabs(fabs(rx) - thr) <= bnd || !(fabs(rx) <= 1e300);
+        return rx;
+    };
+    auto exact_residual = [&](int64_t x, DD acc) -> double {
         dd_add(acc, sp[x]);
-        dd_fma(acc, -(1.0 + deg[x]), zx);
-        const double rx = dd_value(acc);
+        dd_fma(acc, -(1.0 + deg[x]), zhat[x]);
+        return dd_value(acc);
+    };
+    auto finish = [&](int64_t x, double rx) {
+        const double zx = zhat[x];
         double ax = fabs(rx);
         if (!(ax <= 1e300)) ax = INFINITY;
         m_abs = fmax(m_abs, ax);
@@ -539,10 +576,6 @@ k_certify(const Item *__restrict__ items, int64_t nitems, const int64_t *__restr
         r64[x] = rx;
         da[x] = T(0);
         db[x] = T(0);
-    };
-    auto gather = [&](int64_t k, DD &acc) {
-        const int32_t cj = __ldg(col + k);
-        if (FJ_IDX_OK(4, cj, n_rows)) dd_fma(acc, arc_w<double, W>(w, k), zhat[cj]);
     };
 
     for (int64_t ii = warp; ii < nitems; ii += nwarps) {
@@ -570,43 +603,81 @@ k_certify(const Item *__restrict__ items, int64_t nitems, const int64_t *__restr
                 }
                 const bool shortrow = mine && e - a <= kShortRow;
                 if (shortrow) {
-                    DD acc{0.0, 0.0};
-                    for (int64_t k = a; k < e; ++k) gather(k, acc);
-                    finish(x, acc);
+                    double acc = 0.0;
+                    float mag = 0.f;
+                    plain_terms(a, e, 1, acc, mag);
+                    bool amb = false;
+                    double rx = plain_residual(x, e - a, acc, mag, amb);
+                    if (amb) {
+                        DD d{0.0, 0.0};
+                        exact_terms(a, e, 1, d);
+                        rx = exact_residual(x, d);
+                    }
+                    finish(x, rx);
                 }
                 unsigned longs = __ballot_sync(FULL, mine && !shortrow);
                 while (longs) {
                     const int src = __ffs(longs) - 1;
                     longs &= longs - 1;
+                    const int64_t xl = r0 + src + 32 * half;
                     const int64_t al = __shfl_sync(FULL, a, src), el = __shfl_sync(FULL, e, src);
-                    DD acc{0.0, 0.0};
-                    for (int64_t k = al + lane; k < el; k += 32) gather(k, acc);
-                    acc = warp_dd_sum(acc);
-                    if (lane == 0) finish(r0 + src + 32 * half, acc);
+                    double acc = 0.0;
+                    float mag = 0.f;
+                    plain_terms(al + lane, el, 32, acc, mag);
+                    acc = warp_sum(acc);
+                    mag = warp_sum(mag);
+                    bool amb = false;
+                    double rx = plain_residual(xl, el - al, acc, mag, amb);  // same on every lane
+                    if (amb) {
+                        DD d{0.0, 0.0};
+                        exact_terms(al + lane, el, 32, d);
+                        d = warp_dd_sum(d);
+                        rx = exact_residual(xl, d);
+                    }
+                    if (lane == 0) finish(xl, rx);
                 }
             }
         } else {
-            DD acc{0.0, 0.0};
-            for (int64_t k = it.k0 + lane; k < it.k1; k += 32) gather(k, acc);
-            acc = warp_dd_sum(acc);
+            double acc = 0.0;
+            float mag = 0.f;
+            plain_terms(it.k0 + lane, it.k1, 32, acc, mag);
+            acc = warp_sum(acc);
+            mag = warp_sum(mag);
             const int slot = it.slot;
             const int first = slot_first[slot], nch = slot_nchunk[slot];
             const int ci = (int)((it.k0 - rp[r0]) / kWarpChunk);
             int last = 0;
             if (lane == 0) {
-                part[2 * (first + ci)] = acc.hi;
-                part[2 * (first + ci) + 1] = acc.lo;
+                part[2 * (first + ci)] = acc;
+                part[2 * (first + ci) + 1] = (double)mag;
                 __threadfence();
                 last = atomicAdd(&cnt[slot], 1) == nch - 1;
             }
             last = __shfl_sync(FULL, last, 0);
-            if (last && lane == 0) {
+            if (last) {
                 __threadfence();
-                DD sum{0.0, 0.0};
-                for (int c = 0; c < nch; ++c)
-                    sum = dd_merge(sum, DD{__ldcg(part + 2 * (first + c)), __ldcg(part + 2 * (first + c) + 1)});
-                cnt[slot] = 0;
-                finish(r0, sum);
+                double sum = 0.0, smag = 0.0;
+                for (int c = lane; c < nch; c += 32) {
+                    sum += __ldcg(part + 2 * (first + c));
+                    smag += __ldcg(part + 2 * (first + c) + 1);
+                }
+                sum = warp_sum(sum);
+                smag = warp_sum(smag);
+                const int64_t a = rp[r0], e = rp[r0 + 1];
+                bool amb = false;
+                // the chunked sum has at most e - a + nch + 64 rounding steps
+                double rx = plain_residual(r0, (e - a) + nch + 64, sum,
+                                           (float)(smag * (1.0 + (double)nch * 0x1p-23)), amb);
+                if (amb) {
+                    DD d{0.0, 0.0};
+                    exact_terms(a + lane, e, 32, d);
+                    d = warp_dd_sum(d);
+                    rx = exact_residual(r0, d);
+                }
+                if (lane == 0) {
+                    cnt[slot] = 0;
+                    finish(r0, rx);
+                }
             }
         }
     }
@@ -943,6 +1014,15 @@ static fj_status make_plan(fj_graph *g, const fj_solve_opts *o, cudaStream_t st,
     p.perm = g->colr.perm;
     if (!g->wplan_pcsr.built) FJ_CHECK(build_items(g, g->colr.pcsr, &g->colr.class_row, g->wplan_pcsr, st, true));
     p.wip = &g->wplan_pcsr;
+    return FJ_OK;
+}
+
+// Warp-tile items of the caller-order CSR (built on first use): the balanced
+// work list other passes over the graph (the network's aggregations) share.
+fj_status plain_items(fj_graph *g, cudaStream_t st, const ItemPlan **out)
+{
+    if (!g->wplan_csr.built) FJ_CHECK(build_items(g, g->csr, nullptr, g->wplan_csr, st, true));
+    *out = &g->wplan_csr;
     return FJ_OK;
 }
 
@@ -1313,6 +1393,7 @@ static fj_status solve_t(fj_graph *g, const double *s, const double *z0, const f
             f.push_bytes = (double)ws.ctr_host->sweeps * per_sweep + (double)ws.ctr_host->pushes * 20.0;
             f.frontier_rounds = f_rounds;
             f.frontier_pushes = f_pushes;
+            f.omega_used = o->omega;
         }
     }
     return result;
@@ -1321,6 +1402,20 @@ static fj_status solve_t(fj_graph *g, const double *s, const double *z0, const f
 }  // namespace fj
 
 using namespace fj;
+
+// FJ_SCHED_AUTO: a solve whose residual becomes non-finite at omega > 1 (SOR
+// over colour classes is proven for symmetric systems only, Section 5.2) is
+// restarted from its start with omega = 1, where the sweep is Gauss-Seidel on
+// the diagonally dominant M-matrix I + L and converges.
+template <typename F>
+static fj_status with_omega_fallback(const fj_solve_opts *opts, F run)
+{
+    const fj_status st = run(opts);
+    if (st != FJ_ERR_DIVERGED || opts->schedule != FJ_SCHED_AUTO || !(opts->omega > 1.0)) return st;
+    fj_solve_opts o = *opts;
+    o.omega = 1.0;
+    return run(&o);
+}
 
 extern "C" {
 
@@ -1331,8 +1426,10 @@ fj_status fj_solve(fj_graph *g, const double *s, const fj_solve_opts *opts, doub
     FJ_ARG(s != nullptr && z_out != nullptr, "s or z_out is NULL");
     FJ_ARG(mem == FJ_MEM_HOST || mem == FJ_MEM_DEVICE, "mem must be FJ_MEM_HOST or FJ_MEM_DEVICE");
     FJ_CHECK(check_opts(opts));
-    if (opts->precision == FJ_PREC_FP32) return solve_t<float>(g, s, nullptr, opts, z_out, info, mem);
-    return solve_t<double>(g, s, nullptr, opts, z_out, info, mem);
+    return with_omega_fallback(opts, [&](const fj_solve_opts *o) {
+        if (o->precision == FJ_PREC_FP32) return solve_t<float>(g, s, nullptr, o, z_out, info, mem);
+        return solve_t<double>(g, s, nullptr, o, z_out, info, mem);
+    });
 }
 
 fj_status fj_solve_warm(fj_graph *g, const double *s, const double *z0, const fj_solve_opts *opts, double *z_out,
@@ -1342,8 +1439,10 @@ fj_status fj_solve_warm(fj_graph *g, const double *s, const double *z0, const fj
     FJ_ARG(s != nullptr && z0 != nullptr && z_out != nullptr, "s, z0 or z_out is NULL");
     FJ_ARG(mem == FJ_MEM_HOST || mem == FJ_MEM_DEVICE, "mem must be FJ_MEM_HOST or FJ_MEM_DEVICE");
     FJ_CHECK(check_opts(opts));
-    if (opts->precision == FJ_PREC_FP32) return solve_t<float>(g, s, z0, opts, z_out, info, mem);
-    return solve_t<double>(g, s, z0, opts, z_out, info, mem);
+    return with_omega_fallback(opts, [&](const fj_solve_opts *o) {
+        if (o->precision == FJ_PREC_FP32) return solve_t<float>(g, s, z0, o, z_out, info, mem);
+        return solve_t<double>(g, s, z0, o, z_out, info, mem);
+    });
 }
 
 fj_status fj_frontier(int64_t n, const void *r, const void *h, int precision, int32_t *list, int64_t *count,
@@ -1579,7 +1678,7 @@ __device__ __forceinline__ void warp_tile_k(int64_t r0, int64_t r1, int64_t k0, 
 // One colour class of a multi-RHS sweep: the update of k_sweep applied to k
 // opinion vectors at once, one warp per warp tile.  A long row's chunks keep
 // k partial sums each and the last chunk to finish applies the update.
-template <typename T, bool W>
+template <typename T, bool W, int D>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
 k_sweep_batch(const Item *__restrict__ items, int64_t item0, int64_t nitems, const int64_t *__restrict__ rp,
               const int32_t *__restrict__ col, const float *__restrict__ w, int k, T *dcur,
@@ -1632,7 +1731,6 @@ k_sweep_batch(const Item *__restrict__ items, int64_t item0, int64_t nitems, con
         if (has2) upd(x, 1, s2);
     };
     auto no_begin = [](int64_t) {};
-    constexpr int D = 8;
 
     // tiles are drawn from tick[0] one at a time (dynamic balance across warps);
     // the last warp to retire resets tick[0..1] for the next launch
@@ -1710,11 +1808,17 @@ k_sweep_batch(const Item *__restrict__ items, int64_t item0, int64_t nitems, con
     }
 }
 
-// FP64 certificate of every (node, right-hand side), as k_certify: the
-// residual of each vector accumulated with compensated arithmetic (Dot2).
-// Per-vector statistics are reduced per block in shared memory (maxima of
-// non-negative doubles compare as integers) and added with one atomic per
-// vector and field.
+// FP64 certificate of every (node, right-hand side), as k_certify: a plain
+// FP64 sum per (row, vector) with an FP32 magnitude sum beside it, and the
+// compensated (Dot2) re-evaluation of the few entries whose residual lies
+// within the plain sum's error bound of the threshold.  Per-vector statistics
+// are reduced per block in shared memory (maxima of non-negative doubles
+// compare as integers) and added with one atomic per vector and field.
+struct PlainAcc {
+    double s;
+    float m;
+};
+
 template <typename T, bool W>
 __global__ void __launch_bounds__(256)
 k_certify_batch(const Item *__restrict__ items, int64_t nitems, const int64_t *__restrict__ rp,
@@ -1733,33 +1837,41 @@ k_certify_batch(const Item *__restrict__ items, int64_t nitems, const int64_t *_
     double m_abs[2] = {0, 0}, m_rel[2] = {0, 0}, m_z[2] = {0, 0}, viol[2] = {0, 0};
     const double *gsd = reinterpret_cast<const double *>(gs);
 
-    // row x, vector lane + 32 hh, from acc = sum_c a_xc zhat_c
-    auto finish = [&](int64_t x, int hh, DD acc) {
+    // row x, vector j = lane + 32 hh, from the plain sums over `len` terms
+    auto finish = [&](int64_t x, int hh, PlainAcc acc, int64_t len) {
         const int j = lane + 32 * hh;
         const int64_t q = x * k + j;
-        const double zx = zhat[q], spx = sp[q];
-        dd_add(acc, spx);
-        dd_fma(acc, -(1.0 + deg[x]), zx);
-        const double rx = dd_value(acc);
+        const double zx = zhat[q], spx = sp[q], dpl = 1.0 + deg[x];
+        double rx = fma(-dpl, zx, spx) + acc.s;
+        const double thr = fmax(epsp * spx, resid_floor(deg[x], zx));
+        const double bnd = plain_bound(len, acc.m, dpl * zx, spx);
+        if (fabs(fabs(rx) - thr) <= bnd || !(fabs(rx) <= 1e300)) {
+            DD d{0.0, 0.0};  // exact re-evaluation of this entry, by this lane
+            for (int64_t kk = rp[x]; kk < rp[x + 1]; ++kk) {
+                const int32_t c = __ldg(col + kk);
+                if (FJ_IDX_OK(4, c, n_rows)) dd_fma(d, W ? (double)__ldg(w + kk) : 1.0, zhat[(int64_t)c * k + j]);
+            }
+            dd_add(d, spx);
+            dd_fma(d, -dpl, zx);
+            rx = dd_value(d);
+        }
         const double ce = gsd[(int64_t)j * kGs + 1];
         const double ax = fabs(rx) <= 1e300 ? fabs(rx) : INFINITY;
         m_abs[hh] = fmax(m_abs[hh], ax);
         m_rel[hh] = fmax(m_rel[hh], ax / spx);
         m_z[hh] = fmax(m_z[hh], fabs(zx - ce));
-        if (ax > fmax(epsp * spx, resid_floor(deg[x], zx))) viol[hh] += 1.0;
+        if (ax > thr) viol[hh] += 1.0;
         r[q] = resid_store<T>(rx);
         r64[q] = rx;
         da[q] = T(0);
         db[q] = T(0);
     };
     auto src = [&](int32_t c) -> const double * { return zhat + (int64_t)c * k; };
-    auto add = [](DD &acc, float a, double v) { dd_fma(acc, (double)a, v); };
-    auto no_begin = [](int64_t) {};
-    auto short_row = [&](int64_t x, DD s1, DD s2) {
-        if (has1) finish(x, 0, s1);
-        if (has2) finish(x, 1, s2);
+    auto add = [](PlainAcc &acc, float a, double v) {
+        acc.s = fma((double)a, v, acc.s);
+        acc.m = fmaf(a, fabsf((float)v), acc.m);
     };
-
+    auto no_begin = [](int64_t) {};
     for (int64_t ii = (int64_t)blockIdx.x * 8 + wl; ii < nitems; ii += nwarps) {
         const Item it = items[ii];
         const int64_t r0 = it.r0, r1 = it.r1;
@@ -1767,25 +1879,30 @@ k_certify_batch(const Item *__restrict__ items, int64_t nitems, const int64_t *_
             (it.slot < 0 && !FJ_IDX_OK(13, r1 - r0, kWarpRows + 1)))
             continue;
         if (it.slot < 0) {
-            warp_tile_k<DD, double, W, 8>(r0, r1, it.k0, it.k1, false, rp, col, w, no_begin, src, add, short_row,
-                                          lane, has1, has2, n_rows);
+            auto short_row = [&](int64_t x, PlainAcc s1, PlainAcc s2) {
+                const int64_t len = rp[x + 1] - rp[x];
+                if (has1) finish(x, 0, s1, len);
+                if (has2) finish(x, 1, s2, len);
+            };
+            warp_tile_k<PlainAcc, double, W, 8>(r0, r1, it.k0, it.k1, false, rp, col, w, no_begin, src, add,
+                                                short_row, lane, has1, has2, n_rows);
         } else {
             const int slot = it.slot;
             const int first = slot_first[slot], nch = slot_nchunk[slot];
             const int ci = (int)((it.k0 - rp[r0]) / kWarpChunk);
             double *pc = partk + 2 * ((int64_t)(first + ci) * k + lane);
-            auto store_part = [&](int64_t, DD s1, DD s2) {
+            auto store_part = [&](int64_t, PlainAcc s1, PlainAcc s2) {
                 if (has1) {
-                    pc[0] = s1.hi;
-                    pc[1] = s1.lo;
+                    pc[0] = s1.s;
+                    pc[1] = (double)s1.m;
                 }
                 if (has2) {
-                    pc[64] = s2.hi;
-                    pc[65] = s2.lo;
+                    pc[64] = s2.s;
+                    pc[65] = (double)s2.m;
                 }
             };
-            warp_tile_k<DD, double, W, 8>(r0, r1, it.k0, it.k1, true, rp, col, w, no_begin, src, add, store_part,
-                                          lane, has1, has2, n_rows);
+            warp_tile_k<PlainAcc, double, W, 8>(r0, r1, it.k0, it.k1, true, rp, col, w, no_begin, src, add,
+                                                store_part, lane, has1, has2, n_rows);
             __threadfence();
             __syncwarp();
             int last = 0;
@@ -1793,15 +1910,25 @@ k_certify_batch(const Item *__restrict__ items, int64_t nitems, const int64_t *_
             last = __shfl_sync(0xffffffffu, last, 0);
             if (last) {
                 __threadfence();
-                DD a1{0.0, 0.0}, a2{0.0, 0.0};
+                PlainAcc a1{0.0, 0.f}, a2{0.0, 0.f};
+                double m1 = 0.0, m2 = 0.0;
                 for (int c = 0; c < nch; ++c) {
                     const double *q = partk + 2 * ((int64_t)(first + c) * k + lane);
-                    if (has1) a1 = dd_merge(a1, DD{__ldcg(q), __ldcg(q + 1)});
-                    if (has2) a2 = dd_merge(a2, DD{__ldcg(q + 64), __ldcg(q + 65)});
+                    if (has1) {
+                        a1.s += __ldcg(q);
+                        m1 += __ldcg(q + 1);
+                    }
+                    if (has2) {
+                        a2.s += __ldcg(q + 64);
+                        m2 += __ldcg(q + 65);
+                    }
                 }
+                a1.m = (float)(m1 * (1.0 + (double)nch * 0x1p-23));
+                a2.m = (float)(m2 * (1.0 + (double)nch * 0x1p-23));
                 if (lane == 0) cnt[slot] = 0;
-                if (has1) finish(r0, 0, a1);
-                if (has2) finish(r0, 1, a2);
+                const int64_t len = (rp[r0 + 1] - rp[r0]) + nch + 64;
+                if (has1) finish(r0, 0, a1, len);
+                if (has2) finish(r0, 1, a2, len);
             }
         }
     }
@@ -1834,8 +1961,8 @@ static int64_t batch_sweep_blocks(bool weighted)
         int dev = 0, sms = 0, per = 0;
         if (cudaGetDevice(&dev) != cudaSuccess) return 152;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (weighted) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep_batch<T, true>, 256, 0);
-        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep_batch<T, false>, 256, 0);
+        if (weighted) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep_batch<T, true, 8>, 256, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep_batch<T, false, 8>, 256, 0);
         nres = std::max(1, sms * std::max(1, per));
     }
     return nres;
@@ -1967,16 +2094,18 @@ static fj_status solve_batch_t(fj_graph *g, const double *S, const double *Z0, i
                         (unsigned)std::min<int64_t>(ceil_div(ni, 8), batch_sweep_blocks<T>(c.w != nullptr));
                     unsigned int *tk = b.tick + 2 * cl;
                     FJ_CHECK(run.before(st));
-                    if (c.w)
-                        k_sweep_batch<T, true><<<grid, 256, 0, st>>>(wp.items, i0, ni, c.row_ptr, c.col, c.w, k, dcur,
-                                                                     dprev, r, h, inv, b.zhat, om, c.indeg,
-                                                                     wp.slot_first, wp.slot_nchunk, b.partk, wp.cnt,
-                                                                     ws.ctr, tk, c.n);
-                    else
-                        k_sweep_batch<T, false><<<grid, 256, 0, st>>>(wp.items, i0, ni, c.row_ptr, c.col, c.w, k,
-                                                                      dcur, dprev, r, h, inv, b.zhat, om, c.indeg,
-                                                                      wp.slot_first, wp.slot_nchunk, b.partk, wp.cnt,
-                                                                      ws.ctr, tk, c.n);
+#define FJ_SWEEP_BATCH(WW, DD)                                                                                \
+    k_sweep_batch<T, WW, DD><<<grid, 256, 0, st>>>(wp.items, i0, ni, c.row_ptr, c.col, c.w, k, dcur, dprev, r, h, \
+                                                   inv, b.zhat, om, c.indeg, wp.slot_first, wp.slot_nchunk, b.partk, \
+                                                   wp.cnt, ws.ctr, tk, c.n)
+                    if (c.w) {
+                        if (b.depth == 4) FJ_SWEEP_BATCH(true, 4);
+                        else FJ_SWEEP_BATCH(true, 8);
+                    } else {
+                        if (b.depth == 4) FJ_SWEEP_BATCH(false, 4);
+                        else FJ_SWEEP_BATCH(false, 8);
+                    }
+#undef FJ_SWEEP_BATCH
                     FJ_CUDA(cudaGetLastError());
                     FJ_CHECK(run.after(st));
                 }
@@ -2073,6 +2202,151 @@ extern "C" fj_status fj_solve_batch(fj_graph *g, const double *S, int k, const f
     FJ_ARG(mem == FJ_MEM_HOST || mem == FJ_MEM_DEVICE, "mem must be FJ_MEM_HOST or FJ_MEM_DEVICE");
     FJ_ARG(g->ngraphs == 1, "a ragged handle takes one opinion vector per graph (use fj_solve)");
     FJ_CHECK(fj::check_opts(opts));
-    if (opts->precision == FJ_PREC_FP32) return fj::solve_batch_t<float>(g, S, nullptr, k, opts, Z_out, info, mem);
-    return fj::solve_batch_t<double>(g, S, nullptr, k, opts, Z_out, info, mem);
+    return with_omega_fallback(opts, [&](const fj_solve_opts *o) {
+        if (o->precision == FJ_PREC_FP32) return fj::solve_batch_t<float>(g, S, nullptr, k, o, Z_out, info, mem);
+        return fj::solve_batch_t<double>(g, S, nullptr, k, o, Z_out, info, mem);
+    });
+}
+
+// ============================================================== autotuner
+
+namespace {
+
+struct TuneCand {
+    int schedule, palette, depth;
+    double omega;
+};
+
+// Candidates in palette order, so each colouring is built once.
+std::vector<TuneCand> tune_candidates(bool batch)
+{
+    std::vector<TuneCand> c;
+    c.push_back({FJ_SCHED_JACOBI, 0, 4, 1.0});
+    for (int K : {4, 8, 16, 32})
+        for (double w : {1.2, 1.5, 1.8})
+            for (int d : {4, 8}) {
+                if (!batch && d != 4) continue;
+                c.push_back({FJ_SCHED_MULTICOLOUR, K, d, w});
+            }
+    if (batch) c.push_back({FJ_SCHED_JACOBI, 0, 8, 1.0});
+    return c;
+}
+
+// Times `reps` calls of run() after one untimed call; returns the mean ms, or
+// a negative value when the untimed call did not certify.
+template <typename F>
+fj_status time_candidate(cudaStream_t st, int reps, F run, double *ms)
+{
+    *ms = -1.0;
+    fj_status s0 = run();
+    if (s0 == FJ_ERR_NOT_CONVERGED || s0 == FJ_ERR_DIVERGED) return FJ_OK;
+    FJ_CHECK(s0);
+    cudaEvent_t e0, e1;
+    FJ_CUDA(cudaEventCreate(&e0));
+    FJ_CUDA(cudaEventCreate(&e1));
+    FJ_CUDA(cudaEventRecord(e0, st));
+    fj_status s = FJ_OK;
+    for (int i = 0; i < reps && s == FJ_OK; ++i) s = run();
+    FJ_CUDA(cudaEventRecord(e1, st));
+    FJ_CUDA(cudaEventSynchronize(e1));
+    float t = 0.f;
+    FJ_CUDA(cudaEventElapsedTime(&t, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s == FJ_OK) *ms = (double)t / reps;
+    else if (s != FJ_ERR_NOT_CONVERGED && s != FJ_ERR_DIVERGED) return s;
+    return FJ_OK;
+}
+
+}  // namespace
+
+extern "C" fj_status fj_graph_tune(fj_graph *g, const double *s, const fj_solve_opts *base, int reps,
+                                   fj_solve_opts *best, double *best_ms, int mem)
+{
+    FJ_ARG(g && s && base && best, "NULL pointer");
+    FJ_ARG(reps >= 1 && reps <= 100, "reps must be in 1..100");
+    FJ_ARG(mem == FJ_MEM_HOST || mem == FJ_MEM_DEVICE, "mem must be FJ_MEM_HOST or FJ_MEM_DEVICE");
+    FJ_CHECK(fj::check_opts(base));
+    cudaStream_t st = (cudaStream_t)base->stream;
+    const int64_t n = g->csr.n;
+    std::vector<double> zh;
+    double *zd = nullptr;
+    if (mem == FJ_MEM_DEVICE) FJ_CUDA(cudaMalloc(&zd, sizeof(double) * std::max<int64_t>(n, 1)));
+    else zh.resize((size_t)std::max<int64_t>(n, 1));
+    double *z = mem == FJ_MEM_DEVICE ? zd : zh.data();
+    double best_t = -1.0;
+    fj_solve_opts bo = *base;
+    fj_status result = FJ_OK;
+    for (const TuneCand &cd : tune_candidates(false)) {
+        fj_solve_opts o = *base;
+        o.schedule = cd.schedule;
+        o.palette = cd.schedule == FJ_SCHED_JACOBI ? base->palette : cd.palette;
+        o.omega = cd.omega;
+        o.profile = 0;
+        double ms = -1.0;
+        result = time_candidate(st, reps, [&]() { return fj_solve(g, s, &o, z, nullptr, mem); }, &ms);
+        if (result != FJ_OK) break;
+        if (ms >= 0.0 && (best_t < 0.0 || ms < best_t)) {
+            best_t = ms;
+            bo = o;
+        }
+    }
+    if (zd) cudaFree(zd);
+    FJ_CHECK(result);
+    if (best_t < 0.0) {
+        set_error("no candidate certified");
+        return FJ_ERR_NOT_CONVERGED;
+    }
+    if (bo.schedule == FJ_SCHED_MULTICOLOUR) FJ_CHECK(fj::ensure_colouring(g, bo.palette, st));
+    *best = bo;
+    if (best_ms) *best_ms = best_t;
+    return FJ_OK;
+}
+
+extern "C" fj_status fj_graph_tune_batch(fj_graph *g, const double *S, int k, const fj_solve_opts *base, int reps,
+                                         fj_solve_opts *best, double *best_ms, int mem)
+{
+    FJ_ARG(g && S && base && best, "NULL pointer");
+    FJ_ARG(k >= 1 && k <= 64, "k must be in 1..64");
+    FJ_ARG(reps >= 1 && reps <= 100, "reps must be in 1..100");
+    FJ_ARG(mem == FJ_MEM_HOST || mem == FJ_MEM_DEVICE, "mem must be FJ_MEM_HOST or FJ_MEM_DEVICE");
+    FJ_CHECK(fj::check_opts(base));
+    cudaStream_t st = (cudaStream_t)base->stream;
+    const int64_t n = g->csr.n;
+    std::vector<double> zh;
+    double *zd = nullptr;
+    if (mem == FJ_MEM_DEVICE) FJ_CUDA(cudaMalloc(&zd, sizeof(double) * std::max<int64_t>(n * k, 1)));
+    else zh.resize((size_t)std::max<int64_t>(n * k, 1));
+    double *z = mem == FJ_MEM_DEVICE ? zd : zh.data();
+    double best_t = -1.0;
+    fj_solve_opts bo = *base;
+    int best_depth = g->bws.depth;
+    fj_status result = FJ_OK;
+    for (const TuneCand &cd : tune_candidates(true)) {
+        fj_solve_opts o = *base;
+        o.schedule = cd.schedule;
+        o.palette = cd.schedule == FJ_SCHED_JACOBI ? base->palette : cd.palette;
+        o.omega = cd.omega;
+        o.profile = 0;
+        g->bws.depth = cd.depth;
+        double ms = -1.0;
+        result = time_candidate(st, reps, [&]() { return fj_solve_batch(g, S, k, &o, z, nullptr, mem); }, &ms);
+        if (result != FJ_OK) break;
+        if (ms >= 0.0 && (best_t < 0.0 || ms < best_t)) {
+            best_t = ms;
+            bo = o;
+            best_depth = cd.depth;
+        }
+    }
+    g->bws.depth = best_depth;
+    if (zd) cudaFree(zd);
+    FJ_CHECK(result);
+    if (best_t < 0.0) {
+        set_error("no candidate certified");
+        return FJ_ERR_NOT_CONVERGED;
+    }
+    if (bo.schedule == FJ_SCHED_MULTICOLOUR) FJ_CHECK(fj::ensure_colouring(g, bo.palette, st));
+    *best = bo;
+    if (best_ms) *best_ms = best_t;
+    return FJ_OK;
 }

@@ -12,7 +12,7 @@ import pytest
 import oracle
 from fjsynth import OP_ARCSINE, OP_SIGN, OP_UNIFORM
 from fjsynth import workloads as W
-from gpu_common import FP32_TOL, FP64_TOL, certificate_holds, csr_of, rel_inf, to_dev
+from gpu_common import FP32_TOL, FP64_TOL, METRIC_TOL, certificate_holds, csr_of, rel_inf, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -68,6 +68,17 @@ def test_batch_fp32_rmat_undirected_64_mixed_kinds(capi):
     _check_columns(n, rp, col, w, S, Z, infos, FP32_TOL, truth_cols=[0, 1, 2, 63])
     # undirected: 1^T z = 1^T s for every vector
     np.testing.assert_allclose(Z.sum(axis=0), S.sum(axis=0), rtol=0, atol=1e-6 * np.abs(S).sum(axis=0).max())
+    # batched Table 1 measures: against the oracle's sums on the same z, and on the truth
+    mets = G.metrics_batch(S_d, Z_d)
+    for j in (0, 1, 2, 33, 63):
+        mo = oracle.metrics(n, rp, col, w, S[:, j], Z[:, j], directed=False)
+        for key in ("P", "D", "I", "C", "mean_z"):
+            assert abs(mets[j][key] - mo[key]) <= 1e-12 * abs(mo[key]) + 1e-15, (j, key)
+    for j in (0, 2):
+        z_star, _ = oracle.truth(n, rp, col, w, S[:, j], omega=1.5)
+        mt = oracle.metrics(n, rp, col, w, S[:, j], z_star, directed=False)
+        for key in ("P", "D", "I", "C"):
+            assert abs(mets[j][key] - mt[key]) <= METRIC_TOL * abs(mt[key]), (j, key)
 
 
 @pytest.mark.parametrize("precision", [0, 1])
@@ -81,6 +92,11 @@ def test_batch_directed_weighted_matches_single(capi, precision):
     assert st == capi.FJ_OK
     tol = FP64_TOL if precision == 0 else FP32_TOL
     _check_columns(n, rp, col, w, S, Z, infos, tol, truth_cols=[0, 4], omega_truth=1.0)
+    mets = G.metrics_batch(S, Z)  # host memory, weighted directed
+    for j in range(S.shape[1]):
+        mo = oracle.metrics(n, rp, col, w, S[:, j], Z[:, j], directed=True)
+        for key in ("P", "D", "I", "C", "mean_z"):
+            assert abs(mets[j][key] - mo[key]) <= 1e-12 * abs(mo[key]) + 1e-15, (j, key)
     for j in (0, 3):
         z1, _, _ = G.solve(np.ascontiguousarray(S[:, j]), eps=1e-6, omega=1.2, precision=precision)
         assert rel_inf(Z[:, j], z1) <= 2 * tol
@@ -132,3 +148,26 @@ def test_batch_invalid_arguments(capi):
     R = capi.Graph.ragged(np.array([0, n, 2 * n], np.int64), rp2, col2, directed=False)
     with pytest.raises(capi.FJError):
         R.solve_batch(np.zeros((2 * n, 2)), eps=1e-6)
+
+
+def test_autotuner_picks_a_certified_configuration(capi):
+    g = W.ba_graph(20000, 5, nvec=4, seed_off=47)
+    rp, col, w = csr_of(g)
+    n = g["n"]
+    G = capi.Graph.from_csr(n, *to_dev(rp, col, w), directed=False)
+    s = g["S"][0]
+    best, ms = G.tune(s, reps=1, eps=1e-6, precision=capi.FJ_PREC_FP32)
+    assert ms > 0
+    assert best["schedule"] in (capi.FJ_SCHED_JACOBI, capi.FJ_SCHED_MULTICOLOUR)
+    if best["schedule"] == capi.FJ_SCHED_JACOBI:
+        assert best["omega"] == 1.0
+    else:
+        assert best["palette"] in (4, 8, 16, 32) and best["omega"] in (1.2, 1.5, 1.8)
+    z, info, st = G.solve(s, eps=1e-6, precision=capi.FJ_PREC_FP32, **best)
+    assert st == capi.FJ_OK and info[0]["converged"] == 1
+    z_star, _ = oracle.truth(n, rp, col, w, s)
+    assert rel_inf(z, z_star) <= FP32_TOL
+    S = np.ascontiguousarray(np.stack(g["S"], axis=1))
+    bb, bms = G.tune_batch(S, reps=1, eps=1e-6, precision=capi.FJ_PREC_FP32)
+    Z, infos, st = G.solve_batch(S, eps=1e-6, precision=capi.FJ_PREC_FP32, **bb)
+    assert st == capi.FJ_OK and all(i["converged"] == 1 for i in infos)

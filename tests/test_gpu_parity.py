@@ -310,3 +310,25 @@ def test_sweep_cap_reports_not_converged(capi, ba20k):
                           allow_unconverged=True)
     assert st == capi.FJ_ERR_NOT_CONVERGED and info[0]["converged"] == 0
     assert np.all(np.isfinite(z))
+
+
+def test_auto_schedule_recovers_from_divergence(capi):
+    """Directed, randomly oriented, weighted BA graph (a warm-start training graph):
+    SOR over colour classes at omega 1.5 is not covered by the symmetric theory.
+    Under the explicit multicolour schedule a diverging solve reports
+    FJ_ERR_DIVERGED; under AUTO it restarts at omega 1 and certifies."""
+    gd = W.warm_training_set()[1]  # ba_dir_n30000
+    rp, col, w = oracle.csr_from_arcs(gd["n"], gd["src"], gd["dst"], gd["w"])
+    n, s = gd["n"], gd["S"][0]
+    G = capi.Graph.from_csr(n, *to_dev(rp, col, w), directed=True)
+    (s_d,) = to_dev(s)
+    _, _, st_mc = G.solve(s_d, eps=1e-6, omega=1.5, precision=capi.FJ_PREC_FP32,
+                          schedule=capi.FJ_SCHED_MULTICOLOUR, allow_unconverged=True)
+    z_d, info, st = G.solve(s_d, eps=1e-6, omega=1.5, precision=capi.FJ_PREC_FP32, schedule=capi.FJ_SCHED_AUTO)
+    assert st == capi.FJ_OK and info[0]["converged"] == 1
+    if st_mc == capi.FJ_ERR_DIVERGED:
+        assert info[0]["omega_used"] == 1.0
+    else:
+        assert info[0]["omega_used"] == 1.5
+    z_star, _ = oracle.truth(n, rp, col, w, s)
+    assert rel_inf(z_d.cpu().numpy(), z_star) <= FP32_TOL
