@@ -132,6 +132,22 @@ def dist_init():
     return world, rank, local
 
 
+def max_over_ranks(x: float, device) -> float:
+    """The largest value of x over all ranks (replicas exchange only this scalar)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(units_per_step: float, steps: int, world: int, ms: float) -> float:
+    """Units all ranks processed per second, over the slowest rank's time."""
+    return world * steps * units_per_step / (ms / 1e3)
+
+
 # ------------------------------------------------------------------ oracle arm
 
 def oracle_solve_time(name, scale, omega):
@@ -258,6 +274,18 @@ def run_gpu(args):
             dist.barrier()
         torch.cuda.synchronize()
 
+    tuned = None
+    if args.tune and cols is None:
+        # autotuner (outside the timed region): schedule, palette, omega (and the batch gather depth)
+        t0 = time.perf_counter()
+        if k == 1:
+            best, best_ms = G.tune(s_d, reps=1, **opts)
+        else:
+            best, best_ms = G.tune_batch(s_d, reps=1, **opts)
+        opts.update(best)
+        palette = best["palette"]
+        omega = best["omega"]
+        tuned = dict(best, tune_s=time.perf_counter() - t0, best_ms=best_ms)
     for _ in range(args.warmup):
         solve(s_d, z_d, **opts)
     barrier()
@@ -271,14 +299,9 @@ def run_gpu(args):
     ev1.record(stream)
     barrier()
     clocks = clocks_stop(clk, clk_path, local) if rank == 0 else None
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dev)
     ms_per_step = ms / args.steps
-    value = world * args.steps * k / (ms / 1e3)
+    value = whole_job_value(k, args.steps, world, ms)
     assert all(i["converged"] == 1 for i in infos), "a timed solve did not certify"
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
@@ -290,13 +313,8 @@ def run_gpu(args):
     for _ in range(args.steps):
         solve(s_pin, z_pin, **opts)
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * args.steps * k / e2e_s
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
+    e2e_value = whole_job_value(k, args.steps, world, e2e_s * 1e3)
 
     # roofline of the push kernel: algorithmic bytes over CUDA-event time of its launches
     if cols is not None:
@@ -337,8 +355,9 @@ def run_gpu(args):
             "config": {"workload": args.workload, "n": n, "nnz": ginfo["nnz"], "directed": g["directed"],
                        "vectors": k, "palette": palette,
                        "mode": ("batched (fj_solve_batch)" if k > 1 and cols is None else
-                                "plain (one fj_solve per vector)"),
-                       "omega": omega, "eps": EPS, "schedule": "multicolour" if args.schedule != 1 else "jacobi",
+                                "plain (one fj_solve per vector)"), "tuned": tuned,
+                       "omega": omega, "eps": EPS,
+                       "schedule": {0: "auto (multicolour)", 1: "jacobi", 2: "multicolour"}[opts["schedule"]],
                        "precision": "FP32 push, FP64 estimate and certificate" if prec == capi.FJ_PREC_FP32
                        else "FP64", "l2": "inputs larger than L2 (CSR %.2f GB)" % (
                            ginfo["nnz"] * (8 if w is not None else 4) / 1e9),
@@ -450,21 +469,15 @@ def run_warm(args):
             fn(infos)
         ev1.record(stream)
         barrier()
-        ms = ev0.elapsed_time(ev1)
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms, infos
+        return max_over_ranks(ev0.elapsed_time(ev1), dev), infos
 
     ms_zero, inf_zero = timed(zero_step)
     clk, clk_path = clocks_start() if rank == 0 else (None, None)
     ms_warm, inf_warm = timed(warm_step)
     clocks = clocks_stop(clk, clk_path, local) if rank == 0 else None
     assert all(i["converged"] == 1 for i in inf_warm + inf_zero), "a timed solve did not certify"
-    value = world * args.steps * k / (ms_warm / 1e3)
-    zero_value = world * args.steps * k / (ms_zero / 1e3)
+    value = whole_job_value(k, args.steps, world, ms_warm)
+    zero_value = whole_job_value(k, args.steps, world, ms_zero)
     # predict time alone
     barrier()
     ev0.record(stream)
@@ -485,7 +498,7 @@ def run_warm(args):
             net.predict(G, sp, out=z0_pin)
             G.solve(sp, out=z_pin, z0=z0_pin, **opts)
     barrier()
-    e2e_value = world * args.steps * k / (time.perf_counter() - t0)
+    e2e_value = whole_job_value(k, args.steps, world, max_over_ranks(time.perf_counter() - t0, dev) * 1e3)
 
     _, pinfo, _ = G.solve(S[0], out=z_d, z0=z0_d, profile=1, **opts)
     p = pinfo[0]
@@ -496,13 +509,26 @@ def run_warm(args):
                 "kernel": "k_products + k_sweep (one colour class)", "peak_source": peak_kind,
                 "bytes_per_launch": p["push_bytes"] / max(1, p["push_launches"]),
                 "avg_launch_us": 1e3 * p["push_ms"] / max(1, p["push_launches"])}
+    # quality of the start: z0 against the certified zero-start solution, and the
+    # share of nodes whose initial residual is above threshold (zero start: all)
+    zq = {}
+    for j in range(min(k, 4)):
+        net.predict(G, S[j], out=z0_d)
+        _, inf0, _ = G.solve(S[j], out=z_d, **opts)
+        z0 = z0_d.cpu().numpy()
+        zz = z_d.cpu().numpy()
+        zq.setdefault("z0_err_inf_rel", []).append(float(np.max(np.abs(z0 - zz)) / np.max(np.abs(zz))))
+        zq.setdefault("z0_err_rms", []).append(float(np.sqrt(np.mean((z0 - zz) ** 2))))
+        sv = g["S"][j]
+        zq.setdefault("s_err_rms", []).append(float(np.sqrt(np.mean((sv - zz) ** 2))))
+    zq = {key: float(np.mean(v)) for key, v in zq.items()}
     mean = lambda xs: float(np.mean(xs)) if xs else None
     detail = {"zero_start_solves_per_s": zero_value, "warm_vs_zero": value / zero_value,
               "sweeps_warm": mean([i["sweeps"] for i in inf_warm]),
               "sweeps_zero": mean([i["sweeps"] for i in inf_zero]),
               "predict_ms": predict_ms, "train_s": train_s, "train_steps": spec["train_steps"],
               "train_loss_first": losses[0], "train_loss_last": float(np.mean(losses[-20:])),
-              "ncolours": ginfo["ncolours"], "vectors_per_step": k}
+              "ncolours": G.info()["ncolours"], "vectors_per_step": k, **zq}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu_scale = args.cpu_scale if args.cpu_scale is not None else spec.get("cpu_scale")
@@ -609,9 +635,9 @@ def run_ragged(args):
     ev1.record(stream)
     barrier()
     clocks = clocks_stop(clk, clk_path, local) if rank == 0 else None
-    ms = ev0.elapsed_time(ev1)
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dev)
     assert all(i["converged"] == 1 for i in infos), "a timed solve did not certify"
-    value = world * args.steps * ng / (ms / 1e3)
+    value = whole_job_value(ng, args.steps, world, ms)
     e2e_value = None
     if not args.plain_loop:
         s_pin = torch.from_numpy(s_host).pin_memory().numpy()
@@ -622,7 +648,7 @@ def run_ragged(args):
             G.solve(s_pin, out=z_pin, **opts)
             G.metrics(s_pin, z_pin)
         barrier()
-        e2e_value = world * args.steps * ng / (time.perf_counter() - t0)
+        e2e_value = whole_job_value(ng, args.steps, world, max_over_ranks(time.perf_counter() - t0, dev) * 1e3)
         _, pinfo, _ = G.solve(s_d, out=z_d, profile=1, **opts)
         p = pinfo[0]
     else:
@@ -672,6 +698,8 @@ def main():
                     help="R-MAT scale of the CPU-baseline sample (default: the full workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--palette", type=int, default=None)
+    ap.add_argument("--tune", action="store_true",
+                    help="run the autotuner (fj_graph_tune / fj_graph_tune_batch) before timing")
     ap.add_argument("--plain-loop", action="store_true",
                     help="multi-vector workloads: solve the vectors one fj_solve call each")
     args = ap.parse_args()

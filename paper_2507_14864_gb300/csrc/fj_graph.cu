@@ -795,17 +795,13 @@ __device__ __forceinline__ bool higher(unsigned long long ku, int64_t u, unsigne
     return ku > kv || (ku == kv && u < v);
 }
 
-struct UncolouredPred {
-    const int32_t *colour;
-    __device__ bool operator()(int64_t v) const { return colour[v] < 0; }
-};
-
 // One Jones-Plassmann round over the uncoloured worklist, a warp per node.  A
 // node whose higher-priority neighbours are all coloured takes the smallest
 // colour none of its coloured neighbours holds (only higher-priority ones can
 // be coloured at that point), which reproduces sequential greedy colouring in
 // priority order whatever the timing of other warps.
-__global__ void k_jp_round(int64_t cnt, const int32_t *__restrict__ list, const int64_t *__restrict__ rp,
+__global__ void k_jp_round(const long long *__restrict__ cntp, const int32_t *__restrict__ list,
+                           const int64_t *__restrict__ rp,
                            const int32_t *__restrict__ col, const int64_t *__restrict__ tp,
                            const int32_t *__restrict__ tc, const unsigned long long *__restrict__ key,
                            int32_t *colour)
@@ -815,6 +811,7 @@ __global__ void k_jp_round(int64_t cnt, const int32_t *__restrict__ list, const 
     const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     volatile int32_t *vc = colour;
+    const int64_t cnt = *cntp;
     for (int64_t i = warp0; i < cnt; i += nwarps) {
         const int32_t v = list[i];
         const unsigned long long kv = key[v];
@@ -871,7 +868,8 @@ __device__ __forceinline__ unsigned long long fixed_q(const float *w, int64_t k)
 // atomics in shared memory) and takes the smallest colour with zero weight,
 // else the colour of least weight (smallest on ties): the same choice as the
 // sequential greedy pass in priority order.
-__global__ void k_jp_palette_round(int64_t cnt, const int32_t *__restrict__ list, const int64_t *__restrict__ rp,
+__global__ void k_jp_palette_round(const long long *__restrict__ cntp, const int32_t *__restrict__ list,
+                                   const int64_t *__restrict__ rp,
                                    const int32_t *__restrict__ col, const float *__restrict__ w,
                                    const int64_t *__restrict__ tp, const int32_t *__restrict__ tc,
                                    const float *__restrict__ tw, const unsigned long long *__restrict__ key, int K,
@@ -882,6 +880,7 @@ __global__ void k_jp_palette_round(int64_t cnt, const int32_t *__restrict__ list
     const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     volatile int32_t *vc = colour;
+    const int64_t cnt = *cntp;
     for (int64_t i = warp0; i < cnt; i += nwarps) {
         const int32_t v = list[i];
         const unsigned long long kv = key[v];
@@ -1052,6 +1051,38 @@ __global__ void k_colour_keys(int64_t n, const int32_t *__restrict__ colour, con
     }
 }
 
+// Worklist of the next round: the nodes of this round's list still uncoloured
+// (order is irrelevant: a round's result does not depend on it), appended with
+// one atomic per warp.
+__global__ void k_requeue(const long long *__restrict__ cnt_in, const int32_t *__restrict__ in,
+                          const int32_t *__restrict__ colour, long long *cnt_out, int32_t *__restrict__ out)
+{
+    const int64_t cnt = *cnt_in;
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < cnt; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        int32_t v = -1;
+        if (i < cnt) v = in[i];
+        const bool keep = v >= 0 && colour[v] < 0;
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        long long at = 0;
+        if (lane == 0 && m)
+            at = (long long)atomicAdd(reinterpret_cast<unsigned long long *>(cnt_out), (unsigned long long)__popc(m));
+        at = __shfl_sync(0xffffffffu, at, 0);
+        if (keep) out[at + __popc(m & lanemask_lt())] = v;
+    }
+}
+
+__global__ void k_iota_list(int64_t n, int32_t *__restrict__ out, long long *cnt)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (int32_t)i;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        cnt[0] = n;
+        cnt[1] = 0;
+    }
+}
+
 static fj_status colour_graph(fj_graph *g, int palette, cudaStream_t st)
 {
     DevCSR &c = g->csr;
@@ -1067,26 +1098,49 @@ static fj_status colour_graph(fj_graph *g, int palette, cudaStream_t st)
     k_sym_degree<<<grid_for(n * 32, 256), 256, 0, st>>>(n, c.row_ptr, c.col, tp, tc, key);
     k_fill_i32<<<grid_for(n, 256), 256, 0, st>>>(n, cl.colour, -1);
     FJ_CUDA(cudaGetLastError());
-    FJ_CHECK(ws_status(g->ws, scan_tiles(n, 256 * 8)));
+    // Jones-Plassmann rounds over a shrinking worklist (ping-pong buffers, count
+    // on the device); the host reads the count every kBatch rounds
+    constexpr int kBatch = 16;
+    int32_t *lists[2] = {list, nullptr};
+    long long *cnts = nullptr;
+    FJ_CUDA(dalloc(&lists[1], n));
+    FJ_CUDA(dalloc(&cnts, 2));
+    k_iota_list<<<grid_for(n, 256), 256, 0, st>>>(n, lists[0], cnts);
+    FJ_CUDA(cudaGetLastError());
     long long left = n;
-    int rounds = 0;
+    int64_t rounds = 0;
+    int cur = 0;
+    fj_status result = FJ_OK;
     while (left > 0) {
-        FJ_CUDA(compact<256, 8>(n, UncolouredPred{cl.colour}, list, g->ws.count, g->ws.status, g->ws.tile_ctr,
-                                g->err, st));
-        FJ_CUDA(cudaMemcpyAsync(&left, g->ws.count, sizeof(long long), cudaMemcpyDeviceToHost, st));
-        FJ_CUDA(cudaStreamSynchronize(st));
-        if (left == 0) break;
-        if (++rounds > 1000000) {
-            set_error("colouring did not finish");
-            return FJ_ERR_TIMEOUT;
+        const unsigned grid = grid_for(left * 32, 256, 152 * 64);
+        const unsigned qgrid = grid_for(left, 256, 152 * 16);
+        for (int b = 0; b < kBatch; ++b) {
+            const long long *cin = cnts + cur;
+            if (palette > 0)
+                k_jp_palette_round<<<grid, 256, 0, st>>>(cin, lists[cur], c.row_ptr, c.col, c.w, tp, tc,
+                                                         g->directed ? g->tw : nullptr, key, palette, cl.colour);
+            else
+                k_jp_round<<<grid, 256, 0, st>>>(cin, lists[cur], c.row_ptr, c.col, tp, tc, key, cl.colour);
+            FJ_CUDA(cudaMemsetAsync(cnts + (cur ^ 1), 0, sizeof(long long), st));
+            k_requeue<<<qgrid, 256, 0, st>>>(cin, lists[cur], cl.colour, cnts + (cur ^ 1), lists[cur ^ 1]);
+            FJ_CUDA(cudaGetLastError());
+            cur ^= 1;
         }
-        if (palette > 0)
-            k_jp_palette_round<<<grid_for(left * 32, 256, 152 * 64), 256, 0, st>>>(
-                left, list, c.row_ptr, c.col, c.w, tp, tc, g->directed ? g->tw : nullptr, key, palette, cl.colour);
-        else
-            k_jp_round<<<grid_for(left * 32, 256, 152 * 64), 256, 0, st>>>(left, list, c.row_ptr, c.col, tp, tc,
-                                                                          key, cl.colour);
-        FJ_CUDA(cudaGetLastError());
+        rounds += kBatch;
+        FJ_CUDA(cudaMemcpyAsync(&left, cnts + cur, sizeof(long long), cudaMemcpyDeviceToHost, st));
+        FJ_CUDA(cudaStreamSynchronize(st));
+        if (left > 0 && rounds > 4000000) {
+            set_error("colouring did not finish");
+            result = FJ_ERR_TIMEOUT;
+            break;
+        }
+    }
+    dev_free(lists[1]);
+    dev_free(cnts);
+    if (result != FJ_OK) {
+        dev_free(key);
+        dev_free(list);
+        return result;
     }
     dev_free(key);
     dev_free(list);
@@ -1230,6 +1284,7 @@ fj_status ensure_colouring(fj_graph *g, int palette, cudaStream_t st)
     long long *excl = nullptr;
     FJ_CUDA(dalloc(&excl, n + 1));
     k_perm_rowlen<<<grid_for(n, 256), 256, 0, st>>>(n, cl.perm, c.row_ptr, len);
+    FJ_CHECK(ws_status(g->ws, scan_tiles(n, 256 * 8)));
     FJ_CUDA(scan<256, 8>(n, I32Load{len}, excl, g->ws.count, g->ws.status, g->ws.tile_ctr, g->err, st));
     FJ_CUDA(dalloc(&p.row_ptr, n + 1));
     k_finish_ptr<<<grid_for(n + 1, 256), 256, 0, st>>>(n, excl, nnz, p.row_ptr);

@@ -87,7 +87,14 @@ struct ItemPlan {
     int64_t nparts = 0;
     std::vector<int64_t> class_item;  // host: items of class c are [class_item[c], class_item[c+1])
     std::vector<int64_t> class_k;     // host: nonzeros of class c are [class_k[c], class_k[c+1])
+    // host: sweep segments, classes cut at item boundaries into runs of at most
+    // kSegNnz nonzeros (so one segment's products stay in L2): segment s covers
+    // items [seg_item[s], seg_item[s+1]) and nonzeros [seg_k[s], seg_k[s+1]) of
+    // class seg_class[s]
+    std::vector<int64_t> seg_item, seg_k;
+    std::vector<int32_t> seg_class;
 };
+constexpr int64_t kSegNnz = int64_t(1) << 24;
 
 // Solve scratch, grown on demand and kept by the handle.
 struct Workspace {

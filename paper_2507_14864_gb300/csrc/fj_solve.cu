@@ -981,6 +981,25 @@ static fj_status build_items(fj_graph *g, const DevCSR &c, const std::vector<int
     ip.class_k.assign(ip.class_item.size(), bk.empty() ? 0 : bk.back());
     for (size_t k = 0; k + 1 < ip.class_item.size(); ++k)
         ip.class_k[k] = ip.class_item[k] < ip.nitems ? items[(size_t)ip.class_item[k]].k0 : bk.back();
+    // sweep segments: each class cut into item runs of at most kSegNnz nonzeros
+    ip.seg_item.clear();
+    ip.seg_k.clear();
+    ip.seg_class.clear();
+    for (size_t c = 0; c + 1 < ip.class_item.size(); ++c) {
+        int64_t i = ip.class_item[c];
+        const int64_t iend = ip.class_item[c + 1];
+        while (i < iend) {
+            const int64_t kstart = items[(size_t)i].k0;
+            int64_t j = i + 1;
+            while (j < iend && items[(size_t)j].k1 - kstart <= kSegNnz) ++j;
+            ip.seg_item.push_back(i);
+            ip.seg_k.push_back(kstart);
+            ip.seg_class.push_back((int32_t)c);
+            i = j;
+        }
+    }
+    ip.seg_item.push_back(ip.nitems);
+    ip.seg_k.push_back(ip.nitems > 0 ? items.back().k1 : 0);
     ip.nparts = nparts;
     FJ_CUDA(cudaMalloc(&ip.items, sizeof(Item) * std::max<size_t>(items.size(), 1)));
     FJ_CUDA(cudaMalloc(&ip.slot_first, sizeof(int32_t) * std::max<size_t>(sfirst.size(), 1)));
@@ -1065,12 +1084,13 @@ static fj_status launch_sweep(fj_graph *g, const Plan &p, cudaStream_t st, Run &
     T *prod = reinterpret_cast<T *>(ws.prod);
     const int32_t *lo_of = nullptr;
     (void)lo_of;
-    for (size_t k = 0; k + 1 < wp.class_item.size(); ++k) {
-        const int64_t i0 = wp.class_item[k], ni = wp.class_item[k + 1] - i0;
+    // segment by segment (a class cut into runs whose products stay in L2)
+    for (size_t sg = 0; sg + 1 < wp.seg_item.size(); ++sg) {
+        const int64_t i0 = wp.seg_item[sg], ni = wp.seg_item[sg + 1] - i0;
         if (ni <= 0) continue;
-        const int64_t kk0 = wp.class_k[k], kk1 = wp.class_k[k + 1];
+        const int64_t kk0 = wp.seg_k[sg], kk1 = wp.seg_k[sg + 1];
         // the class's first row: every column below it belongs to an earlier class
-        const int lo = p.mc ? (int)g->colr.class_row[k] : 0;
+        const int lo = p.mc ? (int)g->colr.class_row[(size_t)wp.seg_class[sg]] : 0;
         const unsigned pgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(kk1 - kk0, 256 * 4), 152 * 8));
         FJ_CHECK(run.before(st));
         if (c.w)
@@ -1866,6 +1886,26 @@ k_certify_batch(const Item *__restrict__ items, int64_t nitems, const int64_t *_
         da[q] = T(0);
         db[q] = T(0);
     };
+    // row x, vector lane + 32 hh, from the compensated sum of a_xc zhat_c
+    auto finish_exact = [&](int64_t x, int hh, DD acc) {
+        const int j = lane + 32 * hh;
+        const int64_t q = x * k + j;
+        const double zx = zhat[q], spx = sp[q];
+        dd_add(acc, spx);
+        dd_fma(acc, -(1.0 + deg[x]), zx);
+        const double rx = dd_value(acc);
+        const double thr = fmax(epsp * spx, resid_floor(deg[x], zx));
+        const double ce = gsd[(int64_t)j * kGs + 1];
+        const double ax = fabs(rx) <= 1e300 ? fabs(rx) : INFINITY;
+        m_abs[hh] = fmax(m_abs[hh], ax);
+        m_rel[hh] = fmax(m_rel[hh], ax / spx);
+        m_z[hh] = fmax(m_z[hh], fabs(zx - ce));
+        if (ax > thr) viol[hh] += 1.0;
+        r[q] = resid_store<T>(rx);
+        r64[q] = rx;
+        da[q] = T(0);
+        db[q] = T(0);
+    };
     auto src = [&](int32_t c) -> const double * { return zhat + (int64_t)c * k; };
     auto add = [](PlainAcc &acc, float a, double v) {
         acc.s = fma((double)a, v, acc.s);
@@ -1887,22 +1927,25 @@ k_certify_batch(const Item *__restrict__ items, int64_t nitems, const int64_t *_
             warp_tile_k<PlainAcc, double, W, 8>(r0, r1, it.k0, it.k1, false, rp, col, w, no_begin, src, add,
                                                 short_row, lane, has1, has2, n_rows);
         } else {
+            // chunks of long rows: compensated sums from the start (a hub's
+            // plain-sum bound always straddles its threshold)
             const int slot = it.slot;
             const int first = slot_first[slot], nch = slot_nchunk[slot];
             const int ci = (int)((it.k0 - rp[r0]) / kWarpChunk);
             double *pc = partk + 2 * ((int64_t)(first + ci) * k + lane);
-            auto store_part = [&](int64_t, PlainAcc s1, PlainAcc s2) {
+            auto add_dd = [](DD &acc, float a, double v) { dd_fma(acc, (double)a, v); };
+            auto store_part = [&](int64_t, DD s1, DD s2) {
                 if (has1) {
-                    pc[0] = s1.s;
-                    pc[1] = (double)s1.m;
+                    pc[0] = s1.hi;
+                    pc[1] = s1.lo;
                 }
                 if (has2) {
-                    pc[64] = s2.s;
-                    pc[65] = (double)s2.m;
+                    pc[64] = s2.hi;
+                    pc[65] = s2.lo;
                 }
             };
-            warp_tile_k<PlainAcc, double, W, 8>(r0, r1, it.k0, it.k1, true, rp, col, w, no_begin, src, add,
-                                                store_part, lane, has1, has2, n_rows);
+            warp_tile_k<DD, double, W, 8>(r0, r1, it.k0, it.k1, true, rp, col, w, no_begin, src, add_dd,
+                                          store_part, lane, has1, has2, n_rows);
             __threadfence();
             __syncwarp();
             int last = 0;
@@ -1910,25 +1953,15 @@ k_certify_batch(const Item *__restrict__ items, int64_t nitems, const int64_t *_
             last = __shfl_sync(0xffffffffu, last, 0);
             if (last) {
                 __threadfence();
-                PlainAcc a1{0.0, 0.f}, a2{0.0, 0.f};
-                double m1 = 0.0, m2 = 0.0;
+                DD a1{0.0, 0.0}, a2{0.0, 0.0};
                 for (int c = 0; c < nch; ++c) {
                     const double *q = partk + 2 * ((int64_t)(first + c) * k + lane);
-                    if (has1) {
-                        a1.s += __ldcg(q);
-                        m1 += __ldcg(q + 1);
-                    }
-                    if (has2) {
-                        a2.s += __ldcg(q + 64);
-                        m2 += __ldcg(q + 65);
-                    }
+                    if (has1) a1 = dd_merge(a1, DD{__ldcg(q), __ldcg(q + 1)});
+                    if (has2) a2 = dd_merge(a2, DD{__ldcg(q + 64), __ldcg(q + 65)});
                 }
-                a1.m = (float)(m1 * (1.0 + (double)nch * 0x1p-23));
-                a2.m = (float)(m2 * (1.0 + (double)nch * 0x1p-23));
                 if (lane == 0) cnt[slot] = 0;
-                const int64_t len = (rp[r0 + 1] - rp[r0]) + nch + 64;
-                if (has1) finish(r0, 0, a1, len);
-                if (has2) finish(r0, 1, a2, len);
+                if (has1) finish_exact(r0, 0, a1);
+                if (has2) finish_exact(r0, 1, a2);
             }
         }
     }

@@ -332,3 +332,30 @@ def test_auto_schedule_recovers_from_divergence(capi):
         assert info[0]["omega_used"] == 1.5
     z_star, _ = oracle.truth(n, rp, col, w, s)
     assert rel_inf(z_d.cpu().numpy(), z_star) <= FP32_TOL
+
+
+def test_ragged_from_arcs_matches_separate_handles(capi):
+    """The ragged handle the batch bench builds (each graph through the library's
+    own ingest, laid out block-diagonally) gives per graph the same certified z
+    and metrics as that graph's own handle."""
+    r = W.ragged_ba(count=9, lo=200, hi=5000)
+    parts, svecs = [], []
+    for gr in r["graphs"]:
+        a, b, _ = W.symmetrize_arcs(gr["src"], gr["dst"])
+        parts.append((gr["n"], a, b, None))
+        svecs.append(gr["s"])
+    R = capi.Graph.ragged_from_arcs(parts, directed=False)
+    s = np.concatenate(svecs)
+    z, infos, st = R.solve(s, eps=1e-6, omega=1.5, precision=capi.FJ_PREC_FP64)
+    mets = R.metrics(s, z)
+    assert st == capi.FJ_OK and len(infos) == 9
+    off = 0
+    for i, (n, a, b, _) in enumerate(parts):
+        rp, col, _ = oracle.csr_from_arcs(n, a, b)
+        zs, _ = oracle.truth(n, rp, col, None, svecs[i])
+        assert infos[i]["converged"] == 1
+        assert rel_inf(z[off:off + n], zs) <= FP64_TOL
+        mo = oracle.metrics(n, rp, col, None, svecs[i], zs, directed=False)
+        for k in ("P", "D", "I", "C"):
+            assert abs(mets[i][k] - mo[k]) <= METRIC_TOL * abs(mo[k])
+        off += n
