@@ -15,8 +15,12 @@ listen to v:
     layer l    h^l_v = relu(W^l_s^T h^{l-1}_v + W^l_n^T g^{l-1}_v + b^l),
                g^{l-1}_v = sum_j a_vj h^{l-1}_j / d_v (0 when d_v = 0),
                h^0 = x, l = 1, 2, 3, width 64
-    output     z0_v = w_o . h^3_v + b_o
+    output     z0_v = b_v + w_o . h^3_v + b_o,
+               b_v = (s_v + d_v m_v) / (1 + d_v)   (one Jacobi step from s)
     loss       L = (1/n) sum_v (z0_v - z_v)^2
+
+The base term b_v is the equilibrium equation of node v (Section 3.2) with its
+neighbours' values taken as their opinions; the network learns the correction.
 
 Parameters are one flat FP32 vector, in this order: for l = 1, 2, 3 the
 matrices W^l_s [F_in][64] and W^l_n [F_in][64] (row-major) and b^l [64], then
@@ -108,6 +112,14 @@ def features(n, row_ptr, col, w, s):
     return np.stack([s, np.log1p(d), np.log1p(din), m], axis=1)
 
 
+def base_term(n, row_ptr, col, w, s):
+    """b_v = (s_v + d_v m_v) / (1 + d_v): one Jacobi step of (I + L) z = s from z = s."""
+    fwd, _, d = _mean_op(n, row_ptr, col, w)
+    s = np.asarray(s, np.float64)
+    m = fwd(s[:, None])[:, 0]
+    return (s + d * m) / (1.0 + d)
+
+
 def forward(theta, n, row_ptr, col, w, s, bf16=False):
     """z0 and the saved activations (a dict) of the network."""
     layers, wo, bo = unpack(theta)
@@ -122,7 +134,7 @@ def forward(theta, n, row_ptr, col, w, s, bf16=False):
         saved["G"].append(g)
         saved["pre"].append(pre)
         saved["H"].append(h)
-    z0 = h @ wo + bo
+    z0 = base_term(n, row_ptr, col, w, s) + h @ wo + bo
     saved["adj"] = adj
     return z0, saved
 

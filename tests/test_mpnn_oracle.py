@@ -38,6 +38,22 @@ def test_features_by_hand():
     np.testing.assert_allclose(x[:, 3], [0.9, 1.0, 0.0])
 
 
+def _base_by_hand(s):
+    # d = (4, 2, 0), m = (0.9, 1.0, 0): b = (s + d m) / (1 + d)
+    return np.array([(s[0] + 4 * 0.9) / 5, (s[1] + 2 * 1.0) / 3, s[2]])
+
+
+def test_base_term_is_one_jacobi_step():
+    n, rp, col, w = small_digraph()
+    s = np.array([0.2, 0.6, 1.0])
+    np.testing.assert_allclose(mpnn.base_term(n, rp, col, w, s), _base_by_hand(s), rtol=0, atol=1e-15)
+    # the Jacobi update of (I + L) z = s from z = s: b = (I + D)^{-1} (s + A s)
+    dense = oracle.dense_i_plus_l(n, rp, col, w)
+    dgl = np.diag(dense)
+    a = np.diag(dgl) - dense
+    np.testing.assert_allclose(mpnn.base_term(n, rp, col, w, s), (s + a @ s) / dgl, rtol=0, atol=1e-15)
+
+
 @pytest.mark.parametrize("route", ["copy_s", "copy_m", "aggregate_in_layer2", "bias_only"])
 def test_forward_by_hand(route):
     n, rp, col, w = small_digraph()
@@ -64,7 +80,7 @@ def test_forward_by_hand(route):
         want = np.full(3, 0.7)
     theta = mpnn.pack(layers, wo, bo)
     z0, _ = mpnn.forward(theta, n, rp, col, w, s)
-    np.testing.assert_allclose(z0, want, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(z0, _base_by_hand(s) + want, rtol=0, atol=1e-15)
 
 
 def test_relu_cuts_negative_path():
@@ -75,7 +91,7 @@ def test_relu_cuts_negative_path():
     layers[1][0][0, 0] = layers[2][0][0, 0] = 1.0
     wo[0] = 1.0
     z0, _ = mpnn.forward(mpnn.pack(layers, wo, bo), n, rp, col, w, s)
-    assert np.all(z0 == 0.0)
+    np.testing.assert_allclose(z0, _base_by_hand(s), rtol=0, atol=1e-15)
 
 
 def test_aggregation_adjoint_identity():
