@@ -343,7 +343,9 @@ fj_status fj_residual(fj_graph *g, const double *s, const double *z, double c_ef
  *   x_v  = [s_v, log(1 + d_v), log(1 + din_v), sum_j a_vj s_j / d_v]
  *   h^l_v = relu(Ws^l^T h^{l-1}_v + Wn^l^T g^{l-1}_v + b^l),
  *   g^{l-1}_v = sum_j a_vj h^{l-1}_j / d_v (0 when d_v = 0), h^0 = x,
- *   l = 1, 2, 3, width 64;  z0_v = w_o . h^3_v + b_o.
+ *   l = 1, 2, 3, width 64;  z0_v = b_v + w_o . h^3_v + b_o with
+ *   b_v = (s_v + d_v m_v) / (1 + d_v), m_v the weighted mean of s over the
+ *   nodes v listens to (one Jacobi step of (I + L) z = s from z = s).
  * The dense products run on the tensor cores in BF16 with FP32 accumulation.
  *
  * Parameters are one FP32 vector of fj_mpnn_param_count() entries, in this

@@ -691,8 +691,9 @@ void fj_graph_destroy(fj_graph *g)
     }
     Workspace &ws = g->ws;
     dev_free(ws.r); dev_free(ws.h); dev_free(ws.da); dev_free(ws.db); dev_free(ws.om); dev_free(ws.prod);
+    dev_free(ws.z32);
     dev_free(ws.zhat); dev_free(ws.sp); dev_free(ws.sin); dev_free(ws.zout); dev_free(ws.r64);
-    dev_free(ws.gstat); dev_free(ws.ctr); dev_free(ws.status); dev_free(ws.tile_ctr);
+    dev_free(ws.gstat); dev_free(ws.ctr); dev_free(ws.status); dev_free(ws.tile_ctr); dev_free(ws.zmax);
     dev_free(ws.list); dev_free(ws.count); dev_free(ws.partial);
     for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 2; ++b)
@@ -701,6 +702,7 @@ void fj_graph_destroy(fj_graph *g)
     if (ws.ctr_host) cudaFreeHost(ws.ctr_host);
     BatchWorkspace &b = g->bws;
     dev_free(b.r); dev_free(b.h); dev_free(b.da); dev_free(b.db); dev_free(b.zhat); dev_free(b.sp);
+    dev_free(b.z32);
     dev_free(b.sin); dev_free(b.zout); dev_free(b.om); dev_free(b.gstat); dev_free(b.partk);
     dev_free(b.r64); dev_free(b.list); dev_free(b.tick);
     if (b.gstat_host) cudaFreeHost(b.gstat_host);
@@ -795,143 +797,11 @@ __device__ __forceinline__ bool higher(unsigned long long ku, int64_t u, unsigne
     return ku > kv || (ku == kv && u < v);
 }
 
-// One Jones-Plassmann round over the uncoloured worklist, a warp per node.  A
-// node whose higher-priority neighbours are all coloured takes the smallest
-// colour none of its coloured neighbours holds (only higher-priority ones can
-// be coloured at that point), which reproduces sequential greedy colouring in
-// priority order whatever the timing of other warps.
-__global__ void k_jp_round(const long long *__restrict__ cntp, const int32_t *__restrict__ list,
-                           const int64_t *__restrict__ rp,
-                           const int32_t *__restrict__ col, const int64_t *__restrict__ tp,
-                           const int32_t *__restrict__ tc, const unsigned long long *__restrict__ key,
-                           int32_t *colour)
-{
-    __shared__ unsigned bits[8][32];
-    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    volatile int32_t *vc = colour;
-    const int64_t cnt = *cntp;
-    for (int64_t i = warp0; i < cnt; i += nwarps) {
-        const int32_t v = list[i];
-        const unsigned long long kv = key[v];
-        const int64_t a = rp[v], b = rp[v + 1];
-        const int64_t ta = tp ? tp[v] : 0, tb = tp ? tp[v + 1] : 0;
-        bool blocked = false;
-        for (int64_t k = a + lane; k < b && !blocked; k += 32) {
-            int32_t u = col[k];
-            if (higher(key[u], u, kv, v) && vc[u] < 0) blocked = true;
-        }
-        for (int64_t k = ta + lane; k < tb && !blocked; k += 32) {
-            int32_t u = tc[k];
-            if (higher(key[u], u, kv, v) && vc[u] < 0) blocked = true;
-        }
-        if (__any_sync(0xffffffffu, blocked)) continue;
-        int found = -1;
-        for (int base = 0; found < 0; base += 1024) {
-            bits[wl][lane] = 0u;
-            __syncwarp();
-            for (int64_t k = a + lane; k < b; k += 32) {
-                int c = vc[col[k]] - base;
-                if (c >= 0 && c < 1024) atomicOr(&bits[wl][c >> 5], 1u << (c & 31));
-            }
-            for (int64_t k = ta + lane; k < tb; k += 32) {
-                int c = vc[tc[k]] - base;
-                if (c >= 0 && c < 1024) atomicOr(&bits[wl][c >> 5], 1u << (c & 31));
-            }
-            __syncwarp();
-            unsigned freebits = ~bits[wl][lane];
-            unsigned has = __ballot_sync(0xffffffffu, freebits != 0u);
-            if (has) {
-                int l = __ffs(has) - 1;
-                unsigned fb = __shfl_sync(0xffffffffu, freebits, l);
-                found = base + 32 * l + (__ffs(fb) - 1);
-            }
-            __syncwarp();
-        }
-        if (lane == 0) {
-            colour[v] = found;
-            __threadfence();
-        }
-    }
-}
-
 // Arc weight in 32.32 fixed point: conflict sums are integers, so their value
 // does not depend on the order of the additions.
 __device__ __forceinline__ unsigned long long fixed_q(const float *w, int64_t k)
 {
     return w ? (unsigned long long)llrint((double)w[k] * 4294967296.0) : (1ULL << 32);
-}
-
-// Jones-Plassmann round with a palette of K <= 32 colours.  A ready node sums
-// the fixed-point weights of its coloured neighbours per colour (integer
-// atomics in shared memory) and takes the smallest colour with zero weight,
-// else the colour of least weight (smallest on ties): the same choice as the
-// sequential greedy pass in priority order.
-__global__ void k_jp_palette_round(const long long *__restrict__ cntp, const int32_t *__restrict__ list,
-                                   const int64_t *__restrict__ rp,
-                                   const int32_t *__restrict__ col, const float *__restrict__ w,
-                                   const int64_t *__restrict__ tp, const int32_t *__restrict__ tc,
-                                   const float *__restrict__ tw, const unsigned long long *__restrict__ key, int K,
-                                   int32_t *colour)
-{
-    __shared__ unsigned long long conf[8][32];
-    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    volatile int32_t *vc = colour;
-    const int64_t cnt = *cntp;
-    for (int64_t i = warp0; i < cnt; i += nwarps) {
-        const int32_t v = list[i];
-        const unsigned long long kv = key[v];
-        const int64_t a = rp[v], b = rp[v + 1];
-        const int64_t ta = tp ? tp[v] : 0, tb = tp ? tp[v + 1] : 0;
-        bool blocked = false;
-        for (int64_t k = a + lane; k < b && !blocked; k += 32) {
-            int32_t u = col[k];
-            if (higher(key[u], u, kv, v) && vc[u] < 0) blocked = true;
-        }
-        for (int64_t k = ta + lane; k < tb && !blocked; k += 32) {
-            int32_t u = tc[k];
-            if (higher(key[u], u, kv, v) && vc[u] < 0) blocked = true;
-        }
-        if (__any_sync(0xffffffffu, blocked)) continue;
-        conf[wl][lane] = 0ULL;
-        __syncwarp();
-        for (int64_t k = a + lane; k < b; k += 32) {
-            int c = vc[col[k]];
-            if (c >= 0 && c < 32) atomicAdd(&conf[wl][c], fixed_q(w, k));
-        }
-        for (int64_t k = ta + lane; k < tb; k += 32) {
-            int c = vc[tc[k]];
-            if (c >= 0 && c < 32) atomicAdd(&conf[wl][c], fixed_q(tw, k));
-        }
-        __syncwarp();
-        const unsigned long long mine = lane < K ? conf[wl][lane] : ~0ULL;
-        const unsigned zero = __ballot_sync(0xffffffffu, lane < K && mine == 0ULL);
-        int best;
-        if (zero) {
-            best = __ffs(zero) - 1;
-        } else {
-            unsigned long long m = mine;
-            int bl = lane;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                unsigned long long m2 = __shfl_xor_sync(0xffffffffu, m, o);
-                int b2 = __shfl_xor_sync(0xffffffffu, bl, o);
-                if (m2 < m || (m2 == m && b2 < bl)) {
-                    m = m2;
-                    bl = b2;
-                }
-            }
-            best = bl;
-        }
-        if (lane == 0) {
-            colour[v] = best;
-            __threadfence();
-        }
-        __syncwarp();
-    }
 }
 
 // Warp per node: weight to neighbours of the same colour (out-arcs, plus
@@ -1051,35 +921,148 @@ __global__ void k_colour_keys(int64_t n, const int32_t *__restrict__ colour, con
     }
 }
 
-// Worklist of the next round: the nodes of this round's list still uncoloured
-// (order is irrelevant: a round's result does not depend on it), appended with
-// one atomic per warp.
-__global__ void k_requeue(const long long *__restrict__ cnt_in, const int32_t *__restrict__ in,
-                          const int32_t *__restrict__ colour, long long *cnt_out, int32_t *__restrict__ out)
+// Data-driven greedy colouring (the same colours as the sequential greedy in
+// priority order): dep[v] counts v's neighbours of higher priority that are
+// not yet coloured; a node is ready when it reaches zero, takes its colour from
+// its neighbours coloured so far (exactly its higher-priority ones: a
+// lower-priority neighbour waits for it), then releases its lower-priority
+// neighbours.  Each arc is visited a bounded number of times in total.
+__device__ __forceinline__ void append_warp(bool keep, int32_t v, int32_t *out, long long *cnt)
 {
-    const int64_t cnt = *cnt_in;
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    long long at = 0;
+    if ((threadIdx.x & 31) == 0 && m)
+        at = (long long)atomicAdd(reinterpret_cast<unsigned long long *>(cnt), (unsigned long long)__popc(m));
+    at = __shfl_sync(0xffffffffu, at, 0);
+    if (keep) out[at + __popc(m & lanemask_lt())] = v;
+}
+
+__global__ void k_dep_count(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                            const int64_t *__restrict__ tp, const int32_t *__restrict__ tc,
+                            const unsigned long long *__restrict__ key, int32_t *__restrict__ dep,
+                            int32_t *__restrict__ ready, long long *ready_cnt)
+{
     const int lane = threadIdx.x & 31;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < cnt; base += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = base + threadIdx.x;
-        int32_t v = -1;
-        if (i < cnt) v = in[i];
-        const bool keep = v >= 0 && colour[v] < 0;
-        const unsigned m = __ballot_sync(0xffffffffu, keep);
-        long long at = 0;
-        if (lane == 0 && m)
-            at = (long long)atomicAdd(reinterpret_cast<unsigned long long *>(cnt_out), (unsigned long long)__popc(m));
-        at = __shfl_sync(0xffffffffu, at, 0);
-        if (keep) out[at + __popc(m & lanemask_lt())] = v;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    // warps walk nodes in groups of 32 so that the ready append is warp-uniform
+    for (int64_t g0 = warp0 * 32; g0 < n; g0 += nwarps * 32) {
+        int my = 0;
+        for (int q = 0; q < 32 && g0 + q < n; ++q) {
+            const int64_t v = g0 + q;
+            const unsigned long long kv = key[v];
+            int c = 0;
+            for (int64_t k = rp[v] + lane; k < rp[v + 1]; k += 32) c += higher(key[col[k]], col[k], kv, v);
+            if (tp)
+                for (int64_t k = tp[v] + lane; k < tp[v + 1]; k += 32) c += higher(key[tc[k]], tc[k], kv, v);
+            c = (int)warp_sum((unsigned long long)c);
+            if (lane == q) my = c;
+        }
+        const int64_t v = g0 + lane;
+        if (v < n) dep[v] = my;
+        append_warp(v < n && my == 0, (int32_t)v, ready, ready_cnt);
     }
 }
 
-__global__ void k_iota_list(int64_t n, int32_t *__restrict__ out, long long *cnt)
+template <bool PAL>
+__global__ void __launch_bounds__(256)
+k_jp_ready(const long long *__restrict__ cntp, const int32_t *__restrict__ list, const int64_t *__restrict__ rp,
+           const int32_t *__restrict__ col, const float *__restrict__ w, const int64_t *__restrict__ tp,
+           const int32_t *__restrict__ tc, const float *__restrict__ tw, const unsigned long long *__restrict__ key,
+           int K, int32_t *colour, int32_t *dep, int32_t *__restrict__ next, long long *next_cnt)
 {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = (int32_t)i;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        cnt[0] = n;
-        cnt[1] = 0;
+    __shared__ unsigned long long conf[8][32];
+    __shared__ unsigned bits[8][32];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    volatile int32_t *vc = colour;
+    const int64_t cnt = *cntp;
+    for (int64_t i = warp0; i < cnt; i += nwarps) {
+        const int32_t v = list[i];
+        const unsigned long long kv = key[v];
+        const int64_t a = rp[v], b = rp[v + 1];
+        const int64_t ta = tp ? tp[v] : 0, tb = tp ? tp[v + 1] : 0;
+        int best = 0;
+        if (PAL) {
+            conf[wl][lane] = 0ULL;
+            __syncwarp();
+            for (int64_t k = a + lane; k < b; k += 32) {
+                const int c = vc[col[k]];
+                if (c >= 0 && c < 32) atomicAdd(&conf[wl][c], fixed_q(w, k));
+            }
+            for (int64_t k = ta + lane; k < tb; k += 32) {
+                const int c = vc[tc[k]];
+                if (c >= 0 && c < 32) atomicAdd(&conf[wl][c], fixed_q(tw, k));
+            }
+            __syncwarp();
+            const unsigned long long mine = lane < K ? conf[wl][lane] : ~0ULL;
+            const unsigned zero = __ballot_sync(0xffffffffu, lane < K && mine == 0ULL);
+            if (zero) {
+                best = __ffs(zero) - 1;
+            } else {
+                unsigned long long m = mine;
+                int bl = lane;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const unsigned long long m2 = __shfl_xor_sync(0xffffffffu, m, o);
+                    const int b2 = __shfl_xor_sync(0xffffffffu, bl, o);
+                    if (m2 < m || (m2 == m && b2 < bl)) {
+                        m = m2;
+                        bl = b2;
+                    }
+                }
+                best = bl;
+            }
+        } else {
+            int found = -1;
+            for (int base = 0; found < 0; base += 1024) {
+                bits[wl][lane] = 0u;
+                __syncwarp();
+                for (int64_t k = a + lane; k < b; k += 32) {
+                    const int c = vc[col[k]] - base;
+                    if (c >= 0 && c < 1024) atomicOr(&bits[wl][c >> 5], 1u << (c & 31));
+                }
+                for (int64_t k = ta + lane; k < tb; k += 32) {
+                    const int c = vc[tc[k]] - base;
+                    if (c >= 0 && c < 1024) atomicOr(&bits[wl][c >> 5], 1u << (c & 31));
+                }
+                __syncwarp();
+                const unsigned freebits = ~bits[wl][lane];
+                const unsigned has = __ballot_sync(0xffffffffu, freebits != 0u);
+                if (has) {
+                    const int l = __ffs(has) - 1;
+                    const unsigned fb = __shfl_sync(0xffffffffu, freebits, l);
+                    found = base + 32 * l + (__ffs(fb) - 1);
+                }
+                __syncwarp();
+            }
+            best = found;
+        }
+        if (lane == 0) colour[v] = best;
+        __threadfence();
+        __syncwarp();
+        // release the lower-priority neighbours
+        for (int64_t k0 = a; k0 < b; k0 += 32) {
+            const int64_t k = k0 + lane;
+            bool go = false;
+            int32_t u = 0;
+            if (k < b) {
+                u = col[k];
+                go = higher(kv, v, key[u], u) && atomicSub(&dep[u], 1) == 1;
+            }
+            append_warp(go, u, next, next_cnt);
+        }
+        for (int64_t k0 = ta; k0 < tb; k0 += 32) {
+            const int64_t k = k0 + lane;
+            bool go = false;
+            int32_t u = 0;
+            if (k < tb) {
+                u = tc[k];
+                go = higher(kv, v, key[u], u) && atomicSub(&dep[u], 1) == 1;
+            }
+            append_warp(go, u, next, next_cnt);
+        }
     }
 }
 
@@ -1098,31 +1081,35 @@ static fj_status colour_graph(fj_graph *g, int palette, cudaStream_t st)
     k_sym_degree<<<grid_for(n * 32, 256), 256, 0, st>>>(n, c.row_ptr, c.col, tp, tc, key);
     k_fill_i32<<<grid_for(n, 256), 256, 0, st>>>(n, cl.colour, -1);
     FJ_CUDA(cudaGetLastError());
-    // Jones-Plassmann rounds over a shrinking worklist (ping-pong buffers, count
-    // on the device); the host reads the count every kBatch rounds
+    // data-driven rounds over the ready nodes (ping-pong lists, count on the
+    // device); the host reads the count every kBatch rounds
     constexpr int kBatch = 16;
     int32_t *lists[2] = {list, nullptr};
     long long *cnts = nullptr;
+    int32_t *dep = nullptr;
     FJ_CUDA(dalloc(&lists[1], n));
     FJ_CUDA(dalloc(&cnts, 2));
-    k_iota_list<<<grid_for(n, 256), 256, 0, st>>>(n, lists[0], cnts);
+    FJ_CUDA(dalloc(&dep, n));
+    FJ_CUDA(cudaMemsetAsync(cnts, 0, 2 * sizeof(long long), st));
+    k_dep_count<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(n, c.row_ptr, c.col, tp, tc, key, dep, lists[0], cnts);
     FJ_CUDA(cudaGetLastError());
-    long long left = n;
+    long long left = 1;
     int64_t rounds = 0;
     int cur = 0;
     fj_status result = FJ_OK;
+    const unsigned grid = 152 * 8;
     while (left > 0) {
-        const unsigned grid = grid_for(left * 32, 256, 152 * 64);
-        const unsigned qgrid = grid_for(left, 256, 152 * 16);
-        for (int b = 0; b < kBatch; ++b) {
+        for (int bt = 0; bt < kBatch; ++bt) {
             const long long *cin = cnts + cur;
-            if (palette > 0)
-                k_jp_palette_round<<<grid, 256, 0, st>>>(cin, lists[cur], c.row_ptr, c.col, c.w, tp, tc,
-                                                         g->directed ? g->tw : nullptr, key, palette, cl.colour);
-            else
-                k_jp_round<<<grid, 256, 0, st>>>(cin, lists[cur], c.row_ptr, c.col, tp, tc, key, cl.colour);
             FJ_CUDA(cudaMemsetAsync(cnts + (cur ^ 1), 0, sizeof(long long), st));
-            k_requeue<<<qgrid, 256, 0, st>>>(cin, lists[cur], cl.colour, cnts + (cur ^ 1), lists[cur ^ 1]);
+            if (palette > 0)
+                k_jp_ready<true><<<grid, 256, 0, st>>>(cin, lists[cur], c.row_ptr, c.col, c.w, tp, tc,
+                                                       g->directed ? g->tw : nullptr, key, palette, cl.colour, dep,
+                                                       lists[cur ^ 1], cnts + (cur ^ 1));
+            else
+                k_jp_ready<false><<<grid, 256, 0, st>>>(cin, lists[cur], c.row_ptr, c.col, c.w, tp, tc,
+                                                        g->directed ? g->tw : nullptr, key, 0, cl.colour, dep,
+                                                        lists[cur ^ 1], cnts + (cur ^ 1));
             FJ_CUDA(cudaGetLastError());
             cur ^= 1;
         }
@@ -1135,6 +1122,7 @@ static fj_status colour_graph(fj_graph *g, int palette, cudaStream_t st)
             break;
         }
     }
+    dev_free(dep);
     dev_free(lists[1]);
     dev_free(cnts);
     if (result != FJ_OK) {

@@ -105,6 +105,7 @@ struct Workspace {
     void *da = nullptr;     // push increments (current)
     void *db = nullptr;     // push increments (second buffer)
     void *om = nullptr;     // per-node relaxation factor
+    void *z32 = nullptr;    // FP32 paths: increments of the current pass, folded into zhat
     void *prod = nullptr;   // per-nonzero products a_k delta_col(k) of the running class
     int64_t cap_prod = 0;
     double *zhat = nullptr; // estimate of z' (FP64)
@@ -115,6 +116,7 @@ struct Workspace {
     double *gstat = nullptr;  // per graph/RHS: [c_eff, min s, resid_inf, resid_rel, z_inf, violators]
     Counters *ctr = nullptr;
     Counters *ctr_host = nullptr;  // pinned mirror
+    unsigned long long *zmax = nullptr;  // max |zhat| before a certificate (ordered bits)
     double *gstat_host = nullptr;  // pinned mirror
     unsigned long long *status = nullptr;  // look-back tile status
     int64_t cap_status = 0;
@@ -138,6 +140,7 @@ struct BatchWorkspace {
     int64_t cap = 0;   // n * k entries held
     int cap_k = 0;
     void *r = nullptr, *h = nullptr, *da = nullptr, *db = nullptr;
+    void *z32 = nullptr;       // FP32 path: increments of the current pass, folded into zhat
     double *zhat = nullptr, *sp = nullptr, *sin = nullptr, *zout = nullptr;
     double *r64 = nullptr;     // FP64 residual written by the certificate
     int32_t *list = nullptr;   // frontier of (node, vector) entries, n * k capacity

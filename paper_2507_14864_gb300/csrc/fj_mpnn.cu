@@ -5,7 +5,8 @@
 //   x_v = [s_v, log(1 + d_v), log(1 + din_v), m_v],  m_v = sum_j a_vj s_j / d_v
 //   h^l_v = relu(Ws^l^T h^{l-1}_v + Wn^l^T g^{l-1}_v + b^l),
 //   g^{l-1}_v = sum_j a_vj h^{l-1}_j / d_v,  h^0 = x,  width 64,  l = 1, 2, 3
-//   z0_v = w_o . h^3_v + b_o;   loss = mean_v (z0_v - z_v)^2
+//   z0_v = b_v + w_o . h^3_v + b_o,  b_v = (s_v + d_v m_v) / (1 + d_v) (one
+//   Jacobi step from s);   loss = mean_v (z0_v - z_v)^2
 //
 // Every dense product runs on the tensor cores (tcgen05.mma kind::f16, BF16
 // operands, FP32 accumulation in tensor memory), one CTA per 128-row tile:
@@ -34,9 +35,13 @@ constexpr int kHid = 64;
 constexpr int kFin0 = 4;
 constexpr int kTile = 128;  // rows per CTA tile (M of the MMA)
 constexpr uint32_t kWaitLimit = 1u << 22;
-// dynamic shared memory requested by every GEMM kernel: caps residency at
-// three CTAs per SM, so their tensor-memory columns (<= 128 each) always fit
-constexpr int kGemmSmem = 72 * 1024;
+// Dynamic shared memory of each GEMM kernel: its tiles, or more, so that the
+// CTAs resident on one SM never hold more than the 512 tensor-memory columns
+// (64 columns: at most 7 CTAs per SM; 128 columns: at most 4).
+constexpr int kSmemFwd4 = 30 * 1024;   // tiles 6 KB, 64 columns
+constexpr int kSmemFwd64 = 49 * 1024;  // tiles 48 KB, 64 columns
+constexpr int kSmemDx = 57 * 1024;     // tiles 32 KB, 128 columns
+constexpr int kSmemDw = 49 * 1024;     // tiles 48 KB, 64 columns
 
 // Offsets of one layer's parameters in the flat FP32 vector.
 struct LayerOff {
@@ -167,11 +172,13 @@ k_agg_s(const Item *__restrict__ items, int64_t nitems, const int64_t *__restric
     }
 }
 
-// x_v in BF16 (4 per node) from s, the degrees and m.
+// x_v in BF16 (4 per node) from s, the degrees and m; the base term b_v (FP32).
 __global__ void k_features(int64_t n, const double *__restrict__ deg, const int32_t *__restrict__ indeg,
-                           const double *__restrict__ s, const double *__restrict__ m, __nv_bfloat16 *__restrict__ x)
+                           const double *__restrict__ s, const double *__restrict__ m, __nv_bfloat16 *__restrict__ x,
+                           float *__restrict__ base)
 {
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        base[v] = (float)((s[v] + deg[v] * m[v]) / (1.0 + deg[v]));
         x[4 * v + 0] = __float2bfloat16_rn((float)s[v]);
         x[4 * v + 1] = __float2bfloat16_rn((float)log1p(deg[v]));
         x[4 * v + 2] = __float2bfloat16_rn((float)log1p((double)indeg[v]));
@@ -269,10 +276,12 @@ k_agg4(const Item *__restrict__ items, int64_t nitems, const int64_t *__restrict
     }
 }
 
-// g_v = sum_j a_vj h_j / d_v for 64-wide BF16 rows: one warp per tile, lane l
-// owns features 2l and 2l + 1; the tile's columns and weights are read 32 at a
-// time and broadcast, eight row gathers are in flight; rows complete as the
-// walk passes their ends.  A chunk of a long row leaves 64 FP32 partials.
+// g_v = sum_j a_vj h_j / d_v for 64-wide BF16 rows: one warp per tile, rows in
+// turn.  The warp is four slots of eight lanes; lane (slot, sub) loads the
+// 16-byte part `sub` (features 8 sub .. 8 sub + 7) of neighbour row slot,
+// slot + 4, ..., so one load instruction gathers four rows and four
+// instructions (sixteen rows) are in flight.  The slots' FP32 sums are added
+// by shuffles at the row's end.  A chunk of a long row leaves 64 FP32 partials.
 __global__ void __launch_bounds__(256)
 k_agg64(const Item *__restrict__ items, int64_t nitems, const int64_t *__restrict__ rp,
         const int32_t *__restrict__ col, const float *__restrict__ w, const double *__restrict__ deg,
@@ -280,104 +289,105 @@ k_agg64(const Item *__restrict__ items, int64_t nitems, const int64_t *__restric
         const int32_t *__restrict__ slot_first, const int32_t *__restrict__ slot_nchunk, int64_t n, int *err)
 {
     constexpr unsigned FULL = 0xffffffffu;
-    constexpr int D = 8;
-    const int lane = threadIdx.x & 31;
+    constexpr int U = 4;  // load instructions in flight per lane
+    const int lane = threadIdx.x & 31, slot = lane >> 3, sub = lane & 7;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const __nv_bfloat162 *h2 = reinterpret_cast<const __nv_bfloat162 *>(h);
+    const uint4 *h4 = reinterpret_cast<const uint4 *>(h);  // 8 uint4 per row
+    auto add8 = [](float (&acc)[8], uint4 v, float a) {
+        const __nv_bfloat162 *p = reinterpret_cast<const __nv_bfloat162 *>(&v);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float2 f = __bfloat1622float2(p[i]);
+            acc[2 * i] += a * f.x;
+            acc[2 * i + 1] += a * f.y;
+        }
+    };
+    auto store8 = [](uint4 *dst, const float (&acc)[8], float scale) {
+        uint4 o;
+        __nv_bfloat162 *q = reinterpret_cast<__nv_bfloat162 *>(&o);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) q[i] = __floats2bfloat162_rn(acc[2 * i] * scale, acc[2 * i + 1] * scale);
+        *dst = o;
+    };
     for (int64_t ii = warp; ii < nitems; ii += nwarps) {
         const Item it = items[ii];
-        int64_t r0 = it.r0, r1 = it.r1;
-        if (r0 < 0 || r1 > n || r0 >= r1 || (it.slot < 0 && r1 - r0 > kWarpRows)) continue;
+        const int64_t r0 = it.r0;
         const bool chunk = it.slot >= 0;
-        const int64_t k0 = it.k0, k1 = it.k1;
-        int64_t e_lo = k1, e_hi = k1;
-        if (!chunk) {
-            if (r0 + lane < r1) e_lo = rp[r0 + lane + 1];
-            if (r0 + 32 + lane < r1) e_hi = rp[r0 + 33 + lane];
-        } else {
-            r1 = r0 + 1;
-        }
-        auto row_end = [&](int64_t xx) -> int64_t {
-            const int i = (int)(xx - r0);
-            return __shfl_sync(FULL, i < 32 ? e_lo : e_hi, i & 31);
-        };
-        int64_t x = r0;
-        int64_t xe = row_end(x);
-        float a0 = 0.f, a1 = 0.f;
-        auto emit = [&](int64_t v) {
-            if (chunk) {
-                const int slot = it.slot, first = slot_first[slot];
-                const int ci = (int)((k0 - rp[r0]) / kWarpChunk);
-                reinterpret_cast<float2 *>(part + (int64_t)(first + ci) * 64)[lane] = make_float2(a0, a1);
-                return;
-            }
-            const double d = deg[v];
-            const float inv = d > 0.0 ? (float)(1.0 / d) : 0.f;
-            reinterpret_cast<__nv_bfloat162 *>(g + v * 64)[lane] = __floats2bfloat162_rn(a0 * inv, a1 * inv);
-        };
-        auto flush_until = [&](int64_t pos) {
-            while (x < r1 && xe <= pos) {
-                emit(x);
-                a0 = a1 = 0.f;
-                ++x;
-                if (x < r1) xe = row_end(x);
-            }
-        };
-        for (int64_t base = k0; base < k1; base += 32) {
-            const int64_t kk = base + lane;
-            int32_t cl = 0;
-            float al = 0.f;
-            if (kk < k1) {
-                cl = col[kk];
-                al = w ? w[kk] : 1.f;
-                if (cl < 0 || cl >= n) {
-                    dev_error(err, DEV_BAD_COL);
-                    cl = 0;
-                    al = 0.f;
-                }
-            }
-            const int mm = (int)(k1 - base < 32 ? k1 - base : 32);
-            for (int t = 0; t < mm; t += D) {
-                __nv_bfloat162 v[D];
-                float aa[D];
-#pragma unroll
-                for (int u = 0; u < D; ++u) {
-                    const int32_t c = __shfl_sync(FULL, cl, (t + u) & 31);
-                    aa[u] = __shfl_sync(FULL, al, (t + u) & 31);
-                    v[u] = t + u < mm ? h2[(int64_t)c * 32 + lane] : __floats2bfloat162_rn(0.f, 0.f);
-                }
-#pragma unroll
-                for (int u = 0; u < D; ++u) {
-                    if (t + u < mm) {
-                        flush_until(base + t + u);
-                        const float2 f = __bfloat1622float2(v[u]);
-                        a0 += aa[u] * f.x;
-                        a1 += aa[u] * f.y;
+        const int64_t r1 = chunk ? r0 + 1 : it.r1;
+        if (r0 < 0 || r1 > n || r0 >= r1 || (!chunk && r1 - r0 > kWarpRows)) continue;
+        for (int64_t x = r0; x < r1; ++x) {
+            const int64_t a = chunk ? it.k0 : rp[x], e = chunk ? it.k1 : rp[x + 1];
+            float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            for (int64_t base = a; base < e; base += 32) {
+                const int64_t kk = base + lane;
+                int32_t cl = 0;
+                float al = 0.f;
+                if (kk < e) {
+                    cl = col[kk];
+                    al = w ? w[kk] : 1.f;
+                    if (cl < 0 || cl >= n) {
+                        dev_error(err, DEV_BAD_COL);
+                        cl = 0;
+                        al = 0.f;
                     }
                 }
+                const int m = (int)(e - base < 32 ? e - base : 32);
+                for (int t = 0; t < m; t += 4 * U) {
+                    uint4 v[U];
+                    float aa[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int idx = t + 4 * u + slot;
+                        const int32_t c = __shfl_sync(FULL, cl, idx & 31);
+                        aa[u] = __shfl_sync(FULL, al, idx & 31);
+                        v[u] = idx < m ? h4[(int64_t)c * 8 + sub] : make_uint4(0, 0, 0, 0);
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; ++u)
+                        if (t + 4 * u + slot < m) add8(acc, v[u], aa[u]);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                acc[i] += __shfl_xor_sync(FULL, acc[i], 8);
+                acc[i] += __shfl_xor_sync(FULL, acc[i], 16);
+            }
+            if (chunk) {
+                const int slt = it.slot, first = slot_first[slt];
+                const int ci = (int)((it.k0 - rp[r0]) / kWarpChunk);
+                if (slot == 0) {
+                    float4 *pp = reinterpret_cast<float4 *>(part + (int64_t)(first + ci) * 64 + 8 * sub);
+                    pp[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+                    pp[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+                }
+            } else if (slot == 0) {
+                const double d = deg[x];
+                store8(reinterpret_cast<uint4 *>(g + x * 64) + sub, acc, d > 0.0 ? (float)(1.0 / d) : 0.f);
             }
         }
-        flush_until(k1);
         if (chunk) {
             __threadfence();
             __syncwarp();
-            const int slot = it.slot, first = slot_first[slot], nch = slot_nchunk[slot];
+            const int slt = it.slot, first = slot_first[slt], nch = slot_nchunk[slt];
             int last = 0;
-            if (lane == 0) last = atomicAdd(&cnt[slot], 1) == nch - 1;
+            if (lane == 0) last = atomicAdd(&cnt[slt], 1) == nch - 1;
             last = __shfl_sync(FULL, last, 0);
             if (last) {
                 __threadfence();
-                a0 = a1 = 0.f;
-                for (int c = 0; c < nch; ++c) {
-                    const float2 p = __ldcg(reinterpret_cast<const float2 *>(part + (int64_t)(first + c) * 64) + lane);
-                    a0 += p.x;
-                    a1 += p.y;
+                float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                if (slot == 0)
+                    for (int c = 0; c < nch; ++c) {
+                        const float4 *pp = reinterpret_cast<const float4 *>(part + (int64_t)(first + c) * 64 + 8 * sub);
+                        const float4 p0 = __ldcg(pp), p1 = __ldcg(pp + 1);
+                        acc[0] += p0.x; acc[1] += p0.y; acc[2] += p0.z; acc[3] += p0.w;
+                        acc[4] += p1.x; acc[5] += p1.y; acc[6] += p1.z; acc[7] += p1.w;
+                    }
+                if (lane == 0) cnt[slt] = 0;
+                if (slot == 0) {
+                    const double d = deg[r0];
+                    store8(reinterpret_cast<uint4 *>(g + r0 * 64) + sub, acc, d > 0.0 ? (float)(1.0 / d) : 0.f);
                 }
-                if (lane == 0) cnt[slot] = 0;
-                const double d = deg[r0];
-                const float inv = d > 0.0 ? (float)(1.0 / d) : 0.f;
-                reinterpret_cast<__nv_bfloat162 *>(g + r0 * 64)[lane] = __floats2bfloat162_rn(a0 * inv, a1 * inv);
             }
         }
     }
@@ -478,12 +488,13 @@ __device__ __forceinline__ bool gemm_run(uint32_t taddr, uint32_t a_s, uint32_t 
 
 // One layer on a tile of 128 nodes: stage [h_v | g_v] (BF16, g from the
 // aggregation pass) and the packed weights, one MMA chain, epilogue
-// relu(D + b) -> h_out (BF16); the last layer also writes z0 = w_o . h + b_o.
+// relu(D + b) -> h_out (BF16); the last layer also writes
+// z0 = base + w_o . h + b_o.
 template <int FIN, bool LAST>
 __global__ void __launch_bounds__(128)
 k_layer_fwd(int64_t n, const __nv_bfloat16 *__restrict__ h_in, const __nv_bfloat16 *__restrict__ g_in,
             const __nv_bfloat16 *__restrict__ img, const float *__restrict__ bias, const float *__restrict__ head,
-            __nv_bfloat16 *__restrict__ h_out, float *__restrict__ z0, int *err)
+            const float *__restrict__ base, __nv_bfloat16 *__restrict__ h_out, float *__restrict__ z0, int *err)
 {
     constexpr int KP = FIN == kFin0 ? 16 : 2 * FIN;
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -548,7 +559,7 @@ k_layer_fwd(int64_t n, const __nv_bfloat16 *__restrict__ h_in, const __nv_bfloat
             dst[1] = reinterpret_cast<const uint4 *>(hb)[1];
         }
     }
-    if (LAST && v < n) z0[v] = zacc + head[kHid];
+    if (LAST && v < n) z0[v] = base[v] + zacc + head[kHid];
     gemm_teardown(taddr, 64);
 }
 
@@ -807,6 +818,7 @@ struct fj_mpnn {
     __nv_bfloat16 *g[2] = {nullptr, nullptr};           // n x 64 (inputs of layers 2, 3)
     float *z0 = nullptr;
     double *mv = nullptr;                               // n: m_v
+    float *base = nullptr;                              // n: one Jacobi step from s
     int64_t cap_part = 0;
     float *part = nullptr;                              // per long-row chunk: 64 partial sums
     int64_t cap_bwd = 0;
@@ -863,6 +875,7 @@ fj_status ensure_fwd(fj_mpnn *m, int64_t n)
     for (auto &p : m->g) FJ_CHECK(grow(&p, kHid * n));
     FJ_CHECK(grow(&m->z0, n));
     FJ_CHECK(grow(&m->mv, n));
+    FJ_CHECK(grow(&m->base, n));
     m->cap = n;
     return FJ_OK;
 }
@@ -909,25 +922,25 @@ fj_status forward(fj_mpnn *m, fj_graph *g, const double *sd, cudaStream_t st)
     const unsigned agrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ip->nitems, 8), 152 * 8));
     k_agg_s<<<agrid, 256, 0, st>>>(ip->items, ip->nitems, c.row_ptr, c.col, c.w, c.deg64, sd, m->mv, ip->part,
                                    ip->cnt, ip->slot_first, ip->slot_nchunk, n, m->err);
-    k_features<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(n, c.deg64, c.indeg, sd, m->mv, m->x);
+    k_features<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(n, c.deg64, c.indeg, sd, m->mv, m->x, m->base);
     k_agg4<<<agrid, 256, 0, st>>>(ip->items, ip->nitems, c.row_ptr, c.col, c.w, c.deg64, m->x, m->g0, m->part,
                                   ip->cnt, ip->slot_first, ip->slot_nchunk, n, m->err);
     const unsigned tiles = (unsigned)std::max<int64_t>(1, (n + kTile - 1) / kTile);
     const float *th = m->theta;
     const int ho = head_off();
-    k_layer_fwd<kFin0, false><<<tiles, 128, kGemmSmem, st>>>(n, m->x, m->g0, m->img_fwd[0], th + layer_off(0).b,
-                                                             th + ho, m->h[0], m->z0, m->err);
+    k_layer_fwd<kFin0, false><<<tiles, 128, kSmemFwd4, st>>>(n, m->x, m->g0, m->img_fwd[0], th + layer_off(0).b,
+                                                             th + ho, m->base, m->h[0], m->z0, m->err);
     for (int l = 1; l < 3; ++l) {
         k_agg64<<<agrid, 256, 0, st>>>(ip->items, ip->nitems, c.row_ptr, c.col, c.w, c.deg64, m->h[l - 1],
                                        m->g[l - 1], m->part, ip->cnt, ip->slot_first, ip->slot_nchunk, n, m->err);
         if (l == 1)
-            k_layer_fwd<kHid, false><<<tiles, 128, kGemmSmem, st>>>(n, m->h[0], m->g[0], m->img_fwd[1],
-                                                                    th + layer_off(1).b, th + ho, m->h[1], m->z0,
-                                                                    m->err);
+            k_layer_fwd<kHid, false><<<tiles, 128, kSmemFwd64, st>>>(n, m->h[0], m->g[0], m->img_fwd[1],
+                                                                    th + layer_off(1).b, th + ho, m->base, m->h[1],
+                                                                    m->z0, m->err);
         else
-            k_layer_fwd<kHid, true><<<tiles, 128, kGemmSmem, st>>>(n, m->h[1], m->g[1], m->img_fwd[2],
-                                                                   th + layer_off(2).b, th + ho, m->h[2], m->z0,
-                                                                   m->err);
+            k_layer_fwd<kHid, true><<<tiles, 128, kSmemFwd64, st>>>(n, m->h[1], m->g[1], m->img_fwd[2],
+                                                                   th + layer_off(2).b, th + ho, m->base, m->h[2],
+                                                                   m->z0, m->err);
     }
     FJ_CUDA(cudaGetLastError());
     return FJ_OK;
@@ -938,12 +951,12 @@ bool g_attrs_set[64] = {};
 fj_status set_attrs(int dev)
 {
     if (dev >= 0 && dev < 64 && g_attrs_set[dev]) return FJ_OK;
-    FJ_CUDA(cudaFuncSetAttribute(k_layer_fwd<kFin0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem));
-    FJ_CUDA(cudaFuncSetAttribute(k_layer_fwd<kHid, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem));
-    FJ_CUDA(cudaFuncSetAttribute(k_layer_fwd<kHid, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem));
-    FJ_CUDA(cudaFuncSetAttribute(k_layer_dx, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem));
-    FJ_CUDA(cudaFuncSetAttribute(k_layer_dw<kFin0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem));
-    FJ_CUDA(cudaFuncSetAttribute(k_layer_dw<kHid>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem));
+    FJ_CUDA(cudaFuncSetAttribute(k_layer_fwd<kFin0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemFwd4));
+    FJ_CUDA(cudaFuncSetAttribute(k_layer_fwd<kHid, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemFwd64));
+    FJ_CUDA(cudaFuncSetAttribute(k_layer_fwd<kHid, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemFwd64));
+    FJ_CUDA(cudaFuncSetAttribute(k_layer_dx, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemDx));
+    FJ_CUDA(cudaFuncSetAttribute(k_layer_dw<kFin0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemDw));
+    FJ_CUDA(cudaFuncSetAttribute(k_layer_dw<kHid>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemDw));
     if (dev >= 0 && dev < 64) g_attrs_set[dev] = true;
     return FJ_OK;
 }
@@ -998,7 +1011,7 @@ void fj_mpnn_destroy(fj_mpnn *m)
     dev_free(m->x); dev_free(m->g0); dev_free(m->z0);
     for (auto p : m->h) dev_free(p);
     for (auto p : m->g) dev_free(p);
-    dev_free(m->dh); dev_free(m->dg); dev_free(m->mv); dev_free(m->part);
+    dev_free(m->dh); dev_free(m->dg); dev_free(m->mv); dev_free(m->part); dev_free(m->base);
     dev_free(m->sin); dev_free(m->zin); dev_free(m->zout);
     dev_free(m->loss); dev_free(m->mm); dev_free(m->err);
     delete m;
@@ -1078,14 +1091,14 @@ fj_status fj_mpnn_grad(fj_mpnn *m, fj_graph *g, const double *s, const double *z
         const __nv_bfloat16 *hin = l == 0 ? m->x : m->h[l - 1];
         const __nv_bfloat16 *gin = l == 0 ? m->g0 : m->g[l - 1];
         if (l == 0)
-            k_layer_dw<kFin0><<<dwgrid, 128, kGemmSmem, st>>>(n, hin, gin, m->dh, m->h[l], m->grad + o.ws,
+            k_layer_dw<kFin0><<<dwgrid, 128, kSmemDw, st>>>(n, hin, gin, m->dh, m->h[l], m->grad + o.ws,
                                                               m->grad + o.b, m->err);
         else
-            k_layer_dw<kHid><<<dwgrid, 128, kGemmSmem, st>>>(n, hin, gin, m->dh, m->h[l], m->grad + o.ws,
+            k_layer_dw<kHid><<<dwgrid, 128, kSmemDw, st>>>(n, hin, gin, m->dh, m->h[l], m->grad + o.ws,
                                                              m->grad + o.b, m->err);
         if (l > 0) {
             // dh <- gradient through h_{l-1} itself, then + the adjoint of the aggregation
-            k_layer_dx<<<tiles, 128, kGemmSmem, st>>>(n, m->dh, m->h[l], m->img_bwd[l], m->dg, m->err);
+            k_layer_dx<<<tiles, 128, kSmemDx, st>>>(n, m->dh, m->h[l], m->img_bwd[l], m->dg, m->err);
             k_scatter64<<<agrid, 256, 0, st>>>(ip->items, ip->nitems, c.row_ptr, c.col, c.w, c.deg64, m->dg, m->dh,
                                                n, m->err);
         }

@@ -292,7 +292,7 @@ template <typename T, bool W>
 __global__ void __launch_bounds__(32 * sweep_warps<T>())
 k_sweep(const Item *__restrict__ items, int64_t item0, int64_t nitems, const int64_t *__restrict__ rp,
         const T *__restrict__ prod, T *dcur, T *__restrict__ r, const T *__restrict__ h, const T *__restrict__ inv,
-        double *__restrict__ zhat, const int32_t *__restrict__ indeg, const T *__restrict__ om,
+        T *__restrict__ zacc, const int32_t *__restrict__ indeg, const T *__restrict__ om,
         const int32_t *__restrict__ slot_first, const int32_t *__restrict__ slot_nchunk, double *part, int32_t *cnt,
         Counters *ctr, int64_t n_rows)
 {
@@ -310,7 +310,7 @@ k_sweep(const Item *__restrict__ items, int64_t item0, int64_t nitems, const int
         T dx = T(0);
         if (abs_t(rx) > hx) {
             dx = ox * rx * ix;
-            zhat[x] += (double)dx;  // read only when the row pushes
+            zacc[x] += dx;  // the pass's increments (folded into FP64 zhat before a certificate)
             rx = (T(1) - ox) * rx;
             my_push += 1;
             my_edges += (unsigned long long)dgx;
@@ -495,14 +495,39 @@ k_sweep(const Item *__restrict__ items, int64_t item0, int64_t nitems, const int
 // is summed by the warp and the last chunk to finish completes the row.
 constexpr int kShortRow = 8;
 
-// gamma_m of the standard bound on an m-term FP64 sum (u = 2^-53), with the
-// FP32 magnitude sum inflated to an upper bound of itself.
-__device__ __forceinline__ double plain_bound(int64_t m, float abs32, double dpl_zx, double spx)
+// gamma_m of the standard bound on an m-term FP64 sum (u = 2^-53), times an
+// upper bound of the sum of |terms|: d_x max|zhat| for the row's products plus
+// the two diagonal terms.  Evaluated in FP32 and inflated to stay an upper
+// bound (the FP64 pipe of this part is narrow; the bound need not be tight).
+__device__ __forceinline__ double plain_bound(int64_t m, double deg, double zmax, double dpl_zx, double spx)
 {
-    const double mm = (double)(m + 4);
-    const double gam = mm * 0x1p-53 / (1.0 - mm * 0x1p-53);
-    const double mag = (double)abs32 * (1.0 + (double)(m + 2) * 0x1p-23) + fabs(dpl_zx) + fabs(spx);
-    return gam * mag;
+    const float mm = (float)(m + 4);
+    const float gam = mm * 0x1p-53f / (1.f - mm * 0x1p-53f);
+    const float mag = (float)deg * (float)zmax + fabsf((float)dpl_zx) + fabsf((float)spx);
+    return (double)(gam * mag * 1.001f);
+}
+
+// FP32 paths: the increments a pass accumulated in FP32 per entry are added to
+// the FP64 estimate (one rounding per entry per pass) and cleared.
+__global__ void k_fold(int64_t n, float *__restrict__ z32, double *__restrict__ zhat)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float d = z32[i];
+        if (d != 0.f) {
+            zhat[i] += (double)d;
+            z32[i] = 0.f;
+        }
+    }
+}
+
+// max |zhat| over n entries into *out (ordered bits of a non-negative double).
+__global__ void k_absmax(int64_t n, const double *__restrict__ z, unsigned long long *out)
+{
+    double m = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = fmax(m, fabs(z[i]));
+    m = warp_max(m);
+    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(reinterpret_cast<double *>(out), m);
 }
 
 template <typename T, bool W>
@@ -512,9 +537,10 @@ k_certify(const Item *__restrict__ items, int64_t nitems, const int64_t *__restr
           const double *__restrict__ sp, const double *__restrict__ deg, const int32_t *__restrict__ graph_of,
           double epsp, T *__restrict__ r, T *__restrict__ da, T *__restrict__ db, unsigned long long *gs,
           const int32_t *__restrict__ slot_first, const int32_t *__restrict__ slot_nchunk, double *part, int32_t *cnt,
-          double *__restrict__ r64, int64_t n_rows)
+          double *__restrict__ r64, const unsigned long long *__restrict__ zmaxp, int64_t n_rows)
 {
     constexpr unsigned FULL = 0xffffffffu;
+    const double zmax = __longlong_as_double((long long)*zmaxp);
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -533,15 +559,13 @@ k_certify(const Item *__restrict__ items, int64_t nitems, const int64_t *__restr
         }
         m_abs = m_rel = m_z = viol = 0.0;
     };
-    // plain pass over [a, e) by one thread: FP64 sum and FP32 magnitude sum
-    auto plain_terms = [&](int64_t a, int64_t e, int64_t step, double &acc, float &mag) {
+    // plain pass over [a, e) by one thread: one FP64 FMA per nonzero
+    auto plain_terms = [&](int64_t a, int64_t e, int64_t step, double &acc) {
         for (int64_t k = a; k < e; k += step) {
             const int32_t cj = __ldg(col + k);
             if (!FJ_IDX_OK(4, cj, n_rows)) continue;
-            const double zc = zhat[cj];
-            const float wk = W ? __ldg(w + k) : 1.f;
-            acc = fma(W ? (double)wk : 1.0, zc, acc);
-            mag = fmaf(wk, fabsf((float)zc), mag);
+            if (W) acc = fma((double)__ldg(w + k), zhat[cj], acc);
+            else acc += zhat[cj];
         }
     };
     auto exact_terms = [&](int64_t a, int64_t e, int64_t step, DD &acc) {
@@ -551,10 +575,10 @@ k_certify(const Item *__restrict__ items, int64_t nitems, const int64_t *__restr
         }
     };
     // the residual from a plain sum, and whether the decision needs the exact one
-    auto plain_residual = [&](int64_t x, int64_t len, double acc, float mag, bool &ambiguous) -> double {
-        const double zx = zhat[x], spx = sp[x], dpl = 1.0 + deg[x];
+    auto plain_residual = [&](int64_t x, int64_t len, double acc, bool &ambiguous) -> double {
+        const double zx = zhat[x], spx = sp[x], dx = deg[x], dpl = 1.0 + dx;
         const double rx = fma(-dpl, zx, spx) + acc;
-        const double bnd = plain_bound(len, mag, dpl * zx, spx);
+        const double bnd = plain_bound(len, dx, zmax, dpl * zx, spx);
         const double thr = fmax(epsp * spx, resid_floor(deg[x], zx));
         ambiguous = fabs(fabs(rx) - thr) <= bnd || !(fabs(rx) <= 1e300);
         return rx;
@@ -569,7 +593,7 @@ k_certify(const Item *__restrict__ items, int64_t nitems, const int64_t *__restr
         double ax = fabs(rx);
         if (!(ax <= 1e300)) ax = INFINITY;
         m_abs = fmax(m_abs, ax);
-        m_rel = fmax(m_rel, ax / sp[x]);
+        m_rel = fmax(m_rel, (double)((float)ax / (float)sp[x]));  // reported, FP32 is enough
         m_z = fmax(m_z, fabs(zx - ce));
         if (ax > fmax(epsp * sp[x], resid_floor(deg[x], zx))) viol += 1.0;
         r[x] = resid_store<T>(rx);
@@ -604,10 +628,9 @@ k_certify(const Item *__restrict__ items, int64_t nitems, const int64_t *__restr
                 const bool shortrow = mine && e - a <= kShortRow;
                 if (shortrow) {
                     double acc = 0.0;
-                    float mag = 0.f;
-                    plain_terms(a, e, 1, acc, mag);
+                    plain_terms(a, e, 1, acc);
                     bool amb = false;
-                    double rx = plain_residual(x, e - a, acc, mag, amb);
+                    double rx = plain_residual(x, e - a, acc, amb);
                     if (amb) {
                         DD d{0.0, 0.0};
                         exact_terms(a, e, 1, d);
@@ -622,12 +645,10 @@ k_certify(const Item *__restrict__ items, int64_t nitems, const int64_t *__restr
                     const int64_t xl = r0 + src + 32 * half;
                     const int64_t al = __shfl_sync(FULL, a, src), el = __shfl_sync(FULL, e, src);
                     double acc = 0.0;
-                    float mag = 0.f;
-                    plain_terms(al + lane, el, 32, acc, mag);
+                    plain_terms(al + lane, el, 32, acc);
                     acc = warp_sum(acc);
-                    mag = warp_sum(mag);
                     bool amb = false;
-                    double rx = plain_residual(xl, el - al, acc, mag, amb);  // same on every lane
+                    double rx = plain_residual(xl, el - al, acc, amb);  // same on every lane
                     if (amb) {
                         DD d{0.0, 0.0};
                         exact_terms(al + lane, el, 32, d);
@@ -639,35 +660,27 @@ k_certify(const Item *__restrict__ items, int64_t nitems, const int64_t *__restr
             }
         } else {
             double acc = 0.0;
-            float mag = 0.f;
-            plain_terms(it.k0 + lane, it.k1, 32, acc, mag);
+            plain_terms(it.k0 + lane, it.k1, 32, acc);
             acc = warp_sum(acc);
-            mag = warp_sum(mag);
             const int slot = it.slot;
             const int first = slot_first[slot], nch = slot_nchunk[slot];
             const int ci = (int)((it.k0 - rp[r0]) / kWarpChunk);
             int last = 0;
             if (lane == 0) {
                 part[2 * (first + ci)] = acc;
-                part[2 * (first + ci) + 1] = (double)mag;
                 __threadfence();
                 last = atomicAdd(&cnt[slot], 1) == nch - 1;
             }
             last = __shfl_sync(FULL, last, 0);
             if (last) {
                 __threadfence();
-                double sum = 0.0, smag = 0.0;
-                for (int c = lane; c < nch; c += 32) {
-                    sum += __ldcg(part + 2 * (first + c));
-                    smag += __ldcg(part + 2 * (first + c) + 1);
-                }
+                double sum = 0.0;
+                for (int c = lane; c < nch; c += 32) sum += __ldcg(part + 2 * (first + c));
                 sum = warp_sum(sum);
-                smag = warp_sum(smag);
                 const int64_t a = rp[r0], e = rp[r0 + 1];
                 bool amb = false;
                 // the chunked sum has at most e - a + nch + 64 rounding steps
-                double rx = plain_residual(r0, (e - a) + nch + 64, sum,
-                                           (float)(smag * (1.0 + (double)nch * 0x1p-23)), amb);
+                double rx = plain_residual(r0, (e - a) + nch + 64, sum, amb);
                 if (amb) {
                     DD d{0.0, 0.0};
                     exact_terms(a + lane, e, 32, d);
@@ -790,7 +803,7 @@ static fj_status ws_grow(fj_graph *g, int64_t entries, int ngraphs)
 {
     Workspace &ws = g->ws;
     if (entries > ws.cap_n) {
-        void **bufs[] = {&ws.r, &ws.h, &ws.da, &ws.db, &ws.om};
+        void **bufs[] = {&ws.r, &ws.h, &ws.da, &ws.db, &ws.om, &ws.z32};
         for (void **p : bufs) {
             dev_free(*p);
             *p = nullptr;
@@ -829,6 +842,7 @@ static fj_status ws_grow(fj_graph *g, int64_t entries, int ngraphs)
         FJ_CUDA(cudaMalloc(&ws.ctr, sizeof(Counters)));
         FJ_CUDA(cudaMallocHost(&ws.ctr_host, sizeof(Counters)));
     }
+    if (!ws.zmax) FJ_CUDA(cudaMalloc(&ws.zmax, sizeof(unsigned long long)));
     return FJ_OK;
 }
 
@@ -1082,6 +1096,8 @@ static fj_status launch_sweep(fj_graph *g, const Plan &p, cudaStream_t st, Run &
     else inv = reinterpret_cast<const T *>(c.inv64);
     const T *om = reinterpret_cast<const T *>(ws.om);
     T *prod = reinterpret_cast<T *>(ws.prod);
+    // FP32: the pass's increments go to an FP32 accumulator; FP64: straight into zhat
+    T *zacc = sizeof(T) == 4 ? reinterpret_cast<T *>(ws.z32) : reinterpret_cast<T *>(ws.zhat);
     const int32_t *lo_of = nullptr;
     (void)lo_of;
     // segment by segment (a class cut into runs whose products stay in L2)
@@ -1103,11 +1119,11 @@ static fj_status launch_sweep(fj_graph *g, const Plan &p, cudaStream_t st, Run &
             (unsigned)std::min<int64_t>(ceil_div(ni, kSweepWarps), sweep_blocks<T>(c.w != nullptr));
         if (c.w)
             k_sweep<T, true><<<grid, 32 * kSweepWarps, 0, st>>>(wp.items, i0, ni, c.row_ptr, prod, dcur, r, h, inv,
-                                                                ws.zhat, c.indeg, om, wp.slot_first, wp.slot_nchunk,
+                                                                zacc, c.indeg, om, wp.slot_first, wp.slot_nchunk,
                                                                 wp.part, wp.cnt, ws.ctr, c.n);
         else
             k_sweep<T, false><<<grid, 32 * kSweepWarps, 0, st>>>(wp.items, i0, ni, c.row_ptr, prod, dcur, r, h, inv,
-                                                                 ws.zhat, c.indeg, om, wp.slot_first, wp.slot_nchunk,
+                                                                 zacc, c.indeg, om, wp.slot_first, wp.slot_nchunk,
                                                                  wp.part, wp.cnt, ws.ctr, c.n);
         FJ_CUDA(cudaGetLastError());
         FJ_CHECK(run.after(st));
@@ -1168,14 +1184,21 @@ static fj_status launch_certify(fj_graph *g, const Plan &p, double epsp, cudaStr
     T *r = reinterpret_cast<T *>(ws.r), *da = reinterpret_cast<T *>(ws.da), *db = reinterpret_cast<T *>(ws.db);
     unsigned long long *gs = reinterpret_cast<unsigned long long *>(ws.gstat);
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ip.nitems, 8), 152 * 8));
+    if (sizeof(T) == 4) {
+        k_fold<<<grid_for(c.n, 256, 152 * 8), 256, 0, st>>>(c.n, reinterpret_cast<float *>(ws.z32), ws.zhat);
+        run.launches += 1;
+    }
+    FJ_CUDA(cudaMemsetAsync(ws.zmax, 0, sizeof(unsigned long long), st));
+    k_absmax<<<grid_for(c.n, 256, 152 * 8), 256, 0, st>>>(c.n, ws.zhat, ws.zmax);
+    run.launches += 1;
     if (c.w)
         k_certify<T, true><<<grid, 256, 0, st>>>(ip.items, ip.nitems, c.row_ptr, c.col, c.w, ws.zhat, ws.sp, c.deg64,
                                                  c.graph_of, epsp, r, da, db, gs, ip.slot_first, ip.slot_nchunk,
-                                                 ip.part, ip.cnt, ws.r64, c.n);
+                                                 ip.part, ip.cnt, ws.r64, ws.zmax, c.n);
     else
         k_certify<T, false><<<grid, 256, 0, st>>>(ip.items, ip.nitems, c.row_ptr, c.col, c.w, ws.zhat, ws.sp,
                                                   c.deg64, c.graph_of, epsp, r, da, db, gs, ip.slot_first,
-                                                  ip.slot_nchunk, ip.part, ip.cnt, ws.r64, c.n);
+                                                  ip.slot_nchunk, ip.part, ip.cnt, ws.r64, ws.zmax, c.n);
     FJ_CUDA(cudaGetLastError());
     return FJ_OK;
 }
@@ -1302,6 +1325,7 @@ static fj_status solve_t(fj_graph *g, const double *s, const double *z0, const f
                                                          din, ws.sp, ws.zhat, r, h, da, db,
                                                          reinterpret_cast<T *>(ws.om));
     FJ_CUDA(cudaGetLastError());
+    if (sizeof(T) == 4) FJ_CUDA(cudaMemsetAsync(ws.z32, 0, sizeof(float) * n, st));
     FJ_CUDA(cudaMemsetAsync(ws.ctr, 0, sizeof(Counters), st));
     FJ_CHECK(read_dev_error(g, st));
     Run run;
@@ -1703,7 +1727,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
 k_sweep_batch(const Item *__restrict__ items, int64_t item0, int64_t nitems, const int64_t *__restrict__ rp,
               const int32_t *__restrict__ col, const float *__restrict__ w, int k, T *dcur,
               const T *__restrict__ dprev, T *__restrict__ r, const T *__restrict__ h, const T *__restrict__ inv,
-              double *__restrict__ zhat, const T *__restrict__ om, const int32_t *__restrict__ indeg,
+              T *__restrict__ zacc, const T *__restrict__ om, const int32_t *__restrict__ indeg,
               const int32_t *__restrict__ slot_first, const int32_t *__restrict__ slot_nchunk, double *partk,
               int32_t *cnt, Counters *ctr, unsigned int *tick, int64_t n_rows)
 {
@@ -1737,7 +1761,7 @@ k_sweep_batch(const Item *__restrict__ items, int64_t item0, int64_t nitems, con
         T dx = T(0);
         if (abs_t(rx) > ph[hh]) {
             dx = pom * rx * pinv;
-            zhat[q] += (double)dx;
+            zacc[q] += dx;
             rx = (T(1) - pom) * rx;
             my_push += 1;
             my_edges += (unsigned long long)pdeg;
@@ -1836,7 +1860,6 @@ k_sweep_batch(const Item *__restrict__ items, int64_t item0, int64_t nitems, con
 // compare as integers) and added with one atomic per vector and field.
 struct PlainAcc {
     double s;
-    float m;
 };
 
 template <typename T, bool W>
@@ -1846,9 +1869,10 @@ k_certify_batch(const Item *__restrict__ items, int64_t nitems, const int64_t *_
                 const double *__restrict__ sp, const double *__restrict__ deg, double epsp, T *__restrict__ r,
                 T *__restrict__ da, T *__restrict__ db, unsigned long long *gs, const int32_t *__restrict__ slot_first,
                 const int32_t *__restrict__ slot_nchunk, double *partk, int32_t *cnt, double *__restrict__ r64,
-                int64_t n_rows)
+                const unsigned long long *__restrict__ zmaxp, int64_t n_rows)
 {
     __shared__ unsigned long long sred[4][64];
+    const double zmax = __longlong_as_double((long long)*zmaxp);
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < 4 * 64; i += 256) (&sred[0][0])[i] = 0ULL;
     __syncthreads();
@@ -1864,7 +1888,7 @@ k_certify_batch(const Item *__restrict__ items, int64_t nitems, const int64_t *_
         const double zx = zhat[q], spx = sp[q], dpl = 1.0 + deg[x];
         double rx = fma(-dpl, zx, spx) + acc.s;
         const double thr = fmax(epsp * spx, resid_floor(deg[x], zx));
-        const double bnd = plain_bound(len, acc.m, dpl * zx, spx);
+        const double bnd = plain_bound(len, deg[x], zmax, dpl * zx, spx);
         if (fabs(fabs(rx) - thr) <= bnd || !(fabs(rx) <= 1e300)) {
             DD d{0.0, 0.0};  // exact re-evaluation of this entry, by this lane
             for (int64_t kk = rp[x]; kk < rp[x + 1]; ++kk) {
@@ -1878,7 +1902,7 @@ k_certify_batch(const Item *__restrict__ items, int64_t nitems, const int64_t *_
         const double ce = gsd[(int64_t)j * kGs + 1];
         const double ax = fabs(rx) <= 1e300 ? fabs(rx) : INFINITY;
         m_abs[hh] = fmax(m_abs[hh], ax);
-        m_rel[hh] = fmax(m_rel[hh], ax / spx);
+        m_rel[hh] = fmax(m_rel[hh], (double)((float)ax / (float)spx));
         m_z[hh] = fmax(m_z[hh], fabs(zx - ce));
         if (ax > thr) viol[hh] += 1.0;
         r[q] = resid_store<T>(rx);
@@ -1907,10 +1931,7 @@ k_certify_batch(const Item *__restrict__ items, int64_t nitems, const int64_t *_
         db[q] = T(0);
     };
     auto src = [&](int32_t c) -> const double * { return zhat + (int64_t)c * k; };
-    auto add = [](PlainAcc &acc, float a, double v) {
-        acc.s = fma((double)a, v, acc.s);
-        acc.m = fmaf(a, fabsf((float)v), acc.m);
-    };
+    auto add = [](PlainAcc &acc, float a, double v) { acc.s = W ? fma((double)a, v, acc.s) : acc.s + v; };
     auto no_begin = [](int64_t) {};
     for (int64_t ii = (int64_t)blockIdx.x * 8 + wl; ii < nitems; ii += nwarps) {
         const Item it = items[ii];
@@ -2013,7 +2034,7 @@ static fj_status bws_grow(fj_graph *g, int k, int64_t nparts, int64_t nclasses)
     }
     const int64_t need = g->csr.n * k;
     if (need > b.cap) {
-        void **vb[] = {&b.r, &b.h, &b.da, &b.db};
+        void **vb[] = {&b.r, &b.h, &b.da, &b.db, &b.z32};
         for (void **p : vb) {
             dev_free(*p);
             *p = nullptr;
@@ -2058,6 +2079,7 @@ static fj_status solve_batch_t(fj_graph *g, const double *S, const double *Z0, i
         FJ_CUDA(cudaMalloc(&ws.ctr, sizeof(Counters)));
         FJ_CUDA(cudaMallocHost(&ws.ctr_host, sizeof(Counters)));
     }
+    if (!ws.zmax) FJ_CUDA(cudaMalloc(&ws.zmax, sizeof(unsigned long long)));
     Plan p;
     FJ_CHECK(make_plan(g, o, st, p));
     const DevCSR &c = *p.c;
@@ -2081,6 +2103,8 @@ static fj_status solve_batch_t(fj_graph *g, const double *S, const double *Z0, i
     T *r = reinterpret_cast<T *>(b.r), *h = reinterpret_cast<T *>(b.h);
     T *da = reinterpret_cast<T *>(b.da), *db = reinterpret_cast<T *>(b.db);
     T *om = reinterpret_cast<T *>(b.om);
+    T *zacc = sizeof(T) == 4 ? reinterpret_cast<T *>(b.z32) : reinterpret_cast<T *>(b.zhat);
+    if (sizeof(T) == 4) FJ_CUDA(cudaMemsetAsync(b.z32, 0, sizeof(float) * n * k, st));
     const double *din = p.mc ? g->colr.din_p : nullptr;
     k_init_batch<T><<<grid_for(n * k, 256, 152 * 16), 256, 0, st>>>(n, k, Sd, Z0d, p.perm, gs, epsp, o->omega,
                                                                     c.deg64, din, b.sp, b.zhat, r, h, da, db, om);
@@ -2093,14 +2117,18 @@ static fj_status solve_batch_t(fj_graph *g, const double *S, const double *Z0, i
     const unsigned cgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(wp.nitems, 8), 152 * 8));
     auto certify = [&]() -> fj_status {
         k_cert_reset<<<1, 64, 0, st>>>(k, gs);
+        if (sizeof(T) == 4)
+            k_fold<<<grid_for(n * k, 256, 152 * 8), 256, 0, st>>>(n * k, reinterpret_cast<float *>(b.z32), b.zhat);
+        FJ_CUDA(cudaMemsetAsync(ws.zmax, 0, sizeof(unsigned long long), st));
+        k_absmax<<<grid_for(n * k, 256, 152 * 8), 256, 0, st>>>(n * k, b.zhat, ws.zmax);
         if (c.w)
             k_certify_batch<T, true><<<cgrid, 256, 0, st>>>(wp.items, wp.nitems, c.row_ptr, c.col, c.w, k, b.zhat,
                                                             b.sp, c.deg64, epsp, r, da, db, gs, wp.slot_first,
-                                                            wp.slot_nchunk, b.partk, wp.cnt, b.r64, c.n);
+                                                            wp.slot_nchunk, b.partk, wp.cnt, b.r64, ws.zmax, c.n);
         else
             k_certify_batch<T, false><<<cgrid, 256, 0, st>>>(wp.items, wp.nitems, c.row_ptr, c.col, c.w, k, b.zhat,
                                                              b.sp, c.deg64, epsp, r, da, db, gs, wp.slot_first,
-                                                             wp.slot_nchunk, b.partk, wp.cnt, b.r64, c.n);
+                                                             wp.slot_nchunk, b.partk, wp.cnt, b.r64, ws.zmax, c.n);
         FJ_CUDA(cudaGetLastError());
         return FJ_OK;
     };
@@ -2129,7 +2157,7 @@ static fj_status solve_batch_t(fj_graph *g, const double *S, const double *Z0, i
                     FJ_CHECK(run.before(st));
 #define FJ_SWEEP_BATCH(WW, DD)                                                                                \
     k_sweep_batch<T, WW, DD><<<grid, 256, 0, st>>>(wp.items, i0, ni, c.row_ptr, c.col, c.w, k, dcur, dprev, r, h, \
-                                                   inv, b.zhat, om, c.indeg, wp.slot_first, wp.slot_nchunk, b.partk, \
+                                                   inv, zacc, om, c.indeg, wp.slot_first, wp.slot_nchunk, b.partk, \
                                                    wp.cnt, ws.ctr, tk, c.n)
                     if (c.w) {
                         if (b.depth == 4) FJ_SWEEP_BATCH(true, 4);
