@@ -43,7 +43,7 @@ WORKLOADS = {
     "ragged256_ba": dict(gen="ragged", count=256, lo=1000, hi=200000, precision="fp32", omega=1.5, cpu_scale=None),
     # learned warm start: train on SBM/BA triples, then held-out directed R-MAT with 16 vectors
     "rmat23_warm16": dict(gen="warm", scale=23, nvec=16, precision="fp32", omega=1.5, palette=8,
-                          train_steps=400, lr=2e-3, cpu_scale=18),
+                          train_steps=1200, lr=2e-3, cpu_scale=18),
     "rmat18_warm16": dict(gen="warm", scale=18, nvec=16, precision="fp32", omega=1.5, palette=8,
                           train_steps=200, lr=2e-3),
 }
@@ -426,9 +426,12 @@ def run_warm(args):
             triples.append((G, s_d, z_d))
     net = capi.MPNN(capi.MPNN.initial_params(1))
     losses = []
-    for it in range(spec["train_steps"]):
+    nsteps = spec["train_steps"]
+    for it in range(nsteps):
         G, s_d, z_d = triples[it % len(triples)]
-        losses.append(net.train_step(G, s_d, z_d, spec["lr"]))
+        # cosine decay of the learning rate to a tenth over the run
+        lr = spec["lr"] * (0.55 + 0.45 * np.cos(np.pi * it / nsteps))
+        losses.append(net.train_step(G, s_d, z_d, lr))
     barrier()
     train_s = time.perf_counter() - t0
 

@@ -105,7 +105,6 @@ struct Workspace {
     void *da = nullptr;     // push increments (current)
     void *db = nullptr;     // push increments (second buffer)
     void *om = nullptr;     // per-node relaxation factor
-    void *z32 = nullptr;    // FP32 paths: increments of the current pass, folded into zhat
     void *prod = nullptr;   // per-nonzero products a_k delta_col(k) of the running class
     int64_t cap_prod = 0;
     double *zhat = nullptr; // estimate of z' (FP64)

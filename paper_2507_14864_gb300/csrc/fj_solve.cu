@@ -292,7 +292,7 @@ template <typename T, bool W>
 __global__ void __launch_bounds__(32 * sweep_warps<T>())
 k_sweep(const Item *__restrict__ items, int64_t item0, int64_t nitems, const int64_t *__restrict__ rp,
         const T *__restrict__ prod, T *dcur, T *__restrict__ r, const T *__restrict__ h, const T *__restrict__ inv,
-        T *__restrict__ zacc, const int32_t *__restrict__ indeg, const T *__restrict__ om,
+        double *__restrict__ zhat, const int32_t *__restrict__ indeg, const T *__restrict__ om,
         const int32_t *__restrict__ slot_first, const int32_t *__restrict__ slot_nchunk, double *part, int32_t *cnt,
         Counters *ctr, int64_t n_rows)
 {
@@ -310,7 +310,7 @@ k_sweep(const Item *__restrict__ items, int64_t item0, int64_t nitems, const int
         T dx = T(0);
         if (abs_t(rx) > hx) {
             dx = ox * rx * ix;
-            zacc[x] += dx;  // the pass's increments (folded into FP64 zhat before a certificate)
+            zhat[x] += (double)dx;  // read only when the row pushes
             rx = (T(1) - ox) * rx;
             my_push += 1;
             my_edges += (unsigned long long)dgx;
@@ -507,8 +507,11 @@ __device__ __forceinline__ double plain_bound(int64_t m, double deg, double zmax
     return (double)(gam * mag * 1.001f);
 }
 
-// FP32 paths: the increments a pass accumulated in FP32 per entry are added to
-// the FP64 estimate (one rounding per entry per pass) and cleared.
+// FP32 batch path: the increments a check interval accumulated in FP32 per
+// entry are added to the FP64 estimate and cleared (the batch sweep then does
+// an FP32 instead of an FP64 read-modify-write per push; measured: fewer
+// bytes win for 64 vectors, while for one vector the few extra sweeps that
+// the coarser accumulation costs do not pay).
 __global__ void k_fold(int64_t n, float *__restrict__ z32, double *__restrict__ zhat)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -803,7 +806,7 @@ static fj_status ws_grow(fj_graph *g, int64_t entries, int ngraphs)
 {
     Workspace &ws = g->ws;
     if (entries > ws.cap_n) {
-        void **bufs[] = {&ws.r, &ws.h, &ws.da, &ws.db, &ws.om, &ws.z32};
+        void **bufs[] = {&ws.r, &ws.h, &ws.da, &ws.db, &ws.om};
         for (void **p : bufs) {
             dev_free(*p);
             *p = nullptr;
@@ -1096,8 +1099,6 @@ static fj_status launch_sweep(fj_graph *g, const Plan &p, cudaStream_t st, Run &
     else inv = reinterpret_cast<const T *>(c.inv64);
     const T *om = reinterpret_cast<const T *>(ws.om);
     T *prod = reinterpret_cast<T *>(ws.prod);
-    // FP32: the pass's increments go to an FP32 accumulator; FP64: straight into zhat
-    T *zacc = sizeof(T) == 4 ? reinterpret_cast<T *>(ws.z32) : reinterpret_cast<T *>(ws.zhat);
     const int32_t *lo_of = nullptr;
     (void)lo_of;
     // segment by segment (a class cut into runs whose products stay in L2)
@@ -1119,11 +1120,11 @@ static fj_status launch_sweep(fj_graph *g, const Plan &p, cudaStream_t st, Run &
             (unsigned)std::min<int64_t>(ceil_div(ni, kSweepWarps), sweep_blocks<T>(c.w != nullptr));
         if (c.w)
             k_sweep<T, true><<<grid, 32 * kSweepWarps, 0, st>>>(wp.items, i0, ni, c.row_ptr, prod, dcur, r, h, inv,
-                                                                zacc, c.indeg, om, wp.slot_first, wp.slot_nchunk,
+                                                                ws.zhat, c.indeg, om, wp.slot_first, wp.slot_nchunk,
                                                                 wp.part, wp.cnt, ws.ctr, c.n);
         else
             k_sweep<T, false><<<grid, 32 * kSweepWarps, 0, st>>>(wp.items, i0, ni, c.row_ptr, prod, dcur, r, h, inv,
-                                                                 zacc, c.indeg, om, wp.slot_first, wp.slot_nchunk,
+                                                                 ws.zhat, c.indeg, om, wp.slot_first, wp.slot_nchunk,
                                                                  wp.part, wp.cnt, ws.ctr, c.n);
         FJ_CUDA(cudaGetLastError());
         FJ_CHECK(run.after(st));
@@ -1184,10 +1185,6 @@ static fj_status launch_certify(fj_graph *g, const Plan &p, double epsp, cudaStr
     T *r = reinterpret_cast<T *>(ws.r), *da = reinterpret_cast<T *>(ws.da), *db = reinterpret_cast<T *>(ws.db);
     unsigned long long *gs = reinterpret_cast<unsigned long long *>(ws.gstat);
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ip.nitems, 8), 152 * 8));
-    if (sizeof(T) == 4) {
-        k_fold<<<grid_for(c.n, 256, 152 * 8), 256, 0, st>>>(c.n, reinterpret_cast<float *>(ws.z32), ws.zhat);
-        run.launches += 1;
-    }
     FJ_CUDA(cudaMemsetAsync(ws.zmax, 0, sizeof(unsigned long long), st));
     k_absmax<<<grid_for(c.n, 256, 152 * 8), 256, 0, st>>>(c.n, ws.zhat, ws.zmax);
     run.launches += 1;
@@ -1325,7 +1322,6 @@ static fj_status solve_t(fj_graph *g, const double *s, const double *z0, const f
                                                          din, ws.sp, ws.zhat, r, h, da, db,
                                                          reinterpret_cast<T *>(ws.om));
     FJ_CUDA(cudaGetLastError());
-    if (sizeof(T) == 4) FJ_CUDA(cudaMemsetAsync(ws.z32, 0, sizeof(float) * n, st));
     FJ_CUDA(cudaMemsetAsync(ws.ctr, 0, sizeof(Counters), st));
     FJ_CHECK(read_dev_error(g, st));
     Run run;
@@ -2171,6 +2167,10 @@ static fj_status solve_batch_t(fj_graph *g, const double *S, const double *Z0, i
                     FJ_CHECK(run.after(st));
                 }
                 k_end_sweep<<<1, 1, 0, st>>>(ws.ctr);
+                ++run.launches;
+            }
+            if (sizeof(T) == 4) {
+                k_fold<<<grid_for(n * k, 256, 152 * 8), 256, 0, st>>>(n * k, reinterpret_cast<float *>(b.z32), b.zhat);
                 ++run.launches;
             }
             FJ_CUDA(cudaMemcpyAsync(ws.ctr_host, ws.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
