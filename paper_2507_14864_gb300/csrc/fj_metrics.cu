@@ -85,19 +85,21 @@ k_metric_main(const int64_t *__restrict__ rp, const int32_t *__restrict__ col, c
         for (int j = 0; j < 4; ++j) part[(int64_t)blockIdx.x * 4 + j] = v[j];
 }
 
-// One warp per graph sums its blocks' partials (nf fields each) in a fixed order.
-__global__ void k_metric_reduce(int ng, const int64_t *__restrict__ gblk, const double *__restrict__ part, int nf,
-                                double *__restrict__ out)
+// One block per graph sums its blocks' partials (nf fields each): thread t
+// adds partials t, t + 256, ... in order, then a fixed tree over the threads.
+__global__ void __launch_bounds__(256)
+k_metric_reduce(int ng, const int64_t *__restrict__ gblk, const double *__restrict__ part, int nf,
+                double *__restrict__ out)
 {
-    const int lane = threadIdx.x & 31;
-    const int gi = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    __shared__ double sm[4][8];
+    const int gi = blockIdx.x;
     if (gi >= ng) return;
-    for (int f = 0; f < nf; ++f) {
-        double acc = 0.0;
-        for (int64_t b = gblk[gi] + lane; b < gblk[gi + 1]; b += 32) acc += part[b * nf + f];
-        acc = warp_sum(acc);
-        if (lane == 0) out[(int64_t)gi * nf + f] = acc;
-    }
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int64_t b = gblk[gi] + threadIdx.x; b < gblk[gi + 1]; b += 256)
+        for (int f = 0; f < nf; ++f) v[f] += part[b * nf + f];
+    block_sums<4>(v, sm);
+    if (threadIdx.x == 0)
+        for (int f = 0; f < nf; ++f) out[(int64_t)gi * nf + f] = v[f];
 }
 
 __global__ void k_metric_mean_div(int ng, const int64_t *__restrict__ node_off, double *__restrict__ mean)
@@ -223,7 +225,7 @@ extern "C" fj_status fj_metrics(fj_graph *g, const double *s, const double *z, f
         zd = stage + n;
     }
     k_metric_mean<<<(unsigned)nb, 256, 0, st>>>(c.blk_row, zd, part);
-    k_metric_reduce<<<(unsigned)ceil_div(ng * 32, 256), 256, 0, st>>>(ng, gblk, part, 1, mean);
+    k_metric_reduce<<<(unsigned)ng, 256, 0, st>>>(ng, gblk, part, 1, mean);
     k_metric_mean_div<<<(unsigned)ceil_div(ng, 256), 256, 0, st>>>(ng, noff, mean);
     if (c.w)
         k_metric_main<true><<<(unsigned)nb, 256, 0, st>>>(c.row_ptr, c.col, c.w, c.blk_row, sd, zd, c.graph_of, mean,
@@ -231,7 +233,7 @@ extern "C" fj_status fj_metrics(fj_graph *g, const double *s, const double *z, f
     else
         k_metric_main<false><<<(unsigned)nb, 256, 0, st>>>(c.row_ptr, c.col, c.w, c.blk_row, sd, zd, c.graph_of, mean,
                                                            part);
-    k_metric_reduce<<<(unsigned)ceil_div(ng * 32, 256), 256, 0, st>>>(ng, gblk, part, 4, res);
+    k_metric_reduce<<<(unsigned)ng, 256, 0, st>>>(ng, gblk, part, 4, res);
     FJ_CUDA(cudaGetLastError());
     std::vector<double> hres((size_t)4 * ng), hmean((size_t)ng);
     FJ_CUDA(cudaMemcpyAsync(hres.data(), res, sizeof(double) * 4 * ng, cudaMemcpyDeviceToHost, st));

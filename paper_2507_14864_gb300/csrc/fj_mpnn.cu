@@ -118,8 +118,8 @@ k_agg_s(const Item *__restrict__ items, int64_t nitems, const int64_t *__restric
         return (w ? (double)w[k] : 1.0) * s[j];
     };
     auto finish = [&](int64_t x, double acc) {
-        const double d = deg[x];
-        m[x] = d > 0.0 ? acc / d : 0.0;
+        const float d = (float)deg[x];  // FP32 scale: m is rounded to bfloat16 / FP32 downstream
+        m[x] = d > 0.f ? (double)((float)acc * __frcp_rn(d)) : 0.0;
     };
     for (int64_t ii = warp; ii < nitems; ii += nwarps) {
         const Item it = items[ii];
@@ -178,11 +178,12 @@ __global__ void k_features(int64_t n, const double *__restrict__ deg, const int3
                            float *__restrict__ base)
 {
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-        base[v] = (float)((s[v] + deg[v] * m[v]) / (1.0 + deg[v]));
-        x[4 * v + 0] = __float2bfloat16_rn((float)s[v]);
-        x[4 * v + 1] = __float2bfloat16_rn((float)log1p(deg[v]));
-        x[4 * v + 2] = __float2bfloat16_rn((float)log1p((double)indeg[v]));
-        x[4 * v + 3] = __float2bfloat16_rn((float)m[v]);
+        const float d = (float)deg[v], sv = (float)s[v], mv = (float)m[v];
+        base[v] = (sv + d * mv) * __frcp_rn(1.f + d);
+        x[4 * v + 0] = __float2bfloat16_rn(sv);
+        x[4 * v + 1] = __float2bfloat16_rn(log1pf(d));
+        x[4 * v + 2] = __float2bfloat16_rn(log1pf((float)indeg[v]));
+        x[4 * v + 3] = __float2bfloat16_rn(mv);
     }
 }
 
@@ -213,8 +214,8 @@ k_agg4(const Item *__restrict__ items, int64_t nitems, const int64_t *__restrict
         acc[3] += a * q.y;
     };
     auto finish = [&](int64_t v, const float (&acc)[4]) {
-        const double d = deg[v];
-        const float inv = d > 0.0 ? (float)(1.0 / d) : 0.f;
+        const float d = (float)deg[v];
+        const float inv = d > 0.f ? __frcp_rn(d) : 0.f;
         __nv_bfloat162 lo = __floats2bfloat162_rn(acc[0] * inv, acc[1] * inv);
         __nv_bfloat162 hi = __floats2bfloat162_rn(acc[2] * inv, acc[3] * inv);
         uint2 raw;
@@ -362,8 +363,8 @@ k_agg64(const Item *__restrict__ items, int64_t nitems, const int64_t *__restric
                     pp[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
                 }
             } else if (slot == 0) {
-                const double d = deg[x];
-                store8(reinterpret_cast<uint4 *>(g + x * 64) + sub, acc, d > 0.0 ? (float)(1.0 / d) : 0.f);
+                const float d = (float)deg[x];
+                store8(reinterpret_cast<uint4 *>(g + x * 64) + sub, acc, d > 0.f ? __frcp_rn(d) : 0.f);
             }
         }
         if (chunk) {
@@ -385,8 +386,8 @@ k_agg64(const Item *__restrict__ items, int64_t nitems, const int64_t *__restric
                     }
                 if (lane == 0) cnt[slt] = 0;
                 if (slot == 0) {
-                    const double d = deg[r0];
-                    store8(reinterpret_cast<uint4 *>(g + r0 * 64) + sub, acc, d > 0.0 ? (float)(1.0 / d) : 0.f);
+                    const float d = (float)deg[r0];
+                    store8(reinterpret_cast<uint4 *>(g + r0 * 64) + sub, acc, d > 0.f ? __frcp_rn(d) : 0.f);
                 }
             }
         }
@@ -409,9 +410,9 @@ k_scatter64(const Item *__restrict__ items, int64_t nitems, const int64_t *__res
         const int64_t r0 = it.r0, r1 = it.slot >= 0 ? it.r0 + 1 : it.r1;
         if (r0 < 0 || r1 > n || r0 >= r1) continue;
         for (int64_t v = r0; v < r1; ++v) {
-            const double d = deg[v];
-            if (!(d > 0.0)) continue;
-            const float inv = (float)(1.0 / d);
+            const float d = (float)deg[v];
+            if (!(d > 0.f)) continue;
+            const float inv = __frcp_rn(d);
             float2 gv = reinterpret_cast<const float2 *>(dg + v * 64)[lane];
             gv.x *= inv;
             gv.y *= inv;
