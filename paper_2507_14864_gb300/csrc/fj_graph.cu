@@ -691,7 +691,7 @@ void fj_graph_destroy(fj_graph *g)
     }
     Workspace &ws = g->ws;
     dev_free(ws.r); dev_free(ws.h); dev_free(ws.da); dev_free(ws.db); dev_free(ws.om); dev_free(ws.prod);
-    dev_free(ws.zhat); dev_free(ws.sp); dev_free(ws.sin); dev_free(ws.zout); dev_free(ws.r64);
+    dev_free(ws.zhat); dev_free(ws.sp); dev_free(ws.sin); dev_free(ws.zout); dev_free(ws.r64); dev_free(ws.zs);
     dev_free(ws.gstat); dev_free(ws.ctr); dev_free(ws.status); dev_free(ws.tile_ctr); dev_free(ws.zmax);
     dev_free(ws.list); dev_free(ws.count); dev_free(ws.partial);
     for (int a = 0; a < 2; ++a)

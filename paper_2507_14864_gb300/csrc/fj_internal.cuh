@@ -112,6 +112,7 @@ struct Workspace {
     double *sin = nullptr;  // caller's s, z0 or z staged on the device
     double *zout = nullptr; // unshifted result staged on the device
     double *r64 = nullptr;  // FP64 residual written by the certificate (frontier push state)
+    float2 *zs = nullptr;   // zhat as FP32 pairs hi + lo for the certificate's off-diagonal sums
     double *gstat = nullptr;  // per graph/RHS: [c_eff, min s, resid_inf, resid_rel, z_inf, violators]
     Counters *ctr = nullptr;
     Counters *ctr_host = nullptr;  // pinned mirror

@@ -478,27 +478,94 @@ k_sweep(const Item *__restrict__ items, int64_t item0, int64_t nitems, const int
 // ============================================================== FP64 certificate
 
 // r64_x = s'_x - (1 + d_x) zhat_x + sum_j a_xj zhat_j  (= s' - (I + L) zhat').
-// Each row is first summed plainly in FP64 (one FMA per nonzero) with an FP32
-// sum of |a_xj zhat_j| beside it, which gives the a-priori bound
-// gamma_m (sum of |terms|), gamma_m = m u / (1 - m u), on that sum's rounding
-// error.  Only when |r64| lies within that bound of the threshold is the row
-// summed again with compensated arithmetic (Dot2), which is exact to about one
-// rounding; the decision |r64| > max(eps' s', resid_floor) is therefore always
-// the exact one, while most rows cost one FP64 FMA per nonzero.  Per graph:
-// max |r64|, max |r64| / s', max |zhat - c_eff|, the number above threshold.
-// Stores r64 into the push residual (magnitude rounded up for FP32) and the
-// FP64 residual, and clears both increment buffers: the push restarts from
-// this residual (a refinement pass).
+// The off-diagonal sum runs in FP32 pair arithmetic: zhat_j is read as a pair
+// of floats hi + lo (k_split_absmax; |zhat - hi - lo| <= 2^-47 |zhat|), every
+// product a hi is split exactly into p + pe (fma), and the running sum is
+// carried as an unevaluated pair S + C with Knuth's error-free addition (the
+// Sum2/Dot2 scheme of Ogita, Rump and Oishi, in single precision).  S + C
+// then meets the a-priori bound of pair_bound below, about n^2 2^-46 d_x
+// max|zhat| for n terms per lane, without one FP64 operation per nonzero (the
+// FP64 pipe of this part is narrow).  The diagonal part and the pair are
+// combined in FP64.  The decision |r64| > max(eps' s', resid_floor) is taken
+// in FP32 only when |r64| is farther from the threshold than the bound plus
+// the FP32 rounding of both sides; otherwise the row is summed again exactly
+// in FP64 double-double (Dot2 over zhat), so the decision is always the exact
+// one.  Per graph: max |r64|, max |r64| / s', max |zhat - c_eff|, the number
+// above threshold.  Stores r64 into the push residual (magnitude rounded up
+// for FP32) and the FP64 residual, and clears both increment buffers: the push
+// restarts from this residual (a refinement pass).
 //
 // One warp per warp tile (grid-strided): a row of at most kShortRow nonzeros
 // is summed by one lane, a longer row by the whole warp; a chunk of a long row
 // is summed by the warp and the last chunk to finish completes the row.
 constexpr int kShortRow = 8;
 
+// An unevaluated FP32 sum s + c.
+struct FF {
+    float s, c;
+};
+
+// acc += a * (z.x + z.y): the product a z.x exactly as p + pe, a z.y rounded
+// (it is 2^-24 below a z.x), p added to s error-free, every error term into c.
+// The _rn intrinsics keep the compiler from contracting these steps.
+template <bool W>
+__device__ __forceinline__ void ff_fma(FF &acc, float a, float2 z)
+{
+    float p, pe, q;
+    if constexpr (W) {
+        p = __fmul_rn(a, z.x);
+        pe = __fmaf_rn(a, z.x, -p);
+        q = __fmul_rn(a, z.y);
+    } else {
+        p = z.x;
+        pe = 0.f;
+        q = z.y;
+    }
+    const float s = __fadd_rn(acc.s, p);
+    const float bp = __fsub_rn(s, acc.s);
+    const float e = __fadd_rn(__fsub_rn(acc.s, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+    acc.s = s;
+    acc.c = __fadd_rn(acc.c, __fadd_rn(e, __fadd_rn(pe, q)));
+}
+
+// Butterfly sum of the lanes' pairs; every lane ends with the same pair
+// (error-free addition gives the same error term in either operand order).
+__device__ __forceinline__ FF warp_ff_sum(FF a)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float bs = __shfl_xor_sync(0xffffffffu, a.s, o), bc = __shfl_xor_sync(0xffffffffu, a.c, o);
+        const float s = __fadd_rn(a.s, bs);
+        const float bp = __fsub_rn(s, a.s);
+        const float e = __fadd_rn(__fsub_rn(a.s, __fsub_rn(s, bp)), __fsub_rn(bs, bp));
+        a.s = s;
+        a.c = __fadd_rn(__fadd_rn(a.c, bc), e);
+    }
+    return a;
+}
+
+// Upper bound on |r64 - r_exact| for a row whose off-diagonal sum took at most
+// n terms per lane in pair arithmetic (a warp reduction counts as at most 8
+// more) and whose pair values were then combined with m64 FP64 roundings.
+// The pair sum errs by at most (2 n (n + 2) + 2) u^2 sum|a zhat| with
+// u = 2^-24, the hi + lo split by 2^-47 sum|a zhat|; 3 (n + 8)^2 + 8 covers
+// both with the tree levels.  The FP64 steps add gamma_{m64} (2^-53) times the
+// magnitudes involved; sum|a zhat| <= d_x max|zhat|, and 2^-100 (1 + d_x)
+// covers subnormal halves.  Evaluated in FP32 and inflated by 1 %.
+__device__ __forceinline__ float pair_bound(int n, int64_t m64, float deg, float zmax, float dpl_zx, float spx)
+{
+    const float nn = (float)(n + 8);
+    const float kpair = (3.f * nn * nn + 8.f) * 0x1p-48f;
+    const float mm = (float)(m64 + 4);
+    const float g64 = mm * 0x1p-53f / (1.f - mm * 0x1p-53f);
+    const float dz = deg * zmax;
+    return 1.01f * (kpair * dz + g64 * (dz + fabsf(dpl_zx) + fabsf(spx)) + 0x1p-100f * (1.f + deg));
+}
+
 // gamma_m of the standard bound on an m-term FP64 sum (u = 2^-53), times an
 // upper bound of the sum of |terms|: d_x max|zhat| for the row's products plus
-// the two diagonal terms.  Evaluated in FP32 and inflated to stay an upper
-// bound (the FP64 pipe of this part is narrow; the bound need not be tight).
+// the two diagonal terms (the batch certificate's plain FP64 sums).  Evaluated
+// in FP32 and inflated to stay an upper bound.
 __device__ __forceinline__ double plain_bound(int64_t m, double deg, double zmax, double dpl_zx, double spx)
 {
     const float mm = (float)(m + 4);
@@ -533,26 +600,47 @@ __global__ void k_absmax(int64_t n, const double *__restrict__ z, unsigned long 
     if ((threadIdx.x & 31) == 0) atomic_max_nonneg(reinterpret_cast<double *>(out), m);
 }
 
+// k_absmax, and zhat split into float pairs: hi = fl32(zhat), lo =
+// fl32(zhat - hi) (zhat - hi is exact in FP64), so zhat - hi - lo is the
+// rounding error of lo, at most 2^-24 |lo| <= 2^-48 |zhat| for normal floats.
+__global__ void k_split_absmax(int64_t n, const double *__restrict__ z, float2 *__restrict__ zs,
+                               unsigned long long *out)
+{
+    double m = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = z[i];
+        const float hi = __double2float_rn(v);
+        zs[i] = make_float2(hi, __double2float_rn(v - (double)hi));
+        m = fmax(m, fabs(v));
+    }
+    m = warp_max(m);
+    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(reinterpret_cast<double *>(out), m);
+}
+
 template <typename T, bool W>
 __global__ void __launch_bounds__(256)
 k_certify(const Item *__restrict__ items, int64_t nitems, const int64_t *__restrict__ rp,
           const int32_t *__restrict__ col, const float *__restrict__ w, const double *__restrict__ zhat,
-          const double *__restrict__ sp, const double *__restrict__ deg, const int32_t *__restrict__ graph_of,
-          double epsp, T *__restrict__ r, T *__restrict__ da, T *__restrict__ db, unsigned long long *gs,
-          const int32_t *__restrict__ slot_first, const int32_t *__restrict__ slot_nchunk, double *part, int32_t *cnt,
-          double *__restrict__ r64, const unsigned long long *__restrict__ zmaxp, int64_t n_rows)
+          const float2 *__restrict__ zs, const double *__restrict__ sp, const double *__restrict__ deg,
+          const int32_t *__restrict__ graph_of, double epsp, T *__restrict__ r, T *__restrict__ da,
+          T *__restrict__ db, unsigned long long *gs, const int32_t *__restrict__ slot_first,
+          const int32_t *__restrict__ slot_nchunk, double *part, int32_t *cnt, double *__restrict__ r64,
+          const unsigned long long *__restrict__ zmaxp, int64_t n_rows)
 {
     constexpr unsigned FULL = 0xffffffffu;
-    const double zmax = __longlong_as_double((long long)*zmaxp);
+    const float zmaxf = (float)__longlong_as_double((long long)*zmaxp);
+    const float epsf = (float)epsp;
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const double *gsd = reinterpret_cast<const double *>(gs);
     int cur_g = -1;
-    double ce = 0.0, m_abs = 0.0, m_rel = 0.0, m_z = 0.0, viol = 0.0;
+    float cef = 0.f, m_rel = 0.f, m_z = 0.f;
+    double m_abs = 0.0, viol = 0.0;
 
     auto flush = [&]() {  // warp-uniform
-        const double a = warp_max(m_abs), rl = warp_max(m_rel), zz = warp_max(m_z), v = warp_sum(viol);
+        const double a = warp_max(m_abs), v = warp_sum(viol);
+        const double rl = warp_max((double)m_rel), zz = warp_max((double)m_z);
         if (lane == 0 && cur_g >= 0) {
             unsigned long long *g = gs + (int64_t)cur_g * kGs;
             atomic_max_nonneg(reinterpret_cast<double *>(g + 2), a);
@@ -560,15 +648,15 @@ k_certify(const Item *__restrict__ items, int64_t nitems, const int64_t *__restr
             atomic_max_nonneg(reinterpret_cast<double *>(g + 4), zz);
             if (v > 0) atomicAdd(reinterpret_cast<double *>(g + 5), v);
         }
-        m_abs = m_rel = m_z = viol = 0.0;
+        m_abs = viol = 0.0;
+        m_rel = m_z = 0.f;
     };
-    // plain pass over [a, e) by one thread: one FP64 FMA per nonzero
-    auto plain_terms = [&](int64_t a, int64_t e, int64_t step, double &acc) {
+    // pair-arithmetic pass over [a, e) by one thread
+    auto pair_terms = [&](int64_t a, int64_t e, int64_t step, FF &acc) {
         for (int64_t k = a; k < e; k += step) {
             const int32_t cj = __ldg(col + k);
             if (!FJ_IDX_OK(4, cj, n_rows)) continue;
-            if (W) acc = fma((double)__ldg(w + k), zhat[cj], acc);
-            else acc += zhat[cj];
+            ff_fma<W>(acc, W ? __ldg(w + k) : 1.f, __ldg(zs + cj));
         }
     };
     auto exact_terms = [&](int64_t a, int64_t e, int64_t step, DD &acc) {
@@ -577,28 +665,40 @@ k_certify(const Item *__restrict__ items, int64_t nitems, const int64_t *__restr
             if (FJ_IDX_OK(4, cj, n_rows)) dd_fma(acc, arc_w<double, W>(w, k), zhat[cj]);
         }
     };
-    // the residual from a plain sum, and whether the decision needs the exact one
-    auto plain_residual = [&](int64_t x, int64_t len, double acc, bool &ambiguous) -> double {
-        const double zx = zhat[x], spx = sp[x], dx = deg[x], dpl = 1.0 + dx;
-        const double rx = fma(-dpl, zx, spx) + acc;
-        const double bnd = plain_bound(len, dx, zmax, dpl * zx, spx);
-        const double thr = fmax(epsp * spx, resid_floor(deg[x], zx));
-        ambiguous = fabs(fabs(rx) - thr) <= bnd || !(fabs(rx) <= 1e300);
+    // The residual from the pair sum (given as an FP64 value `off` after
+    // m64 FP64 roundings) and, when it is decidable in FP32, the decision:
+    // dec = 1 above threshold, 0 not, -1 undecided (needs the exact sum).
+    auto pair_residual = [&](int64_t x, int n, int64_t m64, double off, int &dec) -> double {
+        const double zx = zhat[x], spx = sp[x], dx = deg[x];
+        const double dpl = 1.0 + dx;
+        const double rx = fma(-dpl, zx, spx) + off;
+        const float degf = (float)dx, spf = (float)spx, zxf = zs[x].x;
+        const float bnd = pair_bound(n, m64, degf, zmaxf, (1.f + degf) * zxf, spf);
+        const float arf = fabsf((float)rx);
+        const float thrf = fmaxf(epsf * spf, 0x1p-51f * (1.f + degf) * fabsf(zxf));
+        const float slack = bnd + 0x1p-20f * (arf + thrf);
+        const float gap = arf - thrf;
+        dec = gap > slack ? 1 : (-gap > slack ? 0 : -1);  // NaN or inf: undecided
         return rx;
     };
-    auto exact_residual = [&](int64_t x, DD acc) -> double {
+    auto exact_residual = [&](int64_t x, DD acc, int &dec) -> double {
         dd_add(acc, sp[x]);
         dd_fma(acc, -(1.0 + deg[x]), zhat[x]);
-        return dd_value(acc);
+        const double rx = dd_value(acc);
+        dec = fabs(rx) > fmax(epsp * sp[x], resid_floor(deg[x], zhat[x])) ? 1 : 0;
+        return rx;
     };
-    auto finish = [&](int64_t x, double rx) {
-        const double zx = zhat[x];
+    auto finish = [&](int64_t x, double rx, int dec) {
         double ax = fabs(rx);
-        if (!(ax <= 1e300)) ax = INFINITY;
+        if (!(ax <= 1e300)) {
+            ax = INFINITY;
+            dec = 1;
+        }
+        const float af = (float)ax;
         m_abs = fmax(m_abs, ax);
-        m_rel = fmax(m_rel, (double)((float)ax / (float)sp[x]));  // reported, FP32 is enough
-        m_z = fmax(m_z, fabs(zx - ce));
-        if (ax > fmax(epsp * sp[x], resid_floor(deg[x], zx))) viol += 1.0;
+        m_rel = fmaxf(m_rel, af / (float)sp[x]);  // reported, FP32 is enough
+        m_z = fmaxf(m_z, fabsf(zs[x].x - cef));   // reported, FP32 is enough
+        if (dec) viol += 1.0;
         r[x] = resid_store<T>(rx);
         r64[x] = rx;
         da[x] = T(0);
@@ -616,61 +716,85 @@ k_certify(const Item *__restrict__ items, int64_t nitems, const int64_t *__restr
         if (gph != cur_g) {
             flush();
             cur_g = gph;
-            ce = gsd[(int64_t)gph * kGs + 1];
+            cef = (float)gsd[(int64_t)gph * kGs + 1];
         }
         if (it.slot < 0) {
+            // off-diagonal pair sums of the tile's rows: a short row by its own
+            // lane, a longer one by the warp with the sum handed to the row's
+            // lane; then every lane takes its rows' FP64 steps in parallel
+            int64_t ra[2], re[2];
+            bool mine[2], shrt[2];
+            FF acc[2];
 #pragma unroll
             for (int half = 0; half < 2; ++half) {
                 const int64_t x = r0 + lane + 32 * half;
-                const bool mine = x < r1;
-                int64_t a = 0, e = 0;
-                if (mine) {
-                    a = rp[x];
-                    e = rp[x + 1];
+                mine[half] = x < r1;
+                ra[half] = re[half] = 0;
+                if (mine[half]) {
+                    ra[half] = rp[x];
+                    re[half] = rp[x + 1];
                 }
-                const bool shortrow = mine && e - a <= kShortRow;
-                if (shortrow) {
-                    double acc = 0.0;
-                    plain_terms(a, e, 1, acc);
-                    bool amb = false;
-                    double rx = plain_residual(x, e - a, acc, amb);
-                    if (amb) {
-                        DD d{0.0, 0.0};
-                        exact_terms(a, e, 1, d);
-                        rx = exact_residual(x, d);
-                    }
-                    finish(x, rx);
-                }
-                unsigned longs = __ballot_sync(FULL, mine && !shortrow);
+                shrt[half] = re[half] - ra[half] <= kShortRow;
+                acc[half] = FF{0.f, 0.f};
+                if (mine[half] && shrt[half]) pair_terms(ra[half], re[half], 1, acc[half]);
+            }
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                unsigned longs = __ballot_sync(FULL, mine[half] && !shrt[half]);
                 while (longs) {
                     const int src = __ffs(longs) - 1;
                     longs &= longs - 1;
-                    const int64_t xl = r0 + src + 32 * half;
-                    const int64_t al = __shfl_sync(FULL, a, src), el = __shfl_sync(FULL, e, src);
-                    double acc = 0.0;
-                    plain_terms(al + lane, el, 32, acc);
-                    acc = warp_sum(acc);
-                    bool amb = false;
-                    double rx = plain_residual(xl, el - al, acc, amb);  // same on every lane
-                    if (amb) {
-                        DD d{0.0, 0.0};
-                        exact_terms(al + lane, el, 32, d);
-                        d = warp_dd_sum(d);
-                        rx = exact_residual(xl, d);
-                    }
-                    if (lane == 0) finish(xl, rx);
+                    const int64_t al = __shfl_sync(FULL, ra[half], src), el = __shfl_sync(FULL, re[half], src);
+                    FF t{0.f, 0.f};
+                    pair_terms(al + lane, el, 32, t);
+                    t = warp_ff_sum(t);
+                    if (lane == src) acc[half] = t;
                 }
             }
+            double rx[2];
+            int dec[2];
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                rx[half] = 0.0;
+                dec[half] = 0;
+                if (mine[half]) {
+                    const int64_t len = re[half] - ra[half];
+                    const int nl = shrt[half] ? (int)len : (int)((len + 31) / 32);
+                    rx[half] = pair_residual(r0 + lane + 32 * half, nl, 1, (double)acc[half].s + (double)acc[half].c,
+                                             dec[half]);
+                }
+            }
+            // rows the FP32 decision left open: exact sums
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                const int64_t x = r0 + lane + 32 * half;
+                if (mine[half] && shrt[half] && dec[half] < 0) {
+                    DD d{0.0, 0.0};
+                    exact_terms(ra[half], re[half], 1, d);
+                    rx[half] = exact_residual(x, d, dec[half]);
+                }
+                unsigned open = __ballot_sync(FULL, mine[half] && !shrt[half] && dec[half] < 0);
+                while (open) {
+                    const int src = __ffs(open) - 1;
+                    open &= open - 1;
+                    const int64_t al = __shfl_sync(FULL, ra[half], src), el = __shfl_sync(FULL, re[half], src);
+                    DD d{0.0, 0.0};
+                    exact_terms(al + lane, el, 32, d);
+                    d = warp_dd_sum(d);
+                    if (lane == src) rx[half] = exact_residual(x, d, dec[half]);
+                }
+                if (mine[half]) finish(x, rx[half], dec[half]);
+            }
         } else {
-            double acc = 0.0;
-            plain_terms(it.k0 + lane, it.k1, 32, acc);
-            acc = warp_sum(acc);
+            FF acc{0.f, 0.f};
+            pair_terms(it.k0 + lane, it.k1, 32, acc);
+            acc = warp_ff_sum(acc);
             const int slot = it.slot;
             const int first = slot_first[slot], nch = slot_nchunk[slot];
             const int ci = (int)((it.k0 - rp[r0]) / kWarpChunk);
             int last = 0;
             if (lane == 0) {
-                part[2 * (first + ci)] = acc;
+                part[2 * (first + ci)] = (double)acc.s + (double)acc.c;
                 __threadfence();
                 last = atomicAdd(&cnt[slot], 1) == nch - 1;
             }
@@ -681,18 +805,19 @@ k_certify(const Item *__restrict__ items, int64_t nitems, const int64_t *__restr
                 for (int c = lane; c < nch; c += 32) sum += __ldcg(part + 2 * (first + c));
                 sum = warp_sum(sum);
                 const int64_t a = rp[r0], e = rp[r0 + 1];
-                bool amb = false;
-                // the chunked sum has at most e - a + nch + 64 rounding steps
-                double rx = plain_residual(r0, (e - a) + nch + 64, sum, amb);
-                if (amb) {
+                int dec;
+                // per chunk: kWarpChunk / 32 pair terms per lane; the chunks'
+                // values are summed with at most nch + 64 FP64 roundings
+                double rx = pair_residual(r0, kWarpChunk / 32, (int64_t)nch + 64, sum, dec);
+                if (dec < 0) {
                     DD d{0.0, 0.0};
                     exact_terms(a + lane, e, 32, d);
                     d = warp_dd_sum(d);
-                    rx = exact_residual(r0, d);
+                    rx = exact_residual(r0, d, dec);
                 }
                 if (lane == 0) {
                     cnt[slot] = 0;
-                    finish(r0, rx);
+                    finish(r0, rx, dec);
                 }
             }
         }
@@ -821,6 +946,9 @@ static fj_status ws_grow(fj_graph *g, int64_t entries, int ngraphs)
         dev_free(ws.list);
         ws.list = nullptr;
         FJ_CUDA(cudaMalloc(&ws.list, sizeof(int32_t) * (size_t)entries));
+        dev_free(ws.zs);
+        ws.zs = nullptr;
+        FJ_CUDA(cudaMalloc(&ws.zs, sizeof(float2) * (size_t)entries));
         ws.cap_n = entries;
         ws.gen++;
     }
@@ -1186,14 +1314,14 @@ static fj_status launch_certify(fj_graph *g, const Plan &p, double epsp, cudaStr
     unsigned long long *gs = reinterpret_cast<unsigned long long *>(ws.gstat);
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ip.nitems, 8), 152 * 8));
     FJ_CUDA(cudaMemsetAsync(ws.zmax, 0, sizeof(unsigned long long), st));
-    k_absmax<<<grid_for(c.n, 256, 152 * 8), 256, 0, st>>>(c.n, ws.zhat, ws.zmax);
+    k_split_absmax<<<grid_for(c.n, 256, 152 * 8), 256, 0, st>>>(c.n, ws.zhat, ws.zs, ws.zmax);
     run.launches += 1;
     if (c.w)
-        k_certify<T, true><<<grid, 256, 0, st>>>(ip.items, ip.nitems, c.row_ptr, c.col, c.w, ws.zhat, ws.sp, c.deg64,
-                                                 c.graph_of, epsp, r, da, db, gs, ip.slot_first, ip.slot_nchunk,
-                                                 ip.part, ip.cnt, ws.r64, ws.zmax, c.n);
+        k_certify<T, true><<<grid, 256, 0, st>>>(ip.items, ip.nitems, c.row_ptr, c.col, c.w, ws.zhat, ws.zs, ws.sp,
+                                                 c.deg64, c.graph_of, epsp, r, da, db, gs, ip.slot_first,
+                                                 ip.slot_nchunk, ip.part, ip.cnt, ws.r64, ws.zmax, c.n);
     else
-        k_certify<T, false><<<grid, 256, 0, st>>>(ip.items, ip.nitems, c.row_ptr, c.col, c.w, ws.zhat, ws.sp,
+        k_certify<T, false><<<grid, 256, 0, st>>>(ip.items, ip.nitems, c.row_ptr, c.col, c.w, ws.zhat, ws.zs, ws.sp,
                                                   c.deg64, c.graph_of, epsp, r, da, db, gs, ip.slot_first,
                                                   ip.slot_nchunk, ip.part, ip.cnt, ws.r64, ws.zmax, c.n);
     FJ_CUDA(cudaGetLastError());
