@@ -30,15 +30,15 @@ import numpy as np  # noqa: E402
 
 WORKLOADS = {
     # name: generator, precision, omega, schedule
-    "rmat22_dir": dict(gen="rmat_dir", scale=22, precision="fp32", omega=1.5, palette=8),
+    "rmat22_dir": dict(gen="rmat_dir", scale=22, precision="fp32", omega=1.6, palette=8),
     "ba20k": dict(gen="ba", n=20000, precision="fp64", omega=1.5),
     "rmat24_und": dict(gen="rmat_und", scale=24, precision="fp32", omega=1.8),
-    "rmat16_dir": dict(gen="rmat_dir", scale=16, precision="fp32", omega=1.5),
-    "rmat20_dir": dict(gen="rmat_dir", scale=20, precision="fp32", omega=1.5),
+    "rmat16_dir": dict(gen="rmat_dir", scale=16, precision="fp32", omega=1.6),
+    "rmat20_dir": dict(gen="rmat_dir", scale=20, precision="fp32", omega=1.6),
     # 64 opinion vectors (U[0,1], Beta(1/2,1/2), +-1 labels) as one multi-right-hand-side push
-    "rmat22_und_k64": dict(gen="rmat_und_multi", scale=22, nvec=64, precision="fp32", omega=1.8, cpu_scale=19),
-    "rmat16_und_k64": dict(gen="rmat_und_multi", scale=16, nvec=64, precision="fp32", omega=1.8),
-    "rmat20_und_k64": dict(gen="rmat_und_multi", scale=20, nvec=64, precision="fp32", omega=1.8),
+    "rmat22_und_k64": dict(gen="rmat_und_multi", scale=22, nvec=64, precision="fp32", omega=1.7, cpu_scale=19),
+    "rmat16_und_k64": dict(gen="rmat_und_multi", scale=16, nvec=64, precision="fp32", omega=1.7),
+    "rmat20_und_k64": dict(gen="rmat_und_multi", scale=20, nvec=64, precision="fp32", omega=1.7),
     # 256 BA graphs (m = 5), n log-uniform in [1e3, 2e5], one U[0,1] vector each, as one ragged handle
     "ragged256_ba": dict(gen="ragged", count=256, lo=1000, hi=200000, precision="fp32", omega=1.5, cpu_scale=None),
     # learned warm start: train on SBM/BA triples, then held-out directed R-MAT with 16 vectors

@@ -260,9 +260,10 @@ fj_status fj_solve_batch(fj_graph *g, const double *S, int k, const fj_solve_opt
  * certified solves of s (reps timed calls after one untimed call each, CUDA
  * events on base->stream) for every candidate: Jacobi rounds at omega 1, and
  * the multicolour schedule for palette K in {4, 8, 16, 32} x omega in {1.2,
- * 1.5, 1.8}.  *best receives base with the schedule, palette and omega of the
- * fastest (its colouring is left built on the handle); *best_ms (may be NULL)
- * its mean time.  Costs one colouring per palette and 13 (reps + 1) solves.
+ * 1.5, 1.6, 1.7, 1.8}.  *best receives base with the schedule, palette and
+ * omega of the fastest (its colouring is left built on the handle); *best_ms
+ * (may be NULL) its mean time.  Costs one colouring per palette and
+ * 21 (reps + 1) solves.
  * FJ_ERR_NOT_CONVERGED when no candidate certifies.
  */
 fj_status fj_graph_tune(fj_graph *g, const double *s, const fj_solve_opts *base, int reps,

@@ -245,10 +245,11 @@ __global__ void k_set_i32(int32_t *p, int32_t v) { *p = v; }
 // ============================================================== host pieces
 
 fj_status build_blocks(DevCSR &c, const std::vector<int64_t> &seg_rows, Workspace &ws, int *err, cudaStream_t st,
-                       bool warp_tiles)
+                       TileKind kind)
 {
     const int64_t n = c.n;
-    int32_t *&blk = warp_tiles ? c.wblk_row : c.blk_row;
+    const bool warp_tiles = kind != kTileBlock;
+    int32_t *&blk = kind == kTileSweep ? c.sblk_row : (warp_tiles ? c.wblk_row : c.blk_row);
     dev_free(blk);
     blk = nullptr;
     FJ_CUDA(dalloc(&blk, n + 2));
@@ -259,8 +260,8 @@ fj_status build_blocks(DevCSR &c, const std::vector<int64_t> &seg_rows, Workspac
     if (!seg.empty())
         FJ_CUDA(cudaMemcpyAsync(seg_d, seg.data(), sizeof(int64_t) * seg.size(), cudaMemcpyHostToDevice, st));
     FJ_CHECK(ws_status(ws, scan_tiles(n, 256 * 8)));
-    const int64_t bucket = warp_tiles ? kWarpNnz : kBlockNnz;
-    const int64_t max_rows = warp_tiles ? kWarpRows : kBlockRows;
+    const int64_t bucket = kind == kTileSweep ? kSweepNnz : (warp_tiles ? kWarpNnz : kBlockNnz);
+    const int64_t max_rows = kind == kTileSweep ? kSweepRows : (warp_tiles ? kWarpRows : kBlockRows);
     FJ_CUDA(compact<256, 8>(n, BlockStartPred{c.row_ptr, seg_d, (int)seg.size(), bucket, max_rows}, blk, ws.count,
                             ws.status, ws.tile_ctr, err, st));
     long long nb = 0;
@@ -268,6 +269,11 @@ fj_status build_blocks(DevCSR &c, const std::vector<int64_t> &seg_rows, Workspac
     FJ_CUDA(cudaStreamSynchronize(st));
     k_set_i32<<<1, 1, 0, st>>>(blk + nb, (int32_t)n);
     FJ_CUDA(cudaGetLastError());
+    if (kind == kTileSweep) {
+        c.nsblocks = nb;
+        dev_free(seg_d);
+        return FJ_OK;
+    }
     if (warp_tiles) {
         c.nwblocks = nb;
         dev_free(seg_d);
@@ -303,6 +309,7 @@ static void csr_free(DevCSR &c)
     dev_free(c.graph_of);
     dev_free(c.blk_row);
     dev_free(c.wblk_row);
+    dev_free(c.sblk_row);
     c = DevCSR();
 }
 
@@ -352,8 +359,9 @@ static fj_status derive_arrays(fj_graph *g, DevCSR &c, bool transpose, const std
             dev_free(k0); dev_free(v0); dev_free(k1); dev_free(v1); dev_free(row_of);
         }
     }
-    FJ_CHECK(build_blocks(c, segs, g->ws, g->err, st, false));
-    FJ_CHECK(build_blocks(c, segs, g->ws, g->err, st, true));
+    FJ_CHECK(build_blocks(c, segs, g->ws, g->err, st, kTileBlock));
+    FJ_CHECK(build_blocks(c, segs, g->ws, g->err, st, kTileWarp));
+    FJ_CHECK(build_blocks(c, segs, g->ws, g->err, st, kTileSweep));
     return FJ_OK;
 }
 
@@ -682,7 +690,7 @@ void fj_graph_destroy(fj_graph *g)
     dev_free(g->colr.tcol);
     dev_free(g->colr.tw);
     csr_free(g->colr.pcsr);
-    for (ItemPlan *ip : {&g->wplan_csr, &g->wplan_pcsr}) {
+    for (ItemPlan *ip : {&g->wplan_csr, &g->wplan_pcsr, &g->splan_csr, &g->splan_pcsr}) {
         dev_free(ip->items);
         dev_free(ip->slot_first);
         dev_free(ip->slot_nchunk);
@@ -1157,6 +1165,7 @@ static void colouring_free(fj_graph *g)
     csr_free(cl.pcsr);
     cl = Colouring();
     item_plan_free(g->wplan_pcsr);
+    item_plan_free(g->splan_pcsr);
     g->ws.gen++;
 }
 
@@ -1314,8 +1323,9 @@ fj_status ensure_colouring(fj_graph *g, int palette, cudaStream_t st)
     std::vector<int64_t> segs(hs.begin(), hs.end());
     dev_free(excl);
     dev_free(k0); dev_free(v0); dev_free(k1); dev_free(v1);
-    FJ_CHECK(build_blocks(p, segs, g->ws, g->err, st, false));
-    FJ_CHECK(build_blocks(p, segs, g->ws, g->err, st, true));
+    FJ_CHECK(build_blocks(p, segs, g->ws, g->err, st, kTileBlock));
+    FJ_CHECK(build_blocks(p, segs, g->ws, g->err, st, kTileWarp));
+    FJ_CHECK(build_blocks(p, segs, g->ws, g->err, st, kTileSweep));
     cl.class_blk.assign((size_t)cl.ncolours + 1, p.nblocks);
     for (int k = 0; k < cl.ncolours; ++k) {
         size_t at = (size_t)(std::lower_bound(segs.begin(), segs.end(), cl.class_row[k]) - segs.begin());

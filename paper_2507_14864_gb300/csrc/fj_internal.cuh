@@ -23,6 +23,13 @@ constexpr int kNnzPad = 4;
 constexpr int kWarpNnz = 256;
 constexpr int kWarpRows = 64;
 constexpr int kWarpChunk = 512;
+// Tiles of the single-vector sweep: as warp tiles, twice the nonzeros (32 per
+// lane); fewer, larger tiles spread the per-tile cost of the row kernel.
+constexpr int kSweepNnz = 512;
+constexpr int kSweepRows = 64;
+constexpr int kSweepChunk = 1024;
+// Tilings of a CSR: metric blocks, warp tiles, sweep tiles.
+enum TileKind { kTileBlock = 0, kTileWarp = 1, kTileSweep = 2 };
 
 // One CSR resident on the device plus the per-row arrays the push needs.
 struct DevCSR {
@@ -39,6 +46,8 @@ struct DevCSR {
     int64_t nblocks = 0;
     int32_t *wblk_row = nullptr;  // nwblocks + 1 entries (warp tiles)
     int64_t nwblocks = 0;
+    int32_t *sblk_row = nullptr;  // nsblocks + 1 entries (sweep tiles)
+    int64_t nsblocks = 0;
     std::vector<int64_t> seg_blk;  // host: block ranges of forced segments (classes / graphs)
 };
 
@@ -168,7 +177,8 @@ struct fj_graph {
     std::vector<int64_t> node_off;     // host, ngraphs + 1
     int64_t *node_off_d = nullptr;
     fj::Colouring colr;
-    fj::ItemPlan wplan_csr, wplan_pcsr;  // warp-tile items (sweep and certificate)
+    fj::ItemPlan wplan_csr, wplan_pcsr;  // warp-tile items (certificate, batch sweep, network)
+    fj::ItemPlan splan_csr, splan_pcsr;  // sweep-tile items (single-vector sweep)
     fj::Workspace ws;
     fj::BatchWorkspace bws;
     fj::SortScratch sort;
@@ -181,7 +191,7 @@ namespace fj {
 // fj_graph.cu
 fj_status graph_finish(fj_graph *g, cudaStream_t st);
 fj_status build_blocks(DevCSR &c, const std::vector<int64_t> &seg_rows, Workspace &ws, int *err,
-                       cudaStream_t st, bool warp_tiles);
+                       cudaStream_t st, TileKind kind);
 fj_status ensure_colouring(fj_graph *g, int palette, cudaStream_t st);
 fj_status ensure_ptranspose(fj_graph *g, cudaStream_t st);
 // fj_solve.cu

@@ -249,21 +249,22 @@ k_products(int64_t k0, int64_t k1, const int32_t *__restrict__ col, const float 
 // (0 when it does not push) into dcur.
 //
 // The grid is persistent (as many blocks as can be resident); warp w of W
-// takes the class's work items w, w + W, ...: a tile of at most 2 * kWarpNnz
-// nonzeros (sixteen per lane) and kWarpRows rows (two per lane), reduced by a
-// warp-synchronous segmented scan, or a kWarpChunk chunk of a long row whose
+// takes the class's work items w, w + W, ...: a tile of at most 2 * kSweepNnz
+// nonzeros (32 per lane) and kSweepRows rows (two per lane), a lane walking
+// each of its rows (the warp together for rows over 32 nonzeros), or a
+// kSweepChunk chunk of a long row whose
 // last chunk to finish sums the chunks' partials and applies the update.
 // The products a_xj delta_j come precomputed (k_products); while a warp works
 // on one item, the products of its next item stream into shared memory by
 // asynchronous 16-byte copies (cp.async), so the stream does not pause
 // between items.
-constexpr int kWE = 2 * kWarpNnz / 32;             // nonzeros per lane of a tile
-constexpr int kWR = kWarpRows / 32;                // rows per lane of a tile
-// warps per block: four, three for FP64 (static shared memory stays under 48 KB)
+constexpr int kWE = 2 * kSweepNnz / 32;            // nonzeros per lane of a tile
+constexpr int kWR = kSweepRows / 32;               // rows per lane of a tile
+// warps per block: four, two for FP64 (static shared memory stays under 48 KB)
 template <typename T>
-constexpr int sweep_warps() { return sizeof(T) == 8 ? 3 : 4; }
-constexpr int kStage = 2 * kWarpNnz + 8;           // staged elements per item (tile rounded out to granules)
-static_assert(kWarpChunk <= 2 * kWarpNnz, "a chunk is staged like a tile");
+constexpr int sweep_warps() { return sizeof(T) == 8 ? 2 : 4; }
+constexpr int kStage = 2 * kSweepNnz + 8;          // staged elements per item (tile rounded out to granules)
+static_assert(kSweepChunk <= 2 * kSweepNnz, "a chunk is staged like a tile");
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 {
@@ -346,7 +347,7 @@ k_sweep(const Item *__restrict__ items, int64_t item0, int64_t nitems, const int
         const int nz = (int)(it.k1 - k0);
         const int off = (int)(k0 & (G - 1));
         const bool ok = FJ_IDX_OK(11, r0, n_rows) && FJ_IDX_OK(12, r1, n_rows + 1) &&
-                        FJ_IDX_OK(13, r1 - r0, kWarpRows + 1) && FJ_IDX_OK(17, nz, kStage - 3);
+                        FJ_IDX_OK(13, r1 - r0, kSweepRows + 1) && FJ_IDX_OK(17, nz, kStage - 3);
         if (ok) {
             const T *sc = sprod[wl][s] + off;
             if (it.slot < 0) {
@@ -425,7 +426,7 @@ k_sweep(const Item *__restrict__ items, int64_t item0, int64_t nitems, const int
                 const int first = slot_first[slot], nch = slot_nchunk[slot];
                 int last = 0;
                 if (lane == 0) {
-                    const int ci = (int)((k0 - rp[r0]) / kWarpChunk);
+                    const int ci = (int)((k0 - rp[r0]) / kSweepChunk);
                     part[first + ci] = (double)acc;
                     __threadfence();
                     last = atomicAdd(&cnt[slot], 1) == nch - 1;
@@ -980,7 +981,8 @@ static fj_status ws_grow(fj_graph *g, int64_t entries, int ngraphs)
 struct Plan {
     const DevCSR *c = nullptr;  // CSR the push runs on
     const int32_t *perm = nullptr;
-    const ItemPlan *wip = nullptr;  // warp-tile items (sweep, certificate)
+    const ItemPlan *wip = nullptr;  // warp-tile items (certificate, batch sweep)
+    const ItemPlan *sip = nullptr;  // sweep-tile items (single-vector sweep)
     bool mc = false;
 };
 
@@ -1060,12 +1062,13 @@ __global__ void k_gather_rp(int64_t nb, const int32_t *__restrict__ blk_row, con
 // two staged tiles cut into kChunkNnz chunks.  class_row (multicolour) gives
 // each item the first row of its colour class; without it every item gets 0.
 static fj_status build_items(fj_graph *g, const DevCSR &c, const std::vector<int64_t> *class_row, ItemPlan &ip,
-                             cudaStream_t st, bool warp_tiles)
+                             cudaStream_t st, TileKind kind)
 {
-    const int64_t nb = warp_tiles ? c.nwblocks : c.nblocks;
-    const int32_t *blk_row = warp_tiles ? c.wblk_row : c.blk_row;
-    const int64_t long_row = warp_tiles ? 2 * kWarpNnz : 2 * kBlockNnz;
-    const int64_t chunk = warp_tiles ? kWarpChunk : kChunkNnz;
+    const bool sweep_tiles = kind == kTileSweep, warp_tiles = kind == kTileWarp;
+    const int64_t nb = sweep_tiles ? c.nsblocks : (warp_tiles ? c.nwblocks : c.nblocks);
+    const int32_t *blk_row = sweep_tiles ? c.sblk_row : (warp_tiles ? c.wblk_row : c.blk_row);
+    const int64_t long_row = sweep_tiles ? 2 * kSweepNnz : (warp_tiles ? 2 * kWarpNnz : 2 * kBlockNnz);
+    const int64_t chunk = sweep_tiles ? kSweepChunk : (warp_tiles ? kWarpChunk : kChunkNnz);
     std::vector<int32_t> br((size_t)nb + 1);
     std::vector<long long> bk((size_t)nb + 1);
     long long *bk_d = nullptr;
@@ -1169,15 +1172,20 @@ static fj_status make_plan(fj_graph *g, const fj_solve_opts *o, cudaStream_t st,
     p.mc = o->schedule != FJ_SCHED_JACOBI;
     if (!p.mc) {
         p.c = &g->csr;
-        if (!g->wplan_csr.built) FJ_CHECK(build_items(g, g->csr, nullptr, g->wplan_csr, st, true));
+        if (!g->wplan_csr.built) FJ_CHECK(build_items(g, g->csr, nullptr, g->wplan_csr, st, kTileWarp));
+        if (!g->splan_csr.built) FJ_CHECK(build_items(g, g->csr, nullptr, g->splan_csr, st, kTileSweep));
         p.wip = &g->wplan_csr;
+        p.sip = &g->splan_csr;
         return FJ_OK;
     }
     FJ_CHECK(ensure_colouring(g, o->palette, st));
     p.c = &g->colr.pcsr;
     p.perm = g->colr.perm;
-    if (!g->wplan_pcsr.built) FJ_CHECK(build_items(g, g->colr.pcsr, &g->colr.class_row, g->wplan_pcsr, st, true));
+    if (!g->wplan_pcsr.built) FJ_CHECK(build_items(g, g->colr.pcsr, &g->colr.class_row, g->wplan_pcsr, st, kTileWarp));
+    if (!g->splan_pcsr.built)
+        FJ_CHECK(build_items(g, g->colr.pcsr, &g->colr.class_row, g->splan_pcsr, st, kTileSweep));
     p.wip = &g->wplan_pcsr;
+    p.sip = &g->splan_pcsr;
     return FJ_OK;
 }
 
@@ -1185,7 +1193,7 @@ static fj_status make_plan(fj_graph *g, const fj_solve_opts *o, cudaStream_t st,
 // work list other passes over the graph (the network's aggregations) share.
 fj_status plain_items(fj_graph *g, cudaStream_t st, const ItemPlan **out)
 {
-    if (!g->wplan_csr.built) FJ_CHECK(build_items(g, g->csr, nullptr, g->wplan_csr, st, true));
+    if (!g->wplan_csr.built) FJ_CHECK(build_items(g, g->csr, nullptr, g->wplan_csr, st, kTileWarp));
     *out = &g->wplan_csr;
     return FJ_OK;
 }
@@ -1216,7 +1224,7 @@ static fj_status launch_sweep(fj_graph *g, const Plan &p, cudaStream_t st, Run &
 {
     Workspace &ws = g->ws;
     const DevCSR &c = *p.c;
-    const ItemPlan &wp = *p.wip;
+    const ItemPlan &wp = *p.sip;
     T *bufs[2] = {reinterpret_cast<T *>(ws.da), reinterpret_cast<T *>(ws.db)};
     T *dcur = bufs[sweep & 1];
     const T *dprev = bufs[(sweep - 1) & 1];
@@ -2412,7 +2420,7 @@ std::vector<TuneCand> tune_candidates(bool batch)
     std::vector<TuneCand> c;
     c.push_back({FJ_SCHED_JACOBI, 0, 4, 1.0});
     for (int K : {4, 8, 16, 32})
-        for (double w : {1.2, 1.5, 1.8})
+        for (double w : {1.2, 1.5, 1.6, 1.7, 1.8})
             for (int d : {4, 8}) {
                 if (!batch && d != 4) continue;
                 c.push_back({FJ_SCHED_MULTICOLOUR, K, d, w});
