@@ -42,9 +42,9 @@ WORKLOADS = {
     # 256 BA graphs (m = 5), n log-uniform in [1e3, 2e5], one U[0,1] vector each, as one ragged handle
     "ragged256_ba": dict(gen="ragged", count=256, lo=1000, hi=200000, precision="fp32", omega=1.5, cpu_scale=None),
     # learned warm start: train on SBM/BA triples, then held-out directed R-MAT with 16 vectors
-    "rmat23_warm16": dict(gen="warm", scale=23, nvec=16, precision="fp32", omega=1.5, palette=8,
+    "rmat23_warm16": dict(gen="warm", scale=23, nvec=16, precision="fp32", omega=1.6, palette=8,
                           train_steps=1200, lr=2e-3, cpu_scale=18),
-    "rmat18_warm16": dict(gen="warm", scale=18, nvec=16, precision="fp32", omega=1.5, palette=8,
+    "rmat18_warm16": dict(gen="warm", scale=18, nvec=16, precision="fp32", omega=1.6, palette=8,
                           train_steps=200, lr=2e-3),
 }
 EPS = 1e-6
@@ -327,7 +327,9 @@ def run_gpu(args):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "traffic": None,
                 "kernel": ("k_products + k_sweep (one colour class)" if (k == 1 or cols is not None) else
-                           "k_sweep_batch (one colour class, %d vectors)" % k), "peak_source": peak_kind,
+                           "%s (one colour class, %d vectors)"
+                           % ("k_sweep_batch_bulk" if (spec["precision"] == "fp32" and k % 4 == 0 and k <= 64)
+                              else "k_sweep_batch", k)), "peak_source": peak_kind,
                 "bytes_per_launch": p["push_bytes"] / max(1, p["push_launches"]),
                 "avg_launch_us": 1e3 * p["push_ms"] / max(1, p["push_launches"])}
     info0 = infos[-1]

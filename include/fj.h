@@ -271,8 +271,10 @@ fj_status fj_graph_tune(fj_graph *g, const double *s, const fj_solve_opts *base,
 
 /*
  * fj_graph_tune_batch - as fj_graph_tune for fj_solve_batch on S[n][k], with
- * one more dimension: the number of k-vector gathers each warp keeps in
- * flight (4 or 8).  The best depth stays on the handle for later batch solves.
+ * one more dimension: how each warp gathers the neighbours' k-vectors (4 or 8
+ * per-lane loads in flight, or, for FP32 with k a multiple of 4, bulk
+ * asynchronous copies of whole rows into shared memory, the default).  The
+ * best choice stays on the handle for later batch solves.
  */
 fj_status fj_graph_tune_batch(fj_graph *g, const double *S, int k, const fj_solve_opts *base, int reps,
                               fj_solve_opts *best, double *best_ms, int mem);

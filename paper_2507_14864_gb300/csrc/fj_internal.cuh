@@ -160,7 +160,7 @@ struct BatchWorkspace {
     int64_t cap_partk = 0;
     unsigned int *tick = nullptr;  // per colour class: next tile, retired warps
     int64_t cap_tick = 0;
-    int depth = 4;                 // k-vector gathers in flight per warp (4 or 8; fj_graph_tune_batch)
+    int depth = 0;                 // gathers in flight per warp: 4 or 8 per-lane loads, 0 = bulk copies (FP32)
 };
 
 }  // namespace fj

@@ -16,6 +16,7 @@
 #include <cstring>
 #include <vector>
 
+#include "fj_tc.cuh"
 #include "fj_internal.cuh"
 
 namespace fj {
@@ -2137,6 +2138,258 @@ k_certify_batch(const Item *__restrict__ items, int64_t nitems, const int64_t *_
     }
 }
 
+// ---------------------------------------------------------------- bulk-copy batch sweep
+//
+// The batch sweep with the neighbours' k-vectors gathered by the copy engine:
+// for each batch of kBulkRows nonzeros of a tile, lane l issues one bulk
+// asynchronous copy (cp.async.bulk, completion counted in bytes on an
+// mbarrier) of row col[l] of the increment buffer (k FP32 values, 16-byte
+// aligned because k is a multiple of 4) into a per-warp shared-memory ring of
+// two stages, then the warp consumes the previous batch from shared memory
+// while this one is in flight.  Each warp keeps up to 2 kBulkRows rows in flight with
+// no registers held for them, which the per-lane loads of k_sweep_batch
+// cannot.  Otherwise the update is k_sweep_batch's.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(bytes), "r"((uint32_t)__cvta_generic_to_shared(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+constexpr uint32_t kBulkWaitLimit = 1u << 22;  // polls of an mbarrier before the kernel reports a timeout
+constexpr int kBulkRows = 16;                  // nonzeros (gathered rows) per stage
+
+template <bool W>
+__global__ void __launch_bounds__(256, 3)
+k_sweep_batch_bulk(const Item *__restrict__ items, int64_t item0, int64_t nitems, const int64_t *__restrict__ rp,
+                   const int32_t *__restrict__ col, const float *__restrict__ w, int k, float *dcur,
+                   const float *__restrict__ dprev, float *__restrict__ r, const float *__restrict__ h,
+                   const float *__restrict__ inv, float *__restrict__ zacc, const float *__restrict__ om,
+                   const int32_t *__restrict__ indeg, const int32_t *__restrict__ slot_first,
+                   const int32_t *__restrict__ slot_nchunk, double *partk, int32_t *cnt, Counters *ctr,
+                   unsigned int *tick, int *err, int64_t n_rows)
+{
+    constexpr unsigned FULL = 0xffffffffu;
+    extern __shared__ __align__(128) float ring_all[];  // [8 warps][2 stages][kBulkRows rows][k]
+    __shared__ uint64_t bars[8][2];
+    __shared__ unsigned long long red[2][8];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    if (*reinterpret_cast<volatile int *>(&ctr->done)) return;
+    float *ring = ring_all + (size_t)wl * 2 * kBulkRows * k;
+    if (lane == 0) {
+        tc::mbar_init(&bars[wl][0], 1);
+        tc::mbar_init(&bars[wl][1], 1);
+    }
+    __syncwarp();
+    uint32_t phase = 0;  // bit s: parity of the next completion of stage s
+    bool timed_out = false;
+    const bool has1 = lane < k, has2 = lane + 32 < k;
+    const uint32_t row_bytes = (uint32_t)k * 4u;
+    unsigned long long my_push = 0, my_edges = 0;
+    bool bad = false;
+
+    float pr[2] = {0.f, 0.f}, ph[2] = {0.f, 0.f}, pom = 0.f, pinv = 0.f;
+    int32_t pdeg = 0;
+    auto begin = [&](int64_t x) {
+        const int64_t q = x * k + lane;
+        if (has1) {
+            pr[0] = r[q];
+            ph[0] = h[q];
+        }
+        if (has2) {
+            pr[1] = r[q + 32];
+            ph[1] = h[q + 32];
+        }
+        pom = om[x];
+        pinv = inv[x];
+        pdeg = indeg[x];
+    };
+    auto upd = [&](int64_t x, int hh, float acc) {
+        const int64_t q = x * k + lane + 32 * hh;
+        float rx = pr[hh] + acc;
+        float dx = 0.f;
+        if (fabsf(rx) > ph[hh]) {
+            dx = pom * rx * pinv;
+            zacc[q] += dx;
+            rx = (1.f - pom) * rx;
+            my_push += 1;
+            my_edges += (unsigned long long)pdeg;
+        }
+        if (!isfinite(rx)) bad = true;
+        r[q] = rx;
+        dcur[q] = dx;
+    };
+    auto apply_row = [&](int64_t x, float s1, float s2) {
+        if (has1) upd(x, 0, s1);
+        if (has2) upd(x, 1, s2);
+    };
+
+    // Walk of [k0, k1): rows r0.. (a tile) or one chunk of row r0.  Returns
+    // false after a wait that timed out (the warp then stops).
+    auto walk = [&](int64_t r0, int64_t r1, int64_t k0, int64_t k1, bool chunk, int32_t lo, float &o1,
+                    float &o2) -> bool {
+        int64_t e_lo = k1, e_hi = k1;
+        if (!chunk) {
+            if (r0 + lane < r1) e_lo = rp[r0 + lane + 1];
+            if (r0 + 32 + lane < r1) e_hi = rp[r0 + 33 + lane];
+        } else {
+            r1 = r0 + 1;
+        }
+        int64_t x = r0;
+        auto row_end = [&](int64_t xx) -> int64_t {
+            const int i = (int)(xx - r0);
+            return __shfl_sync(FULL, i < 32 ? e_lo : e_hi, i & 31);
+        };
+        int64_t xe = x < r1 ? row_end(x) : k1;
+        if (!chunk && x < r1) begin(x);
+        float a1 = 0.f, a2 = 0.f;
+        auto flush_until = [&](int64_t pos) {
+            while (x < r1 && xe <= pos) {
+                if (!chunk) apply_row(x, a1, a2);
+                else {
+                    o1 = a1;
+                    o2 = a2;
+                }
+                a1 = a2 = 0.f;
+                ++x;
+                if (x < r1) {
+                    xe = row_end(x);
+                    if (!chunk) begin(x);
+                }
+            }
+        };
+        // issue the copies of the batch at `base` into stage s; returns the lane's weight
+        auto issue = [&](int64_t base, int s) -> float {
+            const int64_t kk = base + lane;
+            int32_t cl = 0;
+            float al = 0.f;
+            const bool in = lane < kBulkRows && kk < k1;
+            if (in) {
+                cl = __ldg(col + kk);
+                al = W ? __ldg(w + kk) : 1.f;
+                if (!FJ_IDX_OK(15, cl, n_rows)) {
+                    cl = 0;
+                    al = 0.f;
+                }
+            }
+            const int64_t left = k1 - base;
+            const uint32_t m = (uint32_t)(left < kBulkRows ? left : kBulkRows);
+            if (lane == 0) mbar_expect_tx(&bars[wl][s], m * row_bytes);
+            __syncwarp();
+            if (in) {
+                const float *srcp = (cl < lo ? (const float *)dcur : dprev) + (int64_t)cl * k;
+                bulk_g2s(ring + ((size_t)s * kBulkRows + lane) * k, srcp, row_bytes, &bars[wl][s]);
+            }
+            return al;
+        };
+        int s = 0;
+        float al_cur = 0.f;
+        if (k0 < k1) al_cur = issue(k0, 0);
+        for (int64_t base = k0; base < k1; base += kBulkRows) {
+            float al_nxt = 0.f;
+            if (base + kBulkRows < k1) al_nxt = issue(base + kBulkRows, s ^ 1);
+            if (!tc::mbar_wait_bounded(&bars[wl][s], (phase >> s) & 1u, kBulkWaitLimit)) return false;
+            phase ^= 1u << s;
+            const int64_t left = k1 - base;
+            const int m = (int)(left < kBulkRows ? left : kBulkRows);
+            const float *st = ring + (size_t)s * kBulkRows * k;
+            for (int t = 0; t < m; ++t) {
+                flush_until(base + t);
+                const float a = __shfl_sync(FULL, al_cur, t);
+                if (has1) a1 += a * st[t * k + lane];
+                if (has2) a2 += a * st[t * k + lane + 32];
+            }
+            __syncwarp();
+            tc::fence_async_smem();  // these reads come before the next copies into stage s
+            al_cur = al_nxt;
+            s ^= 1;
+        }
+        flush_until(k1);
+        return true;
+    };
+
+    for (;;) {
+        unsigned int got = 0;
+        if (lane == 0) got = atomicAdd(&tick[0], 1u);
+        got = __shfl_sync(FULL, got, 0);
+        if ((int64_t)got >= nitems) break;
+        const Item it = items[item0 + got];
+        const int64_t r0 = it.r0, r1 = it.r1;
+        if (!FJ_IDX_OK(11, r0, n_rows) || !FJ_IDX_OK(12, r1, n_rows + 1) ||
+            (it.slot < 0 && !FJ_IDX_OK(13, r1 - r0, kWarpRows + 1)))
+            continue;
+        float o1 = 0.f, o2 = 0.f;
+        if (!walk(r0, r1, it.k0, it.k1, it.slot >= 0, it.lo, o1, o2)) {
+            timed_out = true;
+            break;
+        }
+        if (it.slot >= 0) {
+            const int slot = it.slot;
+            const int first = slot_first[slot], nch = slot_nchunk[slot];
+            const int ci = (int)((it.k0 - rp[r0]) / kWarpChunk);
+            if (has1) partk[(int64_t)(first + ci) * k + lane] = (double)o1;
+            if (has2) partk[(int64_t)(first + ci) * k + lane + 32] = (double)o2;
+            __threadfence();
+            __syncwarp();
+            int last = 0;
+            if (lane == 0) last = atomicAdd(&cnt[slot], 1) == nch - 1;
+            last = __shfl_sync(FULL, last, 0);
+            if (last) {
+                __threadfence();
+                double a1 = 0.0, a2 = 0.0;
+                for (int c = 0; c < nch; ++c) {
+                    if (has1) a1 += __ldcg(partk + (int64_t)(first + c) * k + lane);
+                    if (has2) a2 += __ldcg(partk + (int64_t)(first + c) * k + lane + 32);
+                }
+                if (lane == 0) cnt[slot] = 0;
+                begin(r0);
+                apply_row(r0, (float)a1, (float)a2);
+            }
+        }
+    }
+    if (timed_out) {
+        // report, then let every copy this warp issued land before the block
+        // leaves (both stages' outstanding phases, each wait bounded)
+        if (lane == 0) dev_error(err, DEV_SPIN_TIMEOUT);
+        for (int s = 0; s < 2; ++s) tc::mbar_wait_bounded(&bars[wl][s], (phase >> s) & 1u, kBulkWaitLimit);
+    }
+    if (lane == 0) {
+        __threadfence();
+        if (atomicAdd(&tick[1], 1u) == gridDim.x * 8u - 1u) {
+            tick[0] = 0u;
+            tick[1] = 0u;
+        }
+    }
+    my_push = warp_sum(my_push);
+    my_edges = warp_sum(my_edges);
+    const unsigned anybad = __ballot_sync(FULL, bad);
+    if (lane == 0) {
+        red[0][wl] = my_push;
+        red[1][wl] = my_edges;
+        if (anybad) ctr->nonfinite = 1.0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long pp = 0, ee = 0;
+        for (int i = 0; i < 8; ++i) {
+            pp += red[0][i];
+            ee += red[1][i];
+        }
+        if (pp) {
+            atomicAdd(&ctr->pushes, pp);
+            atomicAdd(&ctr->sweep_pushes, pp);
+            atomicAdd(&ctr->edges, ee);
+        }
+    }
+}
+
 // Resident blocks of the batch sweep kernel (its persistent grid).
 template <typename T>
 static int64_t batch_sweep_blocks(bool weighted)
@@ -2268,6 +2521,20 @@ static fj_status solve_batch_t(fj_graph *g, const double *S, const double *Z0, i
     Run run;
     run.profile = o->profile != 0;
     run.launches = 6;
+    // bulk-copy gathers (depth 0): FP32 rows of k values, a multiple of 16 bytes
+    const bool bulk = sizeof(T) == 4 && b.depth == 0 && k % 4 == 0 && k >= 4 && k <= 64;
+    const size_t bulk_smem = (size_t)8 * 2 * kBulkRows * (size_t)k * sizeof(float);
+    int64_t sms = 152;
+    if (bulk) {
+        int dev = 0, nsm = 0;
+        FJ_CUDA(cudaGetDevice(&dev));
+        FJ_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        sms = std::max(1, nsm);
+        FJ_CUDA(cudaFuncSetAttribute(k_sweep_batch_bulk<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)bulk_smem));
+        FJ_CUDA(cudaFuncSetAttribute(k_sweep_batch_bulk<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)bulk_smem));
+    }
     int64_t sweep = 0;
     const int check = o->check_every > 0 ? o->check_every : 8;
     int refine = 0, cleanups = 0;
@@ -2291,6 +2558,22 @@ static fj_status solve_batch_t(fj_graph *g, const double *S, const double *Z0, i
     k_sweep_batch<T, WW, DD><<<grid, 256, 0, st>>>(wp.items, i0, ni, c.row_ptr, c.col, c.w, k, dcur, dprev, r, h, \
                                                    inv, zacc, om, c.indeg, wp.slot_first, wp.slot_nchunk, b.partk, \
                                                    wp.cnt, ws.ctr, tk, c.n)
+                    if constexpr (sizeof(T) == 4) {
+                        if (bulk) {
+                            const unsigned bgrid = (unsigned)std::min<int64_t>(ceil_div(ni, 8), 3 * sms);
+                            if (c.w)
+                                k_sweep_batch_bulk<true><<<bgrid, 256, bulk_smem, st>>>(
+                                    wp.items, i0, ni, c.row_ptr, c.col, c.w, k, dcur, dprev, r, h, inv, zacc, om,
+                                    c.indeg, wp.slot_first, wp.slot_nchunk, b.partk, wp.cnt, ws.ctr, tk, g->err, c.n);
+                            else
+                                k_sweep_batch_bulk<false><<<bgrid, 256, bulk_smem, st>>>(
+                                    wp.items, i0, ni, c.row_ptr, c.col, c.w, k, dcur, dprev, r, h, inv, zacc, om,
+                                    c.indeg, wp.slot_first, wp.slot_nchunk, b.partk, wp.cnt, ws.ctr, tk, g->err, c.n);
+                            FJ_CUDA(cudaGetLastError());
+                            FJ_CHECK(run.after(st));
+                            continue;
+                        }
+                    }
                     if (c.w) {
                         if (b.depth == 4) FJ_SWEEP_BATCH(true, 4);
                         else FJ_SWEEP_BATCH(true, 8);
@@ -2313,6 +2596,7 @@ static fj_status solve_batch_t(fj_graph *g, const double *S, const double *Z0, i
             FJ_CUDA(cudaStreamSynchronize(st));
             FJ_CHECK(run.harvest());
             FJ_CHECK(check_index_record());
+            if (bulk) FJ_CHECK(read_dev_error(g, st));
             if (ws.ctr_host->done) break;
         }
         const int done = ws.ctr_host->done;
@@ -2421,7 +2705,7 @@ std::vector<TuneCand> tune_candidates(bool batch)
     c.push_back({FJ_SCHED_JACOBI, 0, 4, 1.0});
     for (int K : {4, 8, 16, 32})
         for (double w : {1.2, 1.5, 1.6, 1.7, 1.8})
-            for (int d : {4, 8}) {
+            for (int d : {0, 4, 8}) {
                 if (!batch && d != 4) continue;
                 c.push_back({FJ_SCHED_MULTICOLOUR, K, d, w});
             }
