@@ -35,6 +35,10 @@ WORKLOADS = {
     "rmat24_und": dict(gen="rmat_und", scale=24, precision="fp32", omega=1.8),
     "rmat16_dir": dict(gen="rmat_dir", scale=16, precision="fp32", omega=1.6),
     "rmat20_dir": dict(gen="rmat_dir", scale=20, precision="fp32", omega=1.6),
+    # the paper's other two opinion laws on the same graph: exponential (x_min = 1) and
+    # power law (alpha = 2.5, x_min = 1), each normalised by its maximum (kinds 4 and 5)
+    "rmat22_dir_exp": dict(gen="rmat_dir", scale=22, precision="fp32", omega=1.6, palette=8, opinions=4),
+    "rmat22_dir_pareto": dict(gen="rmat_dir", scale=22, precision="fp32", omega=1.6, palette=8, opinions=5),
     # 64 opinion vectors (U[0,1], Beta(1/2,1/2), +-1 labels) as one multi-right-hand-side push
     "rmat22_und_k64": dict(gen="rmat_und_multi", scale=22, nvec=64, precision="fp32", omega=1.7, cpu_scale=19),
     "rmat16_und_k64": dict(gen="rmat_und_multi", scale=16, nvec=64, precision="fp32", omega=1.7),
@@ -60,7 +64,7 @@ def make_workload(name, scale_override=None):
         g = W.rmat_directed(spec["scale"], nvec=spec["nvec"])
         src, dst, w = g["src"], g["dst"], g["w"]
     elif spec["gen"] == "rmat_dir":
-        g = W.rmat_directed(spec["scale"])
+        g = W.rmat_directed(spec["scale"], kind=spec.get("opinions", W.OP_UNIFORM))
         src, dst, w = g["src"], g["dst"], g["w"]
     elif spec["gen"] == "rmat_und":
         g = W.rmat_undirected(spec["scale"])
@@ -229,6 +233,12 @@ def run_gpu(args):
     del g["S"]
     s_d = torch.from_numpy(s_host).to(dev)
     z_d = torch.empty_like(s_d)
+    omega_est = None
+    if args.omega_opt:
+        # Eq. 17 from a power-iteration estimate of rho((I + D)^{-1} A), outside the timed region
+        t0 = time.perf_counter()
+        mu, omega = G.omega_opt(args.omega_opt)
+        omega_est = {"mu": mu, "omega": omega, "iters": args.omega_opt, "s": time.perf_counter() - t0}
     opts = dict(eps=EPS, omega=omega, precision=prec, schedule=args.schedule)
     palette = args.palette if args.palette is not None else spec.get("palette")
     if palette is not None:
@@ -358,7 +368,7 @@ def run_gpu(args):
                        "vectors": k, "palette": palette,
                        "mode": ("batched (fj_solve_batch)" if k > 1 and cols is None else
                                 "plain (one fj_solve per vector)"), "tuned": tuned,
-                       "omega": omega, "eps": EPS,
+                       "omega": opts["omega"], "omega_eq17": omega_est, "eps": EPS,
                        "schedule": {0: "auto (multicolour)", 1: "jacobi", 2: "multicolour"}[opts["schedule"]],
                        "precision": "FP32 push, FP64 estimate and certificate" if prec == capi.FJ_PREC_FP32
                        else "FP64", "l2": "inputs larger than L2 (CSR %.2f GB)" % (
@@ -697,6 +707,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rmat22_dir", choices=sorted(WORKLOADS))
     ap.add_argument("--omega", type=float, default=None)
+    ap.add_argument("--omega-opt", type=int, default=0, metavar="ITERS",
+                    help="take omega from Eq. 17 with mu from ITERS power-iteration steps (fj_graph_omega_opt)")
     ap.add_argument("--schedule", type=int, default=2, help="1 Jacobi rounds, 2 multicolour")
     ap.add_argument("--check-every", type=int, default=0)
     ap.add_argument("--cpu-scale", type=int, default=None,

@@ -11,7 +11,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import OP_ARCSINE, OP_BETA_MIX, OP_SIGN, OP_UNIFORM, ba, loguniform_sizes, opinions, rmat, sbm, uniform_array
+from . import OP_ARCSINE, OP_BETA_MIX, OP_EXP, OP_PARETO, OP_SIGN, OP_UNIFORM, ba, loguniform_sizes, opinions, rmat, sbm, uniform_array
 
 BASE_SEED = 20250714
 
@@ -29,15 +29,18 @@ def ba_graph(n: int = 20000, m: int = 5, seed_off: int = 1, nvec: int = 1, kind:
                 fp32=False)
 
 
-def rmat_directed(scale: int = 22, edge_factor: int = 16, seed_off: int = 2, nvec: int = 1):
-    """Directed R-MAT (a=.57, b=c=.19), weights U(0.5,1.5) FP32, s ~ U[0,1] rounded to FP32.
+def rmat_directed(scale: int = 22, edge_factor: int = 16, seed_off: int = 2, nvec: int = 1,
+                  kind: int = OP_UNIFORM):
+    """Directed R-MAT (a=.57, b=c=.19), weights U(0.5,1.5) FP32, s of `kind`
+    (default U[0,1]; OP_EXP and OP_PARETO are the paper's exponential and
+    power-law opinions, normalised by their maximum) rounded to FP32.
 
     Arc (src, dst) means src listens to dst: row src of A holds dst.
     """
     seed = BASE_SEED + seed_off
     src, dst, w = rmat(scale, edge_factor, seed=seed, weighted=True)
     n = 1 << scale
-    S = [_f32(opinions(n, OP_UNIFORM, seed + 1000, vec=k)) for k in range(nvec)]
+    S = [_f32(opinions(n, kind, seed + 1000, vec=k)) for k in range(nvec)]
     return dict(name=f"rmat{scale}_dir_w", n=n, src=src, dst=dst, w=w, directed=True, S=S,
                 fp32=True)
 

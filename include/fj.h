@@ -256,14 +256,32 @@ fj_status fj_solve_batch(fj_graph *g, const double *S, int k, const fj_solve_opt
                          double *Z_out, fj_solve_info *info, int mem);
 
 /*
+ * fj_graph_omega_opt - the SOR factor of Section 5.2's optimal-omega equation
+ * (Eq. 17),  omega_opt = 1 + (mu / (1 + sqrt(1 - mu^2)))^2,  with
+ * mu = rho((I + D)^{-1} A), the spectral radius of the Jacobi iteration matrix
+ * of (I + L) z = s (D the weighted out-degrees).  mu is estimated by `iters`
+ * steps of power iteration on B = (I + M) / 2, M = (I + D)^{-1} A, from the
+ * all-ones vector; B's dominant eigenvalue (1 + mu) / 2 is strictly largest
+ * in modulus even when -mu is an eigenvalue of M (bipartite graphs), so the
+ * iteration converges there too.  Each step is one FP64 SpMV in a fixed
+ * summation order (deterministic).  Eq. 17 is exact for consistently ordered
+ * matrices (bipartite graphs in red-black order, Theorem 2 of the SOR
+ * literature the paper cites); for other graphs it is the standard estimate.
+ * mu_out and omega_out are host pointers, either may be NULL; stream may be
+ * NULL.  FJ_ERR_INVALID_ARG for iters outside 1..100000 or an empty graph.
+ * fj_graph_tune adds omega_opt (200 steps) to its candidates.
+ */
+fj_status fj_graph_omega_opt(fj_graph *g, int iters, double *mu_out, double *omega_out, void *stream);
+
+/*
  * fj_graph_tune - autotuner for fj_solve on this graph.  Times complete,
  * certified solves of s (reps timed calls after one untimed call each, CUDA
  * events on base->stream) for every candidate: Jacobi rounds at omega 1, and
  * the multicolour schedule for palette K in {4, 8, 16, 32} x omega in {1.2,
- * 1.5, 1.6, 1.7, 1.8}.  *best receives base with the schedule, palette and
- * omega of the fastest (its colouring is left built on the handle); *best_ms
- * (may be NULL) its mean time.  Costs one colouring per palette and
- * 21 (reps + 1) solves.
+ * 1.5, 1.6, 1.7, 1.8, omega_opt of fj_graph_omega_opt}.  *best receives base
+ * with the schedule, palette and omega of the fastest (its colouring is left
+ * built on the handle); *best_ms (may be NULL) its mean time.  Costs 200
+ * power-iteration steps, one colouring per palette and 25 (reps + 1) solves.
  * FJ_ERR_NOT_CONVERGED when no candidate certifies.
  */
 fj_status fj_graph_tune(fj_graph *g, const double *s, const fj_solve_opts *base, int reps,

@@ -449,3 +449,32 @@ def safe_omega(omega, d64, din):
     M + M^T - (I + L) diagonally dominant (Gershgorin) on undirected graphs."""
     bound = 0.98 * 2.0 * (1.0 + d64) / (1.0 + d64 + din)
     return np.where(din > 0, np.minimum(omega, bound), omega)
+
+
+def jacobi_radius_power(n, row_ptr, col, w, iters: int) -> float:
+    """mu = rho((I + D)^{-1} A), the spectral radius of the Jacobi iteration
+    matrix M of (I + L) z = s (Section 5.2, the quantity of Eq. 17), by `iters`
+    steps of power iteration on B = (I + M) / 2 from the all-ones vector.
+    B's dominant eigenvalue is (1 + mu) / 2, strictly largest in modulus even
+    when M has -mu in its spectrum (bipartite graphs), so the estimate
+    2 nu - 1, nu = sum(B x) / sum(x), converges to mu.  x is rescaled to sum n
+    after every step.  Plain FP64."""
+    row_ptr = np.asarray(row_ptr, np.int64)
+    col = np.asarray(col, np.int64)
+    a = np.ones(col.shape[0]) if w is None else np.asarray(w, np.float64)
+    rows = np.repeat(np.arange(n), np.diff(row_ptr))
+    d = np.bincount(rows, weights=a, minlength=n)
+    inv = 1.0 / (1.0 + d)
+    x = np.ones(n)
+    nu = 0.0
+    for _ in range(iters):
+        ax = np.bincount(rows, weights=a * x[col], minlength=n)
+        y = 0.5 * (x + inv * ax)
+        nu = y.sum() / x.sum()
+        x = y * (n / y.sum())
+    return 2.0 * nu - 1.0
+
+
+def omega_opt(mu: float) -> float:
+    """The optimal SOR factor of Eq. 17: 1 + (mu / (1 + sqrt(1 - mu^2)))^2."""
+    return 1.0 + (mu / (1.0 + np.sqrt(1.0 - mu * mu))) ** 2

@@ -26,7 +26,7 @@ EXPORTED = [
     "fj_graph_create_from_arcs", "fj_graph_create_ragged", "fj_graph_destroy", "fj_graph_info",
     "fj_graph_export", "fj_graph_colour", "fj_solve", "fj_solve_warm", "fj_solve_batch",
     "fj_metrics", "fj_metrics_batch", "fj_frontier", "fj_frontier_static", "fj_residual",
-    "fj_graph_tune", "fj_graph_tune_batch", "fj_mpnn_param_count", "fj_mpnn_create", "fj_mpnn_destroy", "fj_mpnn_get_params", "fj_mpnn_set_params",
+    "fj_graph_tune", "fj_graph_tune_batch", "fj_graph_omega_opt", "fj_mpnn_param_count", "fj_mpnn_create", "fj_mpnn_destroy", "fj_mpnn_get_params", "fj_mpnn_set_params",
     "fj_mpnn_predict", "fj_mpnn_grad", "fj_mpnn_adam_step",
 ]
 
@@ -97,6 +97,7 @@ def lib():
     L.fj_graph_tune_batch.argtypes = [VP, VP, I32, ctypes.POINTER(fj_solve_opts), I32,
                                       ctypes.POINTER(fj_solve_opts), ctypes.POINTER(D), I32]
     L.fj_metrics_batch.argtypes = [VP, VP, VP, I32, VP, I32, VP]
+    L.fj_graph_omega_opt.argtypes = [VP, I32, ctypes.POINTER(D), ctypes.POINTER(D), VP]
     L.fj_frontier.argtypes = [I64, VP, VP, I32, VP, VP, VP]
     L.fj_frontier_static.argtypes = [I64, VP, VP, I32, VP, VP, VP]
     L.fj_residual.argtypes = [VP, VP, VP, D, VP, I32, VP]
@@ -354,6 +355,14 @@ class Graph:
         _check(lib().fj_graph_tune(self._h, _ptr(s, np.float64), ctypes.byref(base), int(reps), ctypes.byref(best),
                                    ctypes.byref(ms), _mem_of(s)), "fj_graph_tune")
         return {"schedule": best.schedule, "palette": best.palette, "omega": best.omega}, ms.value
+
+    def omega_opt(self, iters=200):
+        """fj_graph_omega_opt: (mu, omega_opt) of Eq. 17, mu by `iters` power-iteration steps."""
+        mu = ctypes.c_double()
+        om = ctypes.c_double()
+        _check(lib().fj_graph_omega_opt(self._h, int(iters), ctypes.byref(mu), ctypes.byref(om), None),
+               "fj_graph_omega_opt")
+        return mu.value, om.value
 
     def tune_batch(self, S, reps=1, **opts):
         """fj_graph_tune_batch; the chosen gather depth stays on the handle."""

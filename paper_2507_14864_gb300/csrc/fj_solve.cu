@@ -2691,20 +2691,203 @@ extern "C" fj_status fj_solve_batch(fj_graph *g, const double *S, int k, const f
 
 // ============================================================== autotuner
 
+// ============================================================== optimal omega (Eq. 17)
+
+// y = (x + (I + D)^{-1} A x) / 2 over the warp-tile items of the caller-order
+// CSR: a row of at most 32 nonzeros is summed by one lane, a longer row of a
+// tile by the whole warp, a chunk of a long row by the warp with the chunks'
+// sums added in chunk order by the last one to finish.  FP64, fixed order.
+template <bool W>
+__global__ void __launch_bounds__(256)
+k_jacobi_half(const Item *__restrict__ items, int64_t nitems, const int64_t *__restrict__ rp,
+              const int32_t *__restrict__ col, const float *__restrict__ w, const double *__restrict__ inv64,
+              const double *__restrict__ x, double *__restrict__ y, const int32_t *__restrict__ slot_first,
+              const int32_t *__restrict__ slot_nchunk, double *part, int32_t *cnt, int64_t n_rows)
+{
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    auto terms = [&](int64_t a, int64_t e, int64_t step) -> double {
+        double acc = 0.0;
+        for (int64_t k = a; k < e; k += step) {
+            const int32_t c = __ldg(col + k);
+            if (!FJ_IDX_OK(4, c, n_rows)) continue;
+            acc = fma(W ? (double)__ldg(w + k) : 1.0, x[c], acc);
+        }
+        return acc;
+    };
+    auto finish = [&](int64_t v, double ax) { y[v] = 0.5 * (x[v] + inv64[v] * ax); };
+    for (int64_t ii = warp; ii < nitems; ii += nwarps) {
+        const Item it = items[ii];
+        const int64_t r0 = it.r0, r1 = it.r1;
+        if (!FJ_IDX_OK(1, r0, n_rows) || !FJ_IDX_OK(2, r1, n_rows + 1) ||
+            (it.slot < 0 && !FJ_IDX_OK(3, r1 - r0, kWarpRows + 1)))
+            continue;
+        if (it.slot < 0) {
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                const int64_t v = r0 + lane + 32 * half;
+                const bool mine = v < r1;
+                int64_t a = 0, e = 0;
+                if (mine) {
+                    a = rp[v];
+                    e = rp[v + 1];
+                }
+                const bool shrt = e - a <= 32;
+                if (mine && shrt) finish(v, terms(a, e, 1));
+                unsigned longs = __ballot_sync(FULL, mine && !shrt);
+                while (longs) {
+                    const int src = __ffs(longs) - 1;
+                    longs &= longs - 1;
+                    const int64_t al = __shfl_sync(FULL, a, src), el = __shfl_sync(FULL, e, src);
+                    const double s = warp_sum(terms(al + lane, el, 32));
+                    if (lane == src) finish(v, s);
+                }
+            }
+        } else {
+            const double s = warp_sum(terms(it.k0 + lane, it.k1, 32));
+            const int slot = it.slot;
+            const int first = slot_first[slot], nch = slot_nchunk[slot];
+            int last = 0;
+            if (lane == 0) {
+                const int ci = (int)((it.k0 - rp[r0]) / kWarpChunk);
+                part[2 * (first + ci)] = s;
+                __threadfence();
+                last = atomicAdd(&cnt[slot], 1) == nch - 1;
+            }
+            last = __shfl_sync(FULL, last, 0);
+            if (last && lane == 0) {
+                __threadfence();
+                double t = 0.0;
+                for (int c = 0; c < nch; ++c) t += __ldcg(part + 2 * (first + c));
+                cnt[slot] = 0;
+                finish(r0, t);
+            }
+        }
+    }
+}
+
+// Per-block sums of y (fixed tree), then one block adds them in block order.
+__global__ void __launch_bounds__(256) k_block_sum(int64_t n, const double *__restrict__ y, double *__restrict__ part)
+{
+    __shared__ double sm[8];
+    double v = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v += y[i];
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < 8; ++i) t += sm[i];
+        part[blockIdx.x] = t;
+    }
+}
+
+// sums[it] = sum of y; x = y * n / sum (x keeps the sum n)
+__global__ void __launch_bounds__(256)
+k_rescale(int64_t n, int nb, const double *__restrict__ part, const double *__restrict__ y, double *__restrict__ x,
+          double *__restrict__ sums, int it)
+{
+    __shared__ double tot;
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int b = 0; b < nb; ++b) t += part[b];
+        tot = t;
+        if (blockIdx.x == 0) sums[it] = t;
+    }
+    __syncthreads();
+    const double f = tot > 0.0 ? (double)n / tot : 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = y[i] * f;
+}
+
+__global__ void k_fill(int64_t n, double *__restrict__ x, double v)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = v;
+}
+
+namespace fj {
+// mu = rho((I + D)^{-1} A) by power iteration on (I + M) / 2 (see the header).
+fj_status jacobi_radius(fj_graph *g, int iters, cudaStream_t st, double *mu)
+{
+    const ItemPlan *ip = nullptr;
+    FJ_CHECK(plain_items(g, st, &ip));
+    const DevCSR &c = g->csr;
+    const int64_t n = c.n;
+    constexpr int kNb = 152 * 4;
+    double *x = nullptr, *y = nullptr, *part = nullptr, *sums = nullptr;
+    fj_status s = FJ_OK;
+    cudaError_t e = cudaMalloc(&x, sizeof(double) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&y, sizeof(double) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&part, sizeof(double) * kNb);
+    if (e == cudaSuccess) e = cudaMalloc(&sums, sizeof(double) * iters);
+    if (e == cudaSuccess) {
+        const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ip->nitems, 8), 152 * 8));
+        k_fill<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(n, x, 1.0);
+        for (int it = 0; it < iters && e == cudaSuccess; ++it) {
+            if (c.w)
+                k_jacobi_half<true><<<grid, 256, 0, st>>>(ip->items, ip->nitems, c.row_ptr, c.col, c.w, c.inv64, x,
+                                                          y, ip->slot_first, ip->slot_nchunk, ip->part, ip->cnt, n);
+            else
+                k_jacobi_half<false><<<grid, 256, 0, st>>>(ip->items, ip->nitems, c.row_ptr, c.col, c.w, c.inv64, x,
+                                                           y, ip->slot_first, ip->slot_nchunk, ip->part, ip->cnt, n);
+            k_block_sum<<<kNb, 256, 0, st>>>(n, y, part);
+            k_rescale<<<kNb, 256, 0, st>>>(n, kNb, part, y, x, sums, it);
+            e = cudaGetLastError();
+        }
+    }
+    double last = 0.0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&last, sums + (iters - 1), sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) s = cuda_fail(e, "omega_opt", __FILE__, __LINE__);
+    dev_free(x);
+    dev_free(y);
+    dev_free(part);
+    dev_free(sums);
+    FJ_CHECK(s);
+    FJ_CHECK(check_index_record());
+    // the iterate entering the last step had sum n, so nu = sum(y) / n
+    *mu = 2.0 * last / (double)n - 1.0;
+    return FJ_OK;
+}
+}  // namespace fj
+
+extern "C" fj_status fj_graph_omega_opt(fj_graph *g, int iters, double *mu_out, double *omega_out, void *stream)
+{
+    FJ_ARG(g, "NULL graph");
+    FJ_ARG(iters >= 1 && iters <= 100000, "iters must be in 1..100000");
+    FJ_ARG(g->csr.n > 0, "empty graph");
+    double mu = 0.0;
+    FJ_CHECK(fj::jacobi_radius(g, iters, (cudaStream_t)stream, &mu));
+    mu = std::min(std::max(mu, 0.0), 1.0);
+    const double r = mu / (1.0 + std::sqrt(1.0 - mu * mu));
+    if (mu_out) *mu_out = mu;
+    if (omega_out) *omega_out = 1.0 + r * r;
+    return FJ_OK;
+}
+
 namespace {
+
+constexpr int kTuneOmegaIters = 200;  // power-iteration steps behind the tuner's Eq. 17 candidate
 
 struct TuneCand {
     int schedule, palette, depth;
     double omega;
 };
 
-// Candidates in palette order, so each colouring is built once.
-std::vector<TuneCand> tune_candidates(bool batch)
+// Candidates in palette order, so each colouring is built once.  wopt > 0
+// adds the omega of Eq. 17 (fj_graph_omega_opt) to the fixed grid.
+std::vector<TuneCand> tune_candidates(bool batch, double wopt)
 {
     std::vector<TuneCand> c;
     c.push_back({FJ_SCHED_JACOBI, 0, 4, 1.0});
+    std::vector<double> ws = {1.2, 1.5, 1.6, 1.7, 1.8};
+    if (wopt > 1.0 && wopt < 2.0) ws.push_back(wopt);
     for (int K : {4, 8, 16, 32})
-        for (double w : {1.2, 1.5, 1.6, 1.7, 1.8})
+        for (double w : ws)
             for (int d : {0, 4, 8}) {
                 if (!batch && d != 4) continue;
                 c.push_back({FJ_SCHED_MULTICOLOUR, K, d, w});
@@ -2758,7 +2941,9 @@ extern "C" fj_status fj_graph_tune(fj_graph *g, const double *s, const fj_solve_
     double best_t = -1.0;
     fj_solve_opts bo = *base;
     fj_status result = FJ_OK;
-    for (const TuneCand &cd : tune_candidates(false)) {
+    double wopt = 0.0;
+    FJ_CHECK(fj_graph_omega_opt(g, kTuneOmegaIters, nullptr, &wopt, base->stream));
+    for (const TuneCand &cd : tune_candidates(false, wopt)) {
         fj_solve_opts o = *base;
         o.schedule = cd.schedule;
         o.palette = cd.schedule == FJ_SCHED_JACOBI ? base->palette : cd.palette;
@@ -2803,7 +2988,9 @@ extern "C" fj_status fj_graph_tune_batch(fj_graph *g, const double *S, int k, co
     fj_solve_opts bo = *base;
     int best_depth = g->bws.depth;
     fj_status result = FJ_OK;
-    for (const TuneCand &cd : tune_candidates(true)) {
+    double wopt = 0.0;
+    FJ_CHECK(fj_graph_omega_opt(g, kTuneOmegaIters, nullptr, &wopt, base->stream));
+    for (const TuneCand &cd : tune_candidates(true, wopt)) {
         fj_solve_opts o = *base;
         o.schedule = cd.schedule;
         o.palette = cd.schedule == FJ_SCHED_JACOBI ? base->palette : cd.palette;

@@ -132,6 +132,25 @@ def test_fp64_ba20k(capi, ba20k, omega, schedule):
         assert abs(m[k] - mo_true[k]) <= METRIC_TOL * abs(mo_true[k])
 
 
+@pytest.mark.parametrize("kind", ["exp", "pareto"])
+def test_fp32_rmat_directed_heavy_tailed_opinions(capi, kind):
+    """The paper's exponential and power-law (alpha = 2.5) opinion laws, each
+    normalised by its maximum: most s_v are small, so the thresholds eps' s'_v
+    are too; the certificate and the truth agree all the same."""
+    g = W.rmat_directed(13, kind=W.OP_EXP if kind == "exp" else W.OP_PARETO)
+    rp, col, w = csr_of(g)
+    n, s = g["n"], g["S"][0]
+    G = capi.Graph.from_csr(n, *to_dev(rp, col, w), directed=True)
+    (s_d,) = to_dev(s)
+    z_d, info, st = G.solve(s_d, eps=1e-6, omega=1.6, palette=8, precision=capi.FJ_PREC_FP32)
+    z = z_d.cpu().numpy()
+    assert st == capi.FJ_OK and info[0]["converged"] == 1
+    ok, _ = certificate_holds(n, rp, col, w, s, z, info[0]["c_eff"], info[0]["eps_prime"])
+    assert ok
+    z_star, _ = oracle.truth(n, rp, col, w, s)
+    assert rel_inf(z, z_star) <= FP32_TOL
+
+
 @pytest.mark.parametrize("omega", [1.0, 1.2, 1.5])
 def test_fp32_rmat_directed(capi, omega):
     g = W.rmat_directed(14)
@@ -359,3 +378,28 @@ def test_ragged_from_arcs_matches_separate_handles(capi):
         for k in ("P", "D", "I", "C"):
             assert abs(mets[i][k] - mo[k]) <= METRIC_TOL * abs(mo[k])
         off += n
+
+
+@pytest.mark.parametrize("name", ["ba2k", "rmat12_dir", "rmat12_und", "path"])
+def test_omega_opt_matches_oracle_power_iteration(capi, name):
+    """fj_graph_omega_opt: mu after the same number of power-iteration steps as
+    the oracle's (FP64, different summation order), and Eq. 17 from it."""
+    if name == "ba2k":
+        g = W.ba_graph(2000, 5, seed_off=51)
+        directed = False
+    elif name == "path":
+        n = 300
+        src = np.arange(n - 1, dtype=np.int32)
+        g = {"n": n, "src": src, "dst": src + 1, "w": None, "directed": False}
+        directed = False
+    else:
+        g = W.rmat_directed(12) if name.endswith("dir") else W.rmat_undirected(12)
+        directed = name.endswith("dir")
+    rp, col, w = csr_of(g)
+    n = g["n"]
+    G = capi.Graph.from_csr(n, *to_dev(rp, col, w), directed=directed)
+    for iters in (1, 7, 300):
+        mu, om = G.omega_opt(iters)
+        mu_o = oracle.jacobi_radius_power(n, rp, col, w, iters)
+        assert abs(mu - mu_o) <= 1e-11, (iters, mu, mu_o)
+        assert abs(om - oracle.omega_opt(min(max(mu_o, 0.0), 1.0))) <= 1e-9

@@ -522,3 +522,52 @@ def test_safe_omega_keeps_split_diagonally_dominant():
     om = oracle.safe_omega(1.8, d, din)
     assert om[0] == 1.8 and om[3] == 1.8
     assert np.all((2 / om - 1) * (1 + d) >= din - 1e-12)
+
+
+# ------------------------------------------------------------ spectral radius for Eq. 17
+
+def test_jacobi_radius_complete_graph_closed_form():
+    # K_m, unit weights: M = (J - I) / m, whose spectral radius is (m - 1) / m
+    m = 9
+    rp, col, w = undirected(m, [(i, j) for i in range(m) for j in range(i + 1, m)])
+    assert abs(oracle.jacobi_radius_power(m, rp, col, w, 5) - (m - 1) / m) < 1e-14
+
+
+@pytest.mark.parametrize("directed", [False, True])
+def test_jacobi_radius_matches_dense_eigenvalues(directed):
+    rng = np.random.default_rng(21 if directed else 22)
+    n = 60
+    arcs = {(int(u), int(v)) for u, v in rng.integers(0, n, (400, 2)) if u != v}
+    if not directed:
+        arcs |= {(v, u) for u, v in arcs}
+    arcs = sorted(arcs)
+    src = np.array([a for a, _ in arcs], np.int32)
+    dst = np.array([b for _, b in arcs], np.int32)
+    wt = (0.5 + rng.random(len(arcs))).astype(np.float32)
+    if not directed:
+        wt = np.array([wt[min(i, arcs.index((b, a)))] for i, (a, b) in enumerate(arcs)], np.float32)
+    rp, col, w = oracle.csr_from_arcs(n, src, dst, wt)
+    dense = oracle.dense_i_plus_l(n, rp, col, w)
+    dg = np.diag(dense)
+    m = (np.diag(dg) - dense) / dg[:, None]  # (I + D)^{-1} A
+    mu = max(abs(np.linalg.eigvals(m)))
+    assert abs(oracle.jacobi_radius_power(n, rp, col, w, 3000) - mu) < 1e-9
+
+
+def test_jacobi_radius_bipartite_path():
+    # a path is bipartite, so M's spectrum is symmetric (+-mu) and plain power
+    # iteration on M would alternate; the shifted iteration converges to mu
+    n = 12
+    rp, col, w = undirected(n, [(i, i + 1) for i in range(n - 1)])
+    dense = oracle.dense_i_plus_l(n, rp, col, w)
+    dg = np.diag(dense)
+    ev = np.linalg.eigvals((np.diag(dg) - dense) / dg[:, None])
+    mu = max(abs(ev))
+    assert np.min(np.abs(ev + mu)) < 1e-12  # -mu is an eigenvalue too
+    assert abs(oracle.jacobi_radius_power(n, rp, col, w, 4000) - mu) < 1e-10
+
+
+def test_omega_opt_is_youngs_formula():
+    # Eq. 17 written as 1 + (mu / (1 + sqrt(1 - mu^2)))^2 equals 2 / (1 + sqrt(1 - mu^2))
+    for mu in (0.0, 0.3, 2.0 / 3.0, 0.9, 0.999):
+        assert abs(oracle.omega_opt(mu) - 2.0 / (1.0 + np.sqrt(1.0 - mu * mu))) < 1e-15
