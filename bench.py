@@ -347,6 +347,10 @@ def run_gpu(args):
               "refine_passes": info0["refine_passes"], "resid_rel_max": info0["resid_rel_max"],
               "eps_prime": info0["eps_prime"], "gteps": info0["edges"] / (ms_per_step / 1e3) / 1e9,
               "ncolours": G.info()["ncolours"], "vectors_per_step": k}
+    if args.trace and k == 1:
+        # relative residual against time for one more solve, outside the timed region (Fig. 1's axes)
+        _, _, _, tr = G.solve_trace(s_d, out=z_d, **opts)
+        detail["trace"] = [[round(float(a), 4), int(b), float(c), int(d)] for a, b, c, d in tr]
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -709,6 +713,8 @@ def main():
     ap.add_argument("--omega", type=float, default=None)
     ap.add_argument("--omega-opt", type=int, default=0, metavar="ITERS",
                     help="take omega from Eq. 17 with mu from ITERS power-iteration steps (fj_graph_omega_opt)")
+    ap.add_argument("--trace", action="store_true",
+                    help="add one traced solve's [ms, sweeps, max|r|/s', kind] rows to detail (fj_solve_trace)")
     ap.add_argument("--schedule", type=int, default=2, help="1 Jacobi rounds, 2 multicolour")
     ap.add_argument("--check-every", type=int, default=0)
     ap.add_argument("--cpu-scale", type=int, default=None,

@@ -256,6 +256,25 @@ fj_status fj_solve_batch(fj_graph *g, const double *S, int k, const fj_solve_opt
                          double *Z_out, fj_solve_info *info, int mem);
 
 /*
+ * fj_solve_trace - fj_solve that also records how the push converges, for
+ * relative-error-versus-time curves (the shape of the paper's Fig. 1).  After
+ * every batch of sweeps between stop checks (opts->check_every, 8 by default)
+ * and after every certificate it appends one row of 4 doubles to trace:
+ *     [ms since the solve's first sweep, sweeps so far, rel, kind]
+ * with rel = max_v |r_v| / s'_v of r = s' - (I + L) zhat, kind 0 after a
+ * batch of sweeps (r evaluated afresh in FP64 from the current estimate; the
+ * time of that evaluation is left out of the rows' times) and kind 1 for the
+ * exact certificate.  By Lemma 5, |z - zhat| <= rel (z + c_eff) elementwise,
+ * so rel bounds the relative error.  trace is a host array of 4 * cap
+ * doubles; at most cap rows are written and *count receives their number.
+ * A kind-0 row costs one FP64 residual evaluation (one pass over the graph).
+ * On a divergence fallback (FJ_SCHED_AUTO) the trace restarts with the
+ * omega = 1 solve.  Otherwise as fj_solve.
+ */
+fj_status fj_solve_trace(fj_graph *g, const double *s, const fj_solve_opts *opts, double *z_out,
+                         fj_solve_info *info, int mem, double *trace, int cap, int *count);
+
+/*
  * fj_graph_omega_opt - the SOR factor of Section 5.2's optimal-omega equation
  * (Eq. 17),  omega_opt = 1 + (mu / (1 + sqrt(1 - mu^2)))^2,  with
  * mu = rho((I + D)^{-1} A), the spectral radius of the Jacobi iteration matrix

@@ -26,7 +26,7 @@ EXPORTED = [
     "fj_graph_create_from_arcs", "fj_graph_create_ragged", "fj_graph_destroy", "fj_graph_info",
     "fj_graph_export", "fj_graph_colour", "fj_solve", "fj_solve_warm", "fj_solve_batch",
     "fj_metrics", "fj_metrics_batch", "fj_frontier", "fj_frontier_static", "fj_residual",
-    "fj_graph_tune", "fj_graph_tune_batch", "fj_graph_omega_opt", "fj_mpnn_param_count", "fj_mpnn_create", "fj_mpnn_destroy", "fj_mpnn_get_params", "fj_mpnn_set_params",
+    "fj_graph_tune", "fj_graph_tune_batch", "fj_graph_omega_opt", "fj_solve_trace", "fj_mpnn_param_count", "fj_mpnn_create", "fj_mpnn_destroy", "fj_mpnn_get_params", "fj_mpnn_set_params",
     "fj_mpnn_predict", "fj_mpnn_grad", "fj_mpnn_adam_step",
 ]
 
@@ -98,6 +98,8 @@ def lib():
                                       ctypes.POINTER(fj_solve_opts), ctypes.POINTER(D), I32]
     L.fj_metrics_batch.argtypes = [VP, VP, VP, I32, VP, I32, VP]
     L.fj_graph_omega_opt.argtypes = [VP, I32, ctypes.POINTER(D), ctypes.POINTER(D), VP]
+    L.fj_solve_trace.argtypes = [VP, VP, ctypes.POINTER(fj_solve_opts), VP, VP, I32, VP, I32,
+                                 ctypes.POINTER(I32)]
     L.fj_frontier.argtypes = [I64, VP, VP, I32, VP, VP, VP]
     L.fj_frontier_static.argtypes = [I64, VP, VP, I32, VP, VP, VP]
     L.fj_residual.argtypes = [VP, VP, VP, D, VP, I32, VP]
@@ -318,6 +320,26 @@ class Graph:
         allow = (FJ_ERR_NOT_CONVERGED, FJ_ERR_DIVERGED) if allow_unconverged else ()
         _check(st, where, allow)
         return out, [i.as_dict() for i in infos], st
+
+    def solve_trace(self, s, out=None, cap=4096, **opts):
+        """fj_solve_trace.  Returns (z, [info per graph], status, trace) with trace an
+        array of rows [ms, sweeps, max |r| / s', kind (0 push residual, 1 certificate)]."""
+        o = default_opts(**opts)
+        ng = self.info()["ngraphs"]
+        infos = (fj_solve_info * ng)()
+        mem = _mem_of(s, out)
+        if out is None:
+            if mem == FJ_MEM_DEVICE:
+                import torch
+                out = torch.empty_like(s)
+            else:
+                out = np.empty_like(np.asarray(s, np.float64))
+        rows = np.zeros((int(cap), 4), np.float64)
+        count = ctypes.c_int()
+        st = lib().fj_solve_trace(self._h, _ptr(s, np.float64), ctypes.byref(o), _ptr(out, np.float64), infos, mem,
+                                  rows.ctypes.data_as(ctypes.c_void_p), int(cap), ctypes.byref(count))
+        _check(st, "fj_solve_trace")
+        return out, [i.as_dict() for i in infos], st, rows[:count.value].copy()
 
     def solve_batch(self, S, out=None, allow_unconverged=False, **opts):
         """fj_solve_batch on node-major S[n, k].  Returns (Z, [info per vector], status)."""

@@ -1424,9 +1424,44 @@ static fj_status frontier_cleanup(fj_graph *g, const Plan &p, int k, double *r64
     return read_dev_error(g, st);
 }
 
+// Convergence trace of a solve (fj_solve_trace): rows of
+// [ms since the first sweep, sweeps so far, max_v |r_v| / s'_v, kind].
+struct Trace {
+    double *rows = nullptr;
+    int cap = 0;
+    int count = 0;
+};
+
+// max_v |r_v| / s'_v of the residual r = s' - (I + L) zhat of the current
+// estimate, in FP64, one warp per row, into *out (ordered bits of a
+// non-negative double).  The push's own residual array lags: in the pull form
+// a row's stored residual leaves out the increments its neighbours made after
+// it in the sweep, so the trace evaluates the residual afresh.
+__global__ void k_trace_resid(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                              const float *__restrict__ w, const double *__restrict__ deg,
+                              const double *__restrict__ sp, const double *__restrict__ zhat, unsigned long long *out)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    double m = 0.0;
+    for (int64_t x = warp0; x < n; x += nwarps) {
+        double acc = 0.0;
+        for (int64_t k = rp[x] + lane; k < rp[x + 1]; k += 32) {
+            const int32_t c = col[k];
+            if (c >= 0 && c < n) acc = fma(w ? (double)w[k] : 1.0, zhat[c], acc);
+        }
+        acc = warp_sum(acc);
+        const double r = fma(-(1.0 + deg[x]), zhat[x], sp[x]) + acc;
+        const double rel = fabs(r) / sp[x];
+        m = rel > m ? rel : m;  // a NaN never wins
+    }
+    if (lane == 0) atomic_max_nonneg(reinterpret_cast<double *>(out), m);
+}
+
 template <typename T>
 static fj_status solve_t(fj_graph *g, const double *s, const double *z0, const fj_solve_opts *o, double *z_out,
-                         fj_solve_info *info, int mem)
+                         fj_solve_info *info, int mem, Trace *tr = nullptr)
 {
     cudaStream_t st = (cudaStream_t)o->stream;
     const int64_t n = g->csr.n;
@@ -1476,6 +1511,54 @@ static fj_status solve_t(fj_graph *g, const double *s, const double *z0, const f
     int refine = 0, cleanups = 0;
     int64_t f_rounds = 0, f_pushes = 0;
     fj_status result = FJ_OK;
+    cudaEvent_t tev[3] = {nullptr, nullptr, nullptr};
+    float excluded_ms = 0.f;  // time the trace's own evaluations took, left out of the rows' times
+    if (tr) {
+        tr->count = 0;
+        for (cudaEvent_t &e : tev) FJ_CUDA(cudaEventCreate(&e));
+        FJ_CUDA(cudaEventRecord(tev[0], st));
+    }
+    // one trace row at this point of the stream (the stream is idle: every
+    // caller has just synchronised); rel < 0 asks for the push residual
+    auto trace_row = [&](double rel, double kind) -> fj_status {
+        if (!tr || tr->count >= tr->cap) return FJ_OK;
+        if (rel < 0.0) {
+            FJ_CUDA(cudaEventRecord(tev[1], st));  // the sweeps end here; the evaluation is not timed
+            FJ_CUDA(cudaMemsetAsync(ws.zmax, 0, sizeof(unsigned long long), st));
+            k_trace_resid<<<152 * 16, 256, 0, st>>>(n, c.row_ptr, c.col, c.w, c.deg64, ws.sp, ws.zhat, ws.zmax);
+            FJ_CUDA(cudaGetLastError());
+            unsigned long long bits = 0;
+            FJ_CUDA(cudaMemcpyAsync(&bits, ws.zmax, sizeof(bits), cudaMemcpyDeviceToHost, st));
+            FJ_CUDA(cudaEventRecord(tev[2], st));
+            FJ_CUDA(cudaStreamSynchronize(st));
+            double d;
+            std::memcpy(&d, &bits, sizeof(d));
+            rel = d;
+        } else {
+            FJ_CUDA(cudaEventRecord(tev[1], st));
+            FJ_CUDA(cudaEventRecord(tev[2], st));
+            FJ_CUDA(cudaStreamSynchronize(st));
+        }
+        float ms = 0.f, ev_ms = 0.f;
+        FJ_CUDA(cudaEventElapsedTime(&ms, tev[0], tev[1]));
+        FJ_CUDA(cudaEventElapsedTime(&ev_ms, tev[1], tev[2]));
+        ms -= excluded_ms;
+        excluded_ms += ev_ms;
+        double *row = tr->rows + 4 * (int64_t)tr->count++;
+        row[0] = ms;
+        row[1] = (double)ws.ctr_host->sweeps;
+        row[2] = rel;
+        row[3] = kind;
+        return FJ_OK;
+    };
+    struct EvFree {
+        cudaEvent_t *e;
+        ~EvFree()
+        {
+            for (int i = 0; i < 3; ++i)
+                if (e[i]) cudaEventDestroy(e[i]);
+        }
+    } ev_free{tev};
     for (;;) {
         k_pass_reset<<<1, 1, 0, st>>>(ws.ctr, o->max_sweeps);
         FJ_CUDA(cudaGetLastError());
@@ -1492,6 +1575,7 @@ static fj_status solve_t(fj_graph *g, const double *s, const double *z0, const f
             FJ_CUDA(cudaStreamSynchronize(st));
             FJ_CHECK(run.harvest());
             FJ_CHECK(check_index_record());
+            FJ_CHECK(trace_row(-1.0, 0.0));
             if (ws.ctr_host->done) break;
         }
         const int done = ws.ctr_host->done;
@@ -1506,8 +1590,12 @@ static fj_status solve_t(fj_graph *g, const double *s, const double *z0, const f
             FJ_CUDA(cudaStreamSynchronize(st));
             FJ_CHECK(check_index_record());
             viol = 0.0;
-            for (int i = 0; i < ng; ++i) viol += ws.gstat_host[i * kGs + 5];
-            return FJ_OK;
+            double rel = 0.0;
+            for (int i = 0; i < ng; ++i) {
+                viol += ws.gstat_host[i * kGs + 5];
+                rel = std::max(rel, ws.gstat_host[i * kGs + 3]);
+            }
+            return trace_row(rel, 1.0);
         };
         double viol = 0.0;
         FJ_CHECK(certify_count(viol));
@@ -1607,6 +1695,25 @@ fj_status fj_solve(fj_graph *g, const double *s, const fj_solve_opts *opts, doub
         if (o->precision == FJ_PREC_FP32) return solve_t<float>(g, s, nullptr, o, z_out, info, mem);
         return solve_t<double>(g, s, nullptr, o, z_out, info, mem);
     });
+}
+
+fj_status fj_solve_trace(fj_graph *g, const double *s, const fj_solve_opts *opts, double *z_out, fj_solve_info *info,
+                         int mem, double *trace, int cap, int *count)
+{
+    FJ_ARG(g != nullptr, "graph is NULL");
+    FJ_ARG(s != nullptr && z_out != nullptr, "s or z_out is NULL");
+    FJ_ARG(trace != nullptr && count != nullptr && cap >= 1, "trace, count or cap");
+    FJ_ARG(mem == FJ_MEM_HOST || mem == FJ_MEM_DEVICE, "mem must be FJ_MEM_HOST or FJ_MEM_DEVICE");
+    FJ_CHECK(check_opts(opts));
+    Trace tr;
+    tr.rows = trace;
+    tr.cap = cap;
+    const fj_status st = with_omega_fallback(opts, [&](const fj_solve_opts *o) {
+        if (o->precision == FJ_PREC_FP32) return solve_t<float>(g, s, nullptr, o, z_out, info, mem, &tr);
+        return solve_t<double>(g, s, nullptr, o, z_out, info, mem, &tr);
+    });
+    *count = tr.count;
+    return st;
 }
 
 fj_status fj_solve_warm(fj_graph *g, const double *s, const double *z0, const fj_solve_opts *opts, double *z_out,

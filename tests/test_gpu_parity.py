@@ -403,3 +403,24 @@ def test_omega_opt_matches_oracle_power_iteration(capi, name):
         mu_o = oracle.jacobi_radius_power(n, rp, col, w, iters)
         assert abs(mu - mu_o) <= 1e-11, (iters, mu, mu_o)
         assert abs(om - oracle.omega_opt(min(max(mu_o, 0.0), 1.0))) <= 1e-9
+
+
+def test_solve_trace_records_convergence(capi):
+    """fj_solve_trace: the same z as fj_solve; rows with nondecreasing time and
+    sweeps; the last row is a certificate (kind 1) at or below eps'."""
+    g = W.rmat_directed(13)
+    rp, col, w = csr_of(g)
+    n, s = g["n"], g["S"][0]
+    G = capi.Graph.from_csr(n, *to_dev(rp, col, w), directed=True)
+    (s_d,) = to_dev(s)
+    opts = dict(eps=1e-6, omega=1.6, palette=8, precision=capi.FJ_PREC_FP32)
+    z_ref, info_ref, _ = G.solve(s_d, **opts)
+    z, info, st, tr = G.solve_trace(s_d, **opts)
+    assert st == capi.FJ_OK
+    assert np.array_equal(z.cpu().numpy(), z_ref.cpu().numpy())  # the trace changes nothing
+    assert tr.shape[0] >= 2 and tr.shape[1] == 4
+    assert np.all(np.diff(tr[:, 0]) >= 0) and np.all(np.diff(tr[:, 1]) >= 0)
+    assert tr[-1, 3] == 1.0 and tr[-1, 2] <= info[0]["eps_prime"]
+    assert tr[-1, 2] == pytest.approx(info[0]["resid_rel_max"], rel=1e-6)
+    push = tr[tr[:, 3] == 0.0]
+    assert push.shape[0] >= 1 and push[0, 2] > push[-1, 2]  # the push residual came down
