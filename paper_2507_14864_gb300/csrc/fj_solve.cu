@@ -1236,8 +1236,6 @@ static fj_status launch_sweep(fj_graph *g, const Plan &p, cudaStream_t st, Run &
     else inv = reinterpret_cast<const T *>(c.inv64);
     const T *om = reinterpret_cast<const T *>(ws.om);
     T *prod = reinterpret_cast<T *>(ws.prod);
-    const int32_t *lo_of = nullptr;
-    (void)lo_of;
     // segment by segment (a class cut into runs whose products stay in L2)
     for (size_t sg = 0; sg + 1 < wp.seg_item.size(); ++sg) {
         const int64_t i0 = wp.seg_item[sg], ni = wp.seg_item[sg + 1] - i0;
