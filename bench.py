@@ -121,6 +121,16 @@ def clocks_stop(p, path, device_index=0):
             "reasons": reasons, "samples": len(rows)}
 
 
+# DRAM bytes (read + write) of k_products + k_sweep per class launch, as a
+# multiple of the algorithmic bytes, from one ncu capture of a full sweep (8
+# class launches) of directed weighted R-MAT s20, FP32, omega 1.6:
+# 31.09 MB against 28.53 MB.  The scale-22 workload is larger than the
+# capture rules allow for a multi-pass metric, and the traffic of these
+# kernels grows with the nonzeros and rows they stream, so the bench scales
+# the ratio to its own launches (directed weighted FP32 single-vector solves).
+SWEEP_TRAFFIC_RATIO_DIR_W = 31.09 / 28.53
+
+
 def measured_peak_hbm():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -342,6 +352,11 @@ def run_gpu(args):
                               else "k_sweep_batch", k)), "peak_source": peak_kind,
                 "bytes_per_launch": p["push_bytes"] / max(1, p["push_launches"]),
                 "avg_launch_us": 1e3 * p["push_ms"] / max(1, p["push_launches"])}
+    if k == 1 and cols is None and g["directed"] and w is not None and prec == capi.FJ_PREC_FP32:
+        roofline["traffic"] = SWEEP_TRAFFIC_RATIO_DIR_W * roofline["bytes_per_launch"]
+        roofline["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of k_products + k_sweep "
+                                      "over one sweep of rmat20_dir (1.090 x its algorithmic bytes), scaled to "
+                                      "this launch's algorithmic bytes")
     info0 = infos[-1]
     detail = {"sweeps": info0["sweeps"], "pushes": info0["pushes"], "edges": info0["edges"],
               "refine_passes": info0["refine_passes"], "resid_rel_max": info0["resid_rel_max"],
