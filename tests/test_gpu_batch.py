@@ -173,3 +173,48 @@ def test_autotuner_picks_a_certified_configuration(capi):
     bb, bms = G.tune_batch(S, reps=1, eps=1e-6, precision=capi.FJ_PREC_FP32)
     Z, infos, st = G.solve_batch(S, eps=1e-6, precision=capi.FJ_PREC_FP32, **bb)
     assert st == capi.FJ_OK and all(i["converged"] == 1 for i in infos)
+
+
+def test_replicas_on_two_streams_match_single_stream(capi):
+    """Replicas: two handles solving disjoint sets of opinion vectors at the
+    same time, each on its own CUDA stream from its own host thread, give
+    bit for bit the results of the same solves run one after another."""
+    import threading
+
+    import torch
+
+    g = W.rmat_multirhs(12, 4)
+    rp, col, w = csr_of(g)
+    n = g["n"]
+    S = [np.ascontiguousarray(v) for v in g["S"]]
+    opts = dict(eps=1e-6, omega=1.5, precision=capi.FJ_PREC_FP32)
+    ref_h = capi.Graph.from_csr(n, *to_dev(rp, col, w), directed=False)
+    want = []
+    for v in S:
+        z, info, st = ref_h.solve(v, **opts)
+        assert st == capi.FJ_OK
+        want.append(np.array(z))
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    handles = []
+    for st_ in streams:
+        with torch.cuda.stream(st_):
+            handles.append(capi.Graph.from_csr(n, *to_dev(rp, col, w), directed=False, stream=st_.cuda_stream))
+    got = [None] * len(S)
+    errors = []
+
+    def replica(r):
+        try:
+            for j in range(r, len(S), 2):
+                z, info, st = handles[r].solve(S[j], stream=streams[r].cuda_stream, **opts)
+                got[j] = np.array(z)
+        except Exception as e:  # reported below, on the main thread
+            errors.append(e)
+
+    threads = [threading.Thread(target=replica, args=(r,)) for r in range(2)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    for j in range(len(S)):
+        assert np.array_equal(got[j], want[j]), j
