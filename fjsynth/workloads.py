@@ -104,12 +104,14 @@ def symmetrize_arcs(src: np.ndarray, dst: np.ndarray, w=None):
     return asrc, adst, aw
 
 
-def warm_training_set(seed_off: int = 7, nvec: int = 3):
+def warm_training_set(seed_off: int = 7, nvec: int = 3, rmat_scales=(14, 16, 17)):
     """Training graphs of the learned warm start: SBM and BA graphs with n from
     10^4 to 10^6, nvec U[0,1] vectors each.  SBM graphs are undirected with
     unit weights; BA graphs are directed, each edge oriented by a fair coin
     and weighted U(0.5, 1.5) FP32, so the network also sees nodes that listen
-    to nobody, nodes nobody listens to, and weights."""
+    to nobody, nodes nobody listens to, and weights.  Then small weighted
+    directed R-MAT graphs (rmat_scales), from seeds of their own: the same
+    family as the evaluation graph, held out by seed and scale."""
     sizes = [10_000, 30_000, 100_000, 300_000, 1_000_000, 20_000, 60_000, 200_000]
     out = []
     for i, n in enumerate(sizes):
@@ -125,4 +127,10 @@ def warm_training_set(seed_off: int = 7, nvec: int = 3):
             dst = np.where(flip, a, b).astype(np.int32)
             w = (0.5 + uniform_array(seed, 8, a.shape[0])).astype(np.float32)
             out.append(dict(name=f"ba_dir_n{n}", n=n, src=src, dst=dst, w=w, directed=True, S=S, fp32=True))
+    for i, sc in enumerate(rmat_scales):
+        seed = BASE_SEED + seed_off + 7919 * (i + 1) + 500
+        src, dst, w = rmat(sc, 16, seed=seed, weighted=True)
+        n = 1 << sc
+        S = [_f32(opinions(n, OP_UNIFORM, seed + 1000, vec=k)) for k in range(nvec)]
+        out.append(dict(name=f"rmat{sc}_dir_train", n=n, src=src, dst=dst, w=w, directed=True, S=S, fp32=True))
     return out
