@@ -62,3 +62,15 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(capi, "LIB_PATH", str(tmp_path / "absent.so"))
     with pytest.raises(RuntimeError, match="no CPU path"):
         capi.lib()
+
+
+def test_new_entry_points_check_arguments_without_gpu(lib):
+    from paper_2507_14864_gb300 import capi
+    mu, om = ctypes.c_double(), ctypes.c_double()
+    assert lib.fj_graph_omega_opt(None, 10, ctypes.byref(mu), ctypes.byref(om), None) == capi.FJ_ERR_INVALID_ARG
+    o = capi.fj_solve_opts()
+    lib.fj_solve_opts_default(ctypes.byref(o))
+    cnt = ctypes.c_int()
+    st = lib.fj_solve_trace(None, None, ctypes.byref(o), None, None, capi.FJ_MEM_HOST, None, 4, ctypes.byref(cnt))
+    assert st == capi.FJ_ERR_INVALID_ARG
+    assert b"graph is NULL" in lib.fj_last_error()
