@@ -3,14 +3,16 @@
 // as synchronous rounds, an FP64 certificate (Lemmas 3-5) and FP64 restarts.
 //
 // State per node u (shifted system s' = s + c_eff, Alg. 2):
-//   r_u    residual of s' - (I + L) zhat'          (T = float or double)
-//   h_u    threshold eps' s'_u                      (T; FP32 rounded down)
-//   d_u    last push increment of u not yet pulled by every in-neighbour
-//   zhat_u estimate of z'_u                         (FP64)
-// A push of u (Eqs. sor1-sor3) is delta = omega r_u / (1 + d_u),
-// zhat_u += delta, r_u <- (1 - omega) r_u, and r_x += a_xu delta for every x
-// with a_xu > 0.  The kernels apply the last step in pull form: when row x is
-// visited it adds sum_j a_xj delta_j over its row.
+//   r_u     residual of s' - (I + L) zhat'          (T = float or double)
+//   h_u     threshold eps' s'_u                      (T; FP32 rounded down)
+//   delta_u last push increment of u, kept in two buffers (this sweep's and
+//           the previous one's) until every in-neighbour has pulled it
+//   zhat_u  estimate of z'_u                         (FP64)
+// With d_u the weighted out-degree, a push of u (Eqs. sor1-sor3) is
+// delta = omega r_u / (1 + d_u), zhat_u += delta, r_u <- (1 - omega) r_u, and
+// r_x += a_xu delta for every x with a_xu > 0.  The kernels apply the last
+// step in pull form: when row x is visited it adds sum_j a_xj delta_j over
+// its row.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
