@@ -268,15 +268,17 @@ def sor_ordered(n, row_ptr, col, w, s, order, eps, omega, c=C_DEFAULT, sigma=SIG
     return z, r, int(stats[0]), int(stats[1]), int(stats[2]), rc == 0
 
 
-def truth(n, row_ptr, col, w, s, tol=None, omega=1.0, max_sweeps=200000):
+def truth(n, row_ptr, col, w, s, tol=None, omega=1.0, max_sweeps=200000, force_sor=False):
     """Certified FP64 equilibrium: LU for n <= 2000, else SOR sweeps to a tiny residual.
 
     The bound max_v |z_v - z*_v| <= max_v |r_v| holds because (I + L)^{-1} is
     nonnegative and row-stochastic (Section 3.3).  Returns ``(z, resid_inf)``.
+    ``force_sor`` takes the sweep branch at any n (its pins compare the two
+    branches on small graphs).
     """
     row_ptr, col, w64 = _graph_args(row_ptr, col, w)
     s = np.ascontiguousarray(s, np.float64)
-    if n <= 2000:
+    if n <= 2000 and not force_sor:
         z = lu_solve(n, row_ptr, col, w, s)
         return z, float(np.max(np.abs(residual(n, row_ptr, col, w, s, z)))) if n else 0.0
     if tol is None:

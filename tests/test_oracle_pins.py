@@ -154,6 +154,99 @@ def test_library_sparse_solve_matches_lu(directed):
     assert res < 1e-12
 
 
+# ------------------------------------------------------------ truth oracle, sweep branch
+#
+# truth() solves by dense LU up to n = 2000 and by sequential SOR sweeps with
+# an inline residual stop above that; the sweep branch is the reference of
+# every GPU parity test on a larger graph (Lemma 1's z = (I + L)^{-1} s).  Its
+# update and its stopping residual share the degree and weight code, so a
+# slip common to both would go unseen by the residual alone: these pins judge
+# it against LU and against a library sparse solve instead.
+
+def weighted_ba(n, directed, seed):
+    """BA graph with U(0.5, 1.5) FP32 weights; directed: each edge oriented at random."""
+    g = W.ba_graph(n, 5, seed_off=seed)
+    rng = np.random.default_rng(seed)
+    a, b = g["src"].astype(np.int32), g["dst"].astype(np.int32)
+    wt = (0.5 + rng.random(a.shape[0])).astype(np.float32)
+    if directed:
+        flip = rng.random(a.shape[0]) < 0.5
+        a, b = np.where(flip, b, a), np.where(flip, a, b)
+        return oracle.csr_from_arcs(n, a, b, wt)
+    return oracle.csr_from_arcs(n, np.concatenate([a, b]), np.concatenate([b, a]), np.concatenate([wt, wt]))
+
+
+@pytest.mark.parametrize("directed,omega", [(False, 1.0), (True, 1.0), (False, 1.5), (True, 1.2)])
+def test_truth_sweep_branch_matches_lu(directed, omega):
+    n = 1500
+    rp, col, w = weighted_ba(n, directed, seed=31 + 2 * directed)
+    s = np.random.default_rng(9).random(n)
+    z_sor, res = oracle.truth(n, rp, col, w, s, omega=omega, force_sor=True)
+    z_lu = oracle.lu_solve(n, rp, col, w, s)
+    assert res <= 1e-12
+    np.testing.assert_allclose(z_sor, z_lu, rtol=0, atol=1e-12)
+    # the residual it reports is the residual of what it returns, up to the
+    # rounding of its plain FP64 row sums: gamma_{deg+2} times the row's magnitudes
+    r = oracle.residual_accurate(n, rp, col, w, s, z_sor)
+    d = oracle.out_degree(n, rp, w)
+    deg = np.diff(rp)
+    rows = np.repeat(np.arange(n), deg)
+    mag = (1 + d) * np.abs(z_sor) + np.bincount(rows, weights=np.asarray(w, np.float64) * np.abs(z_sor[col]),
+                                                minlength=n) + np.abs(s)
+    gam = (deg + 2) * 2.0 ** -53 / (1 - (deg + 2) * 2.0 ** -53)
+    assert abs(float(np.max(np.abs(r))) - res) <= float(np.max(gam * mag))
+
+
+def test_truth_sweep_branch_matches_library_solve_at_20k():
+    scipy_sparse = pytest.importorskip("scipy.sparse")
+    spla = pytest.importorskip("scipy.sparse.linalg")
+    n = 20000
+    rp, col, w = weighted_ba(n, True, seed=47)
+    s = np.random.default_rng(10).random(n)
+    z_t, res = oracle.truth(n, rp, col, w, s)  # n > 2000: the sweep branch
+    A = scipy_sparse.csr_matrix((np.asarray(w, np.float64), col, rp), shape=(n, n))
+    d = np.asarray(A.sum(axis=1)).ravel()
+    M = (scipy_sparse.identity(n) + scipy_sparse.diags(d) - A).tocsr()
+    # a direct factorisation fills in badly on a power-law graph, so the library
+    # side is Jacobi-preconditioned GMRES with a few steps of iterative refinement
+    P = scipy_sparse.diags(1.0 / (1.0 + d))
+    z_lib = np.zeros(n)
+    for _ in range(4):
+        dz, info = spla.gmres(M, s - M @ z_lib, rtol=1e-12, atol=0, restart=200, maxiter=50, M=P)
+        assert info == 0
+        z_lib = z_lib + dz
+    dmax = float(np.max(d))
+    tol = max(1e-13, 4e-15 * (1.0 + dmax))
+    assert res <= tol
+    # both are within their residual of z*: ||(I + L)^{-1}||_inf <= 1
+    r_lib = float(np.max(np.abs(s - M @ z_lib)))
+    np.testing.assert_allclose(z_t, z_lib, rtol=0, atol=tol + r_lib + 1e-14)
+    r = oracle.residual_accurate(n, rp, col, w, s, z_t)
+    assert float(np.max(np.abs(r))) <= tol * (1 + 1e-9)
+
+
+def test_truth_sweep_branch_planted_degree_slip_is_caught():
+    # the same sweeps with the in-degree in place of the out-degree (a slip the
+    # inline residual would share) converge to another vector, which the LU
+    # comparison above rejects; here the slip is made in numpy on the side
+    n = 400
+    rp, col, w = weighted_ba(n, True, seed=53)
+    s = np.random.default_rng(11).random(n)
+    z_lu = oracle.lu_solve(n, rp, col, w, s)
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    wa = np.asarray(w, np.float64)
+    din = np.bincount(col, weights=wa, minlength=n)
+    z = np.zeros(n)
+    for _ in range(400):
+        for v in range(n):
+            k0, k1 = rp[v], rp[v + 1]
+            z[v] = (s[v] + float(np.dot(wa[k0:k1], z[col[k0:k1]]))) / (1.0 + din[v])
+    assert np.max(np.abs(z - z_lu)) > 1e-6
+    z_sor, _ = oracle.truth(n, rp, col, w, s, force_sor=True)
+    assert np.max(np.abs(z_sor - z_lu)) <= 1e-12
+    del rows
+
+
 # ------------------------------------------------------------ push lemmas
 
 def small_ba(n=1500, directed=False):
