@@ -32,7 +32,9 @@ WORKLOADS = {
     # name: generator, precision, omega, schedule
     "rmat22_dir": dict(gen="rmat_dir", scale=22, precision="fp32", omega=1.6, palette=8),
     "ba20k": dict(gen="ba", n=20000, precision="fp64", omega=1.5),
-    "rmat24_und": dict(gen="rmat_und", scale=24, precision="fp32", omega=1.8),
+    "rmat24_und": dict(gen="rmat_und", scale=24, precision="fp32", omega=1.8, cpu_scale=20),
+    "rmat23_und": dict(gen="rmat_und", scale=23, precision="fp32", omega=1.8, cpu_scale=20),
+    "rmat22_und": dict(gen="rmat_und", scale=22, precision="fp32", omega=1.8, cpu_scale=20),
     "rmat16_dir": dict(gen="rmat_dir", scale=16, precision="fp32", omega=1.6),
     "rmat20_dir": dict(gen="rmat_dir", scale=20, precision="fp32", omega=1.6),
     # the paper's other two opinion laws on the same graph: exponential (x_min = 1) and
@@ -52,6 +54,7 @@ WORKLOADS = {
                           train_steps=200, lr=2e-3),
 }
 EPS = 1e-6
+REF_BUDGET_S = 240.0  # timed oracle work of one --impl reference run
 METRIC = "FJ solves/s to 1e-6 rel. err (GTEPS, % HBM roofline): plain vs batched/warm-start"
 
 
@@ -121,14 +124,62 @@ def clocks_stop(p, path, device_index=0):
             "reasons": reasons, "samples": len(rows)}
 
 
-# DRAM bytes (read + write) of k_products + k_sweep per class launch, as a
-# multiple of the algorithmic bytes, from one ncu capture of a full sweep (8
-# class launches) of directed weighted R-MAT s20, FP32, omega 1.6:
-# 31.09 MB against 28.53 MB.  The scale-22 workload is larger than the
-# capture rules allow for a multi-pass metric, and the traffic of these
-# kernels grows with the nonzeros and rows they stream, so the bench scales
-# the ratio to its own launches (directed weighted FP32 single-vector solves).
-SWEEP_TRAFFIC_RATIO_DIR_W = 31.09 / 28.53
+
+
+# Name of the single-vector sweep kernel the roofline object reports.
+SWEEP_KERNEL = "k_products + k_sweep (one sweep segment of a colour class)"
+
+# DRAM bytes (read + write) per launch of the single-vector sweep, as a
+# multiple of the dense bytes it streams, from one ncu capture per graph kind
+# (key: generator, single vector).  Filled in from captures listed under
+# profiles/; a kind without a capture reports traffic null.
+SWEEP_TRAFFIC_RATIO = {
+    ("rmat_dir", True): (31.09 / 28.53, "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_products + k_sweep "
+                         "over one sweep of directed R-MAT s20 (1.090 x its dense bytes), scaled to this launch"),
+}
+
+
+def roofline_of(p, kernel, traffic_key=None):
+    """Roofline object of the push kernel from one profiled solve's info record.
+
+    achieved = the method's own bytes of the profiled launches (per residual
+    update the column, weight and increment, per push 32 bytes: the unit of
+    work of Alg. 1-3) over their summed CUDA-event time.  The dense bytes the
+    pull-form sweep actually streams (every nonzero of every class, every
+    sweep) are reported beside it."""
+    peak, peak_kind = measured_peak_hbm()
+    secs = p["push_ms"] / 1e3
+    launches = max(1, p["push_launches"])
+    achieved = p["method_bytes"] / secs / 1e9 if secs > 0 else None
+    dense = p["push_bytes"] / secs / 1e9 if secs > 0 else None
+    ratio = SWEEP_TRAFFIC_RATIO.get(traffic_key)
+    r = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+         "frac": achieved / peak if achieved else None,
+         "traffic": ratio[0] * p["push_bytes"] / launches if ratio else None,
+         "kernel": kernel, "peak_source": peak_kind,
+         "bytes_per_launch": p["method_bytes"] / launches,
+         "bytes_basis": "method: 4 col + 4 w (weighted) + sizeof(T) increment per residual update, 32 per push",
+         "dense_bytes_per_launch": p["push_bytes"] / launches,
+         "dense_achieved": dense, "dense_frac": dense / peak if dense else None,
+         "avg_launch_us": 1e3 * p["push_ms"] / launches}
+    if ratio:
+        r["traffic_source"] = ratio[1]
+    return r
+
+
+def host_cpu():
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                low = line.lower()
+                if low.startswith("model name") or low.startswith("cpu part") and model is None:
+                    model = line.split(":", 1)[1].strip()
+                    if low.startswith("model name"):
+                        break
+    except OSError:
+        pass
+    return {"model": model, "host_cores": os.cpu_count()}
 
 
 def measured_peak_hbm():
@@ -177,37 +228,56 @@ def oracle_solve_time(name, scale, omega):
 
 
 def run_reference(args):
+    """The oracle's FIFO ImprovedBLISOR (FP64, one host thread) on the full workload.
+
+    Every timed step is one complete solve of the same graph and opinion vector
+    the GPU arm solves.  A full-size solve of the large workloads takes minutes,
+    so the run times as many of the requested steps as fit in REF_BUDGET_S
+    (at least one) and skips the warm-up steps (a CPU loop has nothing to warm);
+    the line reports the steps actually timed."""
     world, rank, _ = dist_init()
     if rank != 0:
         return 0
+    import oracle
     spec = WORKLOADS[args.workload]
     omega = args.omega if args.omega is not None else spec["omega"]
-    full_scale = spec.get("scale")
-    sample_scale = min(full_scale, 18) if full_scale else None
-    # nnz of the full workload for the scaling of the sample's rate
-    times = []
-    nnz_full = None
-    if full_scale:
-        import oracle
-        _, g, src, dst, w = make_workload(args.workload)
-        nnz_full = int(oracle.csr_from_arcs(g["n"], src, dst, w)[0][-1])
-    for i in range(args.warmup + args.steps):
-        dt, nnz_s, ok = oracle_solve_time(args.workload, sample_scale, omega)
-        if i >= args.warmup:
-            times.append((dt, nnz_s))
-    tot = sum(t for t, _ in times)
-    nnz_s = times[0][1]
-    scale_f = (nnz_s / nnz_full) if nnz_full else 1.0
-    value = len(times) / tot * scale_f
-    sample = (f"FIFO ImprovedBLISOR (omega={omega}, eps={EPS}) full solves of the same generator at "
-              f"scale {sample_scale} (nnz {nnz_s}), rate scaled by nnz {nnz_s}/{nnz_full}"
-              if nnz_full else f"full FIFO solves of the workload (omega={omega})")
+    if spec["gen"] in ("ragged", "warm"):
+        print(json.dumps({"impl": "reference", "unavailable": "the reference arm covers the single-graph "
+                          "workloads; %s is timed by its own GPU-arm modes" % args.workload}), flush=True)
+        return 0
+    t0 = time.perf_counter()
+    _, g, src, dst, w = make_workload(args.workload)
+    n = g["n"]
+    rp, col, wc = oracle.csr_from_arcs(n, src, dst, w)
+    del src, dst
+    S = g["S"]
+    prep_s = time.perf_counter() - t0
+    times, info = [], None
+    while len(times) < max(1, args.steps):
+        j = len(times) % len(S)
+        t1 = time.perf_counter()
+        z, r, pushes, upd, ok = oracle.blisor_fifo(n, rp, col, wc, S[j], EPS, omega)
+        times.append(time.perf_counter() - t1)
+        assert ok, "the oracle's FIFO solve did not finish"
+        info = {"pushes": pushes, "updates": upd}
+        if sum(times) * (len(times) + 1) / len(times) > REF_BUDGET_S:
+            break
+    tot = sum(times)
+    value = len(times) / tot
+    cpu = host_cpu()
+    sample = (f"{len(times)} complete FIFO ImprovedBLISOR solve(s) (omega={omega}, eps={EPS}, FP64, one host "
+              f"thread) of the full workload (n={n}, nnz={int(rp[-1])}); warm-up skipped; the run stops "
+              f"after the step that reaches {REF_BUDGET_S:.0f} s; graph build {prep_s:.1f} s untimed")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value if value else None,
+            "steps": len(times), "warmup": 0, "ms_per_step": 1e3 * tot / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": args.workload, "omega": omega, "eps": EPS},
-            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample},
-            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "data": "synthetic", "config": {"workload": args.workload, "n": n, "nnz": int(rp[-1]),
+                                            "omega": omega, "eps": EPS},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample,
+                             "host_cpu": cpu["model"], "host_cores": cpu["host_cores"]},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "detail": {"pushes": info["pushes"], "updates": info["updates"], "steps_requested": args.steps,
+                       "warmup_requested": args.warmup}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -342,21 +412,11 @@ def run_gpu(args):
     else:
         _, pinfo, _ = solve(s_d, z_d, profile=1, **opts)
     p = pinfo[0]
-    peak, peak_kind = measured_peak_hbm()
-    achieved = p["push_bytes"] / (p["push_ms"] / 1e3) / 1e9 if p["push_ms"] > 0 else None
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak if achieved else None, "traffic": None,
-                "kernel": ("k_products + k_sweep (one colour class)" if (k == 1 or cols is not None) else
-                           "%s (one colour class, %d vectors)"
-                           % ("k_sweep_batch_bulk" if (spec["precision"] == "fp32" and k % 4 == 0 and k <= 64)
-                              else "k_sweep_batch", k)), "peak_source": peak_kind,
-                "bytes_per_launch": p["push_bytes"] / max(1, p["push_launches"]),
-                "avg_launch_us": 1e3 * p["push_ms"] / max(1, p["push_launches"])}
-    if k == 1 and cols is None and g["directed"] and w is not None and prec == capi.FJ_PREC_FP32:
-        roofline["traffic"] = SWEEP_TRAFFIC_RATIO_DIR_W * roofline["bytes_per_launch"]
-        roofline["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of k_products + k_sweep "
-                                      "over one sweep of rmat20_dir (1.090 x its algorithmic bytes), scaled to "
-                                      "this launch's algorithmic bytes")
+    kernel = (SWEEP_KERNEL if (k == 1 or cols is not None) else
+              "%s (one colour class, %d vectors)"
+              % ("k_sweep_batch_bulk" if (spec["precision"] == "fp32" and k % 4 == 0 and k <= 64)
+                 else "k_sweep_batch", k))
+    roofline = roofline_of(p, kernel, traffic_key=(spec["gen"], k == 1 or cols is not None))
     info0 = infos[-1]
     detail = {"sweeps": info0["sweeps"], "pushes": info0["pushes"], "edges": info0["edges"],
               "refine_passes": info0["refine_passes"], "resid_rel_max": info0["resid_rel_max"],
@@ -372,11 +432,14 @@ def run_gpu(args):
         cpu_scale = args.cpu_scale if args.cpu_scale is not None else spec.get("cpu_scale")
         dt, nnz_c, ok = oracle_solve_time(args.workload, cpu_scale, omega)
         scale_f = nnz_c / ginfo["nnz"]
+        hc = host_cpu()
         cpu = {"value": scale_f / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
                "sample": (f"one FIFO ImprovedBLISOR solve (omega={omega}, eps={EPS}, FP64, one host thread) of "
                           + ("the full workload" if cpu_scale is None else
-                             f"the same generator at scale {cpu_scale}, rate scaled by nnz "
-                             f"{nnz_c}/{ginfo['nnz']}") + f", {dt:.1f} s")}
+                             f"the same generator at scale {cpu_scale} (a bounded sample: a full-size solve "
+                             f"takes minutes; bench.py --impl reference times full-size solves), rate scaled "
+                             f"by nnz {nnz_c}/{ginfo['nnz']}") + f", {dt:.1f} s"),
+               "host_cpu": hc["model"], "host_cores": hc["host_cores"]}
 
     if rank == 0:
         line = {
@@ -399,6 +462,138 @@ def run_gpu(args):
             "gpu_launches": int(sum(i["launches"] for i in (infos if cols is not None else infos[::k])))
             + 5 * args.steps * (k if cols is not None else 1),
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "detail": detail,
+        }
+        print(json.dumps(line), flush=True)
+    G.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def run_omega_sweep(args):
+    """One graph, several relaxation factors (Section 5.2's omega search; the
+    update counts of Fig. 2): per omega, certified solves/s, sweeps, pushes and
+    residual updates of the GPU schedule, next to the pushes and updates of the
+    oracle's FIFO ImprovedBLISOR at the same omega (host, untimed).  omega = 1
+    runs both synchronous rounds (JACOBI, the round view of Alg. 1) and the
+    multicolour Gauss-Seidel order.  The line's value is the fastest entry."""
+    import torch
+
+    world, rank, local = dist_init()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import __graft_entry__
+    __graft_entry__.build()
+    import oracle
+    from paper_2507_14864_gb300 import capi
+
+    spec, g, src, dst, w = make_workload(args.workload)
+    n = g["n"]
+    prec = capi.FJ_PREC_FP32 if spec["precision"] == "fp32" else capi.FJ_PREC_FP64
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    G = capi.Graph.from_arcs(n, torch.from_numpy(src).to(dev), torch.from_numpy(dst).to(dev),
+                             None if w is None else torch.from_numpy(w).to(dev), directed=g["directed"])
+    ginfo = G.info()
+    s_host = g["S"][0]
+    s_d = torch.from_numpy(s_host).to(dev)
+    z_d = torch.empty_like(s_d)
+    small = n <= 2_000_000
+    rp = col = wc = None
+    if small and rank == 0:
+        rp, col, wc = oracle.csr_from_arcs(n, src, dst, w)
+    omegas = [float(x) for x in args.omega_sweep.split(",")]
+    cases = []
+    for om in omegas:
+        if om == 1.0:
+            cases.append((om, capi.FJ_SCHED_JACOBI))
+        cases.append((om, capi.FJ_SCHED_MULTICOLOUR))
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    rows = []
+    clk, clk_path = clocks_start() if rank == 0 else (None, None)
+    for om, sched in cases:
+        opts = dict(eps=EPS, omega=om, precision=prec, schedule=sched)
+        if spec.get("palette") is not None:
+            opts["palette"] = spec["palette"]
+        for _ in range(args.warmup):
+            G.solve(s_d, out=z_d, **opts)
+            G.metrics(s_d, z_d)
+        barrier()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        infos = []
+        ev0.record(stream)
+        for _ in range(args.steps):
+            _, inf, _ = G.solve(s_d, out=z_d, **opts)
+            G.metrics(s_d, z_d)
+            infos.extend(inf)
+        ev1.record(stream)
+        barrier()
+        ms = max_over_ranks(ev0.elapsed_time(ev1), dev)
+        assert all(i["converged"] == 1 for i in infos), "a timed solve did not certify"
+        i0 = infos[-1]
+        row = {"omega": om, "schedule": "jacobi" if sched == capi.FJ_SCHED_JACOBI else "multicolour",
+               "solves_per_s": whole_job_value(1, args.steps, world, ms), "ms_per_solve": ms / args.steps,
+               "sweeps": i0["sweeps"], "pushes": i0["pushes"], "updates": i0["edges"],
+               "launches": i0["launches"], "opts": opts}
+        if rp is not None:
+            _, _, fp, fu, ok = oracle.blisor_fifo(n, rp, col, wc, s_host, EPS, om)
+            row.update(oracle_fifo_pushes=fp, oracle_fifo_updates=fu)
+        rows.append(row)
+    clocks = clocks_stop(clk, clk_path, local) if rank == 0 else None
+    best = max(rows, key=lambda r: r["solves_per_s"])
+    opts = best.pop("opts")
+    for r in rows:
+        r.pop("opts", None)
+
+    s_pin = torch.from_numpy(s_host).pin_memory().numpy()
+    z_pin = torch.empty(n, dtype=torch.float64).pin_memory().numpy()
+    G.solve(s_pin, out=z_pin, **opts)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        G.solve(s_pin, out=z_pin, **opts)
+        G.metrics(s_pin, z_pin)
+    barrier()
+    e2e_value = whole_job_value(1, args.steps, world, max_over_ranks(time.perf_counter() - t0, dev) * 1e3)
+    _, pinfo, _ = G.solve(s_d, out=z_d, profile=1, **opts)
+    roofline = roofline_of(pinfo[0], SWEEP_KERNEL)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and rp is not None:
+        t0 = time.perf_counter()
+        reps = 0
+        while reps < 1 or time.perf_counter() - t0 < 10.0:
+            oracle.blisor_fifo(n, rp, col, wc, s_host, EPS, best["omega"])
+            reps += 1
+        dt = (time.perf_counter() - t0) / reps
+        hc = host_cpu()
+        cpu = {"value": 1.0 / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
+               "sample": f"{reps} complete FIFO ImprovedBLISOR solves of the full workload (omega="
+                         f"{best['omega']}, eps={EPS}, FP64, one host thread)",
+               "host_cpu": hc["model"], "host_cores": hc["host_cores"]}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": best["solves_per_s"], "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": best["ms_per_solve"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if prec == capi.FJ_PREC_FP32 else "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "n": n, "nnz": ginfo["nnz"], "directed": g["directed"],
+                       "omega": best["omega"], "schedule": best["schedule"], "eps": EPS,
+                       "mode": "omega sweep " + args.omega_sweep, "l2": "inputs smaller than L2: the "
+                       "whole graph and state stay L2-resident (a latency-bound small solve)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
+            "gpu_launches": int(sum(r["launches"] for r in rows)) * args.steps + 5 * args.steps * len(rows),
+            "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
+            "detail": {"omega_sweep": rows},
         }
         print(json.dumps(line), flush=True)
     G.close()
@@ -490,6 +685,25 @@ def run_warm(args):
             if infos is not None:
                 infos.extend(inf)
 
+    # the batched forms: the k vectors as one multi-right-hand-side push, from
+    # zero or from the network's starts (each judged against its zero start)
+    S_b = torch.stack(S, dim=1).contiguous()
+    Z_b = torch.empty_like(S_b)
+    Z0_b = torch.empty_like(S_b)
+
+    def warm_batch_step(infos=None):
+        for j, s_d in enumerate(S):
+            net.predict(G, s_d, out=z0_d)
+            Z0_b[:, j].copy_(z0_d)
+        _, inf, _ = G.solve_batch(S_b, out=Z_b, Z0=Z0_b, **opts)
+        if infos is not None:
+            infos.extend(inf)
+
+    def zero_batch_step(infos=None):
+        _, inf, _ = G.solve_batch(S_b, out=Z_b, **opts)
+        if infos is not None:
+            infos.extend(inf)
+
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stream = torch.cuda.current_stream()
 
@@ -509,9 +723,17 @@ def run_warm(args):
     clk, clk_path = clocks_start() if rank == 0 else (None, None)
     ms_warm, inf_warm = timed(warm_step)
     clocks = clocks_stop(clk, clk_path, local) if rank == 0 else None
-    assert all(i["converged"] == 1 for i in inf_warm + inf_zero), "a timed solve did not certify"
+    ms_zero_b, inf_zero_b = timed(zero_batch_step)
+    ms_warm_b, inf_warm_b = timed(warm_batch_step)
+    assert all(i["converged"] == 1 for i in inf_warm + inf_zero + inf_zero_b + inf_warm_b), \
+        "a timed solve did not certify"
     value = whole_job_value(k, args.steps, world, ms_warm)
     zero_value = whole_job_value(k, args.steps, world, ms_zero)
+    batch = {"zero_batch_solves_per_s": whole_job_value(k, args.steps, world, ms_zero_b),
+             "warm_batch_solves_per_s": whole_job_value(k, args.steps, world, ms_warm_b),
+             "sweeps_zero_batch": inf_zero_b[-1]["sweeps"], "sweeps_warm_batch": inf_warm_b[-1]["sweeps"],
+             "warm_batch_starts_kept": int(sum(1 for i in inf_warm_b[-k:] if i["warm_start"] == 1))}
+    batch["warm_batch_vs_zero_batch"] = batch["warm_batch_solves_per_s"] / batch["zero_batch_solves_per_s"]
     # predict time alone
     barrier()
     ev0.record(stream)
@@ -536,13 +758,7 @@ def run_warm(args):
 
     _, pinfo, _ = G.solve(S[0], out=z_d, z0=z0_d, profile=1, **opts)
     p = pinfo[0]
-    peak, peak_kind = measured_peak_hbm()
-    achieved = p["push_bytes"] / (p["push_ms"] / 1e3) / 1e9 if p["push_ms"] > 0 else None
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak if achieved else None, "traffic": None,
-                "kernel": "k_products + k_sweep (one colour class)", "peak_source": peak_kind,
-                "bytes_per_launch": p["push_bytes"] / max(1, p["push_launches"]),
-                "avg_launch_us": 1e3 * p["push_ms"] / max(1, p["push_launches"])}
+    roofline = roofline_of(p, SWEEP_KERNEL)
     # quality of the start: z0 against the certified zero-start solution, and the
     # share of nodes whose initial residual is above threshold (zero start: all)
     zq = {}
@@ -557,7 +773,8 @@ def run_warm(args):
         zq.setdefault("s_err_rms", []).append(float(np.sqrt(np.mean((sv - zz) ** 2))))
     zq = {key: float(np.mean(v)) for key, v in zq.items()}
     mean = lambda xs: float(np.mean(xs)) if xs else None
-    detail = {"zero_start_solves_per_s": zero_value, "warm_vs_zero": value / zero_value,
+    detail = {"zero_start_solves_per_s": zero_value, "warm_vs_zero": value / zero_value, **batch,
+              "starts_kept": int(sum(1 for i in inf_warm[-k:] if i["warm_start"] == 1)),
               "sweeps_warm": mean([i["sweeps"] for i in inf_warm]),
               "sweeps_zero": mean([i["sweeps"] for i in inf_zero]),
               "predict_ms": predict_ms, "train_s": train_s, "train_steps": spec["train_steps"],
@@ -688,13 +905,7 @@ def run_ragged(args):
     else:
         _, pinfo, _ = handles[-1].solve(svecs[-1], profile=1, **opts)
         p = pinfo[0]
-    peak, peak_kind = measured_peak_hbm()
-    achieved = p["push_bytes"] / (p["push_ms"] / 1e3) / 1e9 if p["push_ms"] > 0 else None
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak if achieved else None, "traffic": None,
-                "kernel": "k_products + k_sweep (one colour class)", "peak_source": peak_kind,
-                "bytes_per_launch": p["push_bytes"] / max(1, p["push_launches"]),
-                "avg_launch_us": 1e3 * p["push_ms"] / max(1, p["push_launches"])}
+    roofline = roofline_of(p, SWEEP_KERNEL)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
@@ -724,7 +935,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rmat22_dir", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="rmat24_und", choices=sorted(WORKLOADS))
     ap.add_argument("--omega", type=float, default=None)
     ap.add_argument("--omega-opt", type=int, default=0, metavar="ITERS",
                     help="take omega from Eq. 17 with mu from ITERS power-iteration steps (fj_graph_omega_opt)")
@@ -738,11 +949,15 @@ def main():
     ap.add_argument("--palette", type=int, default=None)
     ap.add_argument("--tune", action="store_true",
                     help="run the autotuner (fj_graph_tune / fj_graph_tune_batch) before timing")
+    ap.add_argument("--omega-sweep", default=None, metavar="W1,W2,...",
+                    help="time the workload at each relaxation factor (omega = 1 also as Jacobi rounds)")
     ap.add_argument("--plain-loop", action="store_true",
                     help="multi-vector workloads: solve the vectors one fj_solve call each")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.omega_sweep:
+        return run_omega_sweep(args)
     if WORKLOADS[args.workload]["gen"] == "warm":
         return run_warm(args)
     if WORKLOADS[args.workload]["gen"] == "ragged":

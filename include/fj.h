@@ -126,6 +126,19 @@ typedef struct {
     int64_t frontier_pushes; /* entries pushed by those rounds */
     double omega_used;       /* relaxation factor of the reported solve: opts.omega, or 1
                                 after the FJ_SCHED_AUTO divergence fallback */
+    int64_t frontier_edges;  /* residual updates of those frontier rounds (included in edges) */
+    double method_bytes;     /* the push's own bytes: per residual update of the sweeps the
+                                column, weight (weighted graphs) and increment (4 + 4 + sizeof
+                                push precision), plus 32 per push (offsets, residual, estimate,
+                                threshold, 1/(1+d)); a batch counts columns and weights once per
+                                sweep and nonzero, since one load serves all k vectors */
+    double seconds;          /* host wall time of the call */
+    double cert_rel_err;     /* resid_inf / (z_inf - resid_inf): a bound on
+                                max_v |z_v - zhat_v| / max_v |z*_v| (infinite when
+                                resid_inf >= z_inf) */
+    int32_t warm_start;      /* start of the push: -1 zero start (no z0 given), 1 the caller's
+                                z0, 0 the zero start after z0 lost to it (fj_solve_warm) */
+    int32_t reserved;        /* 0 */
 } fj_solve_info;
 
 /* The measures of Table 1 (Section 3.4). */
@@ -210,6 +223,27 @@ fj_status fj_graph_export(const fj_graph *g, int transposed, int64_t *row_ptr, i
 fj_status fj_graph_colour(fj_graph *g, int palette, int32_t *colour, int *ncolours, int mem, void *stream);
 
 /*
+ * fj_graph_order - the row order of the multicolour schedule with this
+ * palette (built here if no solve or fj_graph_colour has built it).  Rows are
+ * renumbered so that each colour class is contiguous, except for a hub
+ * prefix: for one graph and a palette of 1..32 colours, the nodes of largest
+ * in-degree (in-degree >= the smallest threshold that admits at most 49,152
+ * of them; every node when n <= 49,152) come first, ordered by class.  Inside
+ * every range the order is in-degree descending, then caller id.  So class c
+ * is rows [hub_row[c], hub_row[c+1]) and [class_row[c], class_row[c+1]), with
+ * hub_row[ncolours] = *nhub = class_row[0].  Without a hub prefix (palette 0
+ * or a ragged handle) the order is by colour then caller id and *nhub = 0.
+ * The order keeps the increments most rows gather together (the sweep stages
+ * the hubs' in shared memory); any order is a valid Gauss-Seidel order
+ * (Theorem 2), and results are returned in caller order.  perm[i] = the caller
+ * id of row i (n entries, per mem; may be NULL); hub_row and class_row are host
+ * arrays of ncolours + 1 entries (fj_graph_colour or fj_graph_info give
+ * ncolours; either may be NULL); *nhub (host) may be NULL.
+ */
+fj_status fj_graph_order(fj_graph *g, int palette, int32_t *perm, int64_t *nhub, int64_t *hub_row,
+                         int64_t *class_row, int mem, void *stream);
+
+/*
  * fj_solve - ImprovedBLISOR (Alg. 3 with the shift of Alg. 2) on the GPU.
  * Under opts->schedule == FJ_SCHED_AUTO a solve whose residual becomes
  * non-finite with omega > 1 (the multicolour SOR is only proven for
@@ -236,7 +270,11 @@ fj_status fj_solve(fj_graph *g, const double *s, const fj_solve_opts *opts, doub
  * fj_solve_warm - as fj_solve, but the push starts from the estimate z0[n]
  * (FP64) instead of zero: the initial residual is r = s' - (I + L)(z0 + c_eff),
  * computed in FP64, and pushes use the |r| test of Alg. 3, so any start
- * converges to the same certificate (Lemmas 3 and 5).
+ * converges to the same certificate (Lemmas 3 and 5).  The zero start judges
+ * z0 and is its fallback: the push's work falls with the residual sum
+ * (Section 5.1.2), so z0 is used only when sum_v |r_v| < sum_v s'_v, the
+ * zero start's residual sum (both summed in a fixed order); otherwise the
+ * solve starts from zero.  info.warm_start reports which start was used.
  */
 fj_status fj_solve_warm(fj_graph *g, const double *s, const double *z0, const fj_solve_opts *opts,
                         double *z_out, fj_solve_info *info, int mem);
@@ -254,6 +292,15 @@ fj_status fj_solve_warm(fj_graph *g, const double *s, const double *z0, const fj
  */
 fj_status fj_solve_batch(fj_graph *g, const double *S, int k, const fj_solve_opts *opts,
                          double *Z_out, fj_solve_info *info, int mem);
+
+/*
+ * fj_solve_batch_warm - fj_solve_batch from the starts Z0[n][k] (node-major,
+ * FP64): every vector's start is judged against its zero start as in
+ * fj_solve_warm, and a vector whose start loses restarts from zero while the
+ * others keep theirs (info[j].warm_start).  S, Z0 and Z_out must not alias.
+ */
+fj_status fj_solve_batch_warm(fj_graph *g, const double *S, const double *Z0, int k, const fj_solve_opts *opts,
+                              double *Z_out, fj_solve_info *info, int mem);
 
 /*
  * fj_solve_trace - fj_solve that also records how the push converges, for
@@ -346,10 +393,12 @@ fj_status fj_frontier(int64_t n, const void *r, const void *h, int precision, in
 /*
  * fj_frontier_static - the same frontier as fj_frontier, for callers that
  * cannot allocate device memory: a process whose device memory is all handed
- * out by its own pool, or code that must not let a call synchronise the
- * device, which cudaMalloc and cudaFree can do.  It makes no allocation of
- * any kind (no cudaMalloc, cudaFree, stream-ordered or library allocation).
- * The paper has no counterpart: this is a property of the interface only.
+ * out up front by its own pool or arena (a serving process that reserves the
+ * GPU's memory at start-up, or a framework that owns the allocator), where a
+ * cudaMalloc would fail or take memory the pool has promised elsewhere.  It
+ * makes no allocation of any kind (no cudaMalloc, cudaFree, stream-ordered or
+ * library allocation).  The paper has no counterpart: this is a property of
+ * the interface only.
  *
  * The look-back scratch is a file-scope device array sized for n up to 2^26
  * (67,108,864) nodes, about 256 KB, which every GPU that loads the library
@@ -357,10 +406,14 @@ fj_status fj_frontier(int64_t n, const void *r, const void *h, int precision, in
  * array is shared by every call: the call clears what must start at zero, and
  * calls whose work overlaps on the GPU (on different streams, or from
  * different threads) race on it and must not be made.  The first call on each
- * device looks up the array's device address with cudaGetSymbolAddress; make
- * that first call before any stream capture.  Arguments, layout and errors are
- * those of fj_frontier: r, h, list and count are device pointers, list holds
- * n entries, *count receives |F|.
+ * device looks up the array's device address with cudaGetSymbolAddress and
+ * keeps it for the life of the process; make that first call before any stream
+ * capture begins.  After cudaDeviceReset the kept address is stale, like every
+ * other handle of this library, so no call may follow a reset.  Each call
+ * waits for its stream to finish: it reads the count back to the host to
+ * check the look-back's status.  Arguments, layout and errors are those of
+ * fj_frontier: r, h, list and count are device pointers, list holds n entries,
+ * *count receives |F|.
  */
 fj_status fj_frontier_static(int64_t n, const void *r, const void *h, int precision, int32_t *list,
                              int64_t *count, void *stream);
@@ -372,6 +425,27 @@ fj_status fj_frontier_static(int64_t n, const void *r, const void *h, int precis
  */
 fj_status fj_residual(fj_graph *g, const double *s, const double *z, double c_eff, double *r,
                       int mem, void *stream);
+
+/* ------------------------------------------------------------------ failure paths
+ *
+ * Two hooks for testing how the library fails, without faulting the GPU.
+ * Neither has a counterpart in the paper.
+ *
+ * fj_wait_selftest - runs the library's two bounded device waits (the scan
+ * look-back's wait on a tile status word, the bulk-copy ring's wait on an
+ * mbarrier) on one thread of one block, each on something that nothing
+ * completes, with a limit of `polls` polls (1..2^24).  Returns FJ_ERR_TIMEOUT
+ * when both gave up, as they must; the context stays usable (later calls
+ * work).  FJ_OK means a wait returned although nothing completed it.
+ *
+ * fj_debug_fail_allocation - makes device allocation number after + 1 of the
+ * library, counted from this call, fail as if the device were full (the call
+ * that made it returns FJ_ERR_OOM); one allocation fails, then the hook
+ * disarms itself.  after < 0 disarms it.  Process-wide; meant for tests, not
+ * for use while other threads call the library.
+ */
+fj_status fj_wait_selftest(int64_t polls, void *stream);
+void fj_debug_fail_allocation(int64_t after);
 
 /* ------------------------------------------------------------------ learned warm start
  *

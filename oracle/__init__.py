@@ -445,6 +445,48 @@ def palette_colour(n, row_ptr, col, w, directed: bool, K: int):
     return colour, int(k), din
 
 
+# Largest hub prefix of the multicolour row order (a layout parameter of the
+# sweep, not of the method: the size of its shared-memory increment table).
+HUB_CAPACITY = 49152
+
+
+def sweep_order(n, row_ptr, col, colour, hubs: bool):
+    """Row order of the multicolour schedule: any order is a Gauss-Seidel order
+    (Theorem 2), so the one chosen only has to be reproducible.  With hubs (one
+    graph, a bounded palette), the nodes of largest in-degree come first,
+    ordered by class: in-degree >= the smallest threshold that admits at most
+    HUB_CAPACITY of them (every node when n <= HUB_CAPACITY).  Then every
+    class's other nodes.  Inside each range: in-degree descending (clamped to
+    2^22 - 1), then id.  Without hubs: colour, then id.
+
+    Returns (perm int32[n]: id of row i, nhub, hub_row[K+1], class_row[K+1]);
+    class c is rows [hub_row[c], hub_row[c+1]) and [class_row[c], class_row[c+1]).
+    """
+    colour = np.asarray(colour, np.int64)
+    col = np.asarray(col, np.int64)
+    K = int(colour.max()) + 1 if n else 0
+    indeg = np.bincount(col, minlength=n).astype(np.int64)  # rows that list the node
+    ids = np.arange(n)
+    if hubs:
+        if n <= HUB_CAPACITY:
+            hub = np.ones(n, bool)
+        else:
+            v = int(np.sort(indeg)[::-1][HUB_CAPACITY - 1])
+            thr = v if int(np.count_nonzero(indeg >= v)) <= HUB_CAPACITY else v + 1
+            hub = indeg >= thr
+        d = np.minimum(indeg, (1 << 22) - 1)
+        perm = np.lexsort((ids, -d, colour, ~hub))
+    else:
+        hub = np.zeros(n, bool)
+        perm = np.lexsort((ids, colour))
+    nhub = int(np.count_nonzero(hub))
+    pc = colour[perm]
+    hub_row = np.array([int(np.searchsorted(pc[:nhub], c, side="left")) for c in range(K + 1)], np.int64)
+    class_row = np.array([nhub + int(np.searchsorted(pc[nhub:], c, side="left")) for c in range(K + 1)], np.int64)
+    hub_row[K], class_row[K] = nhub, n
+    return perm.astype(np.int32), nhub, hub_row, class_row
+
+
 def safe_omega(omega, d64, din):
     """Per-node relaxation for a colouring with in-class conflicts: the largest
     omega_v <= omega with (2 / omega_v - 1)(1 + d_v) >= din_v / 0.98, which keeps

@@ -25,7 +25,8 @@ EXPORTED = [
     "fj_solve_opts_default", "fj_status_string", "fj_last_error", "fj_graph_create",
     "fj_graph_create_from_arcs", "fj_graph_create_ragged", "fj_graph_destroy", "fj_graph_info",
     "fj_graph_export", "fj_graph_colour", "fj_solve", "fj_solve_warm", "fj_solve_batch",
-    "fj_metrics", "fj_metrics_batch", "fj_frontier", "fj_frontier_static", "fj_residual",
+    "fj_metrics", "fj_metrics_batch", "fj_frontier", "fj_frontier_static", "fj_residual", "fj_solve_batch_warm", "fj_graph_order",
+    "fj_wait_selftest", "fj_debug_fail_allocation",
     "fj_graph_tune", "fj_graph_tune_batch", "fj_graph_omega_opt", "fj_solve_trace", "fj_mpnn_param_count", "fj_mpnn_create", "fj_mpnn_destroy", "fj_mpnn_get_params", "fj_mpnn_set_params",
     "fj_mpnn_predict", "fj_mpnn_grad", "fj_mpnn_adam_step",
 ]
@@ -45,7 +46,10 @@ class fj_solve_info(ctypes.Structure):
                 ("resid_rel_max", ctypes.c_double), ("z_inf", ctypes.c_double), ("err_bound", ctypes.c_double),
                 ("launches", ctypes.c_int64), ("push_launches", ctypes.c_int64), ("push_ms", ctypes.c_double),
                 ("push_bytes", ctypes.c_double), ("frontier_rounds", ctypes.c_int64),
-                ("frontier_pushes", ctypes.c_int64), ("omega_used", ctypes.c_double)]
+                ("frontier_pushes", ctypes.c_int64), ("omega_used", ctypes.c_double),
+                ("frontier_edges", ctypes.c_int64), ("method_bytes", ctypes.c_double),
+                ("seconds", ctypes.c_double), ("cert_rel_err", ctypes.c_double),
+                ("warm_start", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -88,9 +92,14 @@ def lib():
                                 ctypes.POINTER(I32)]
     L.fj_graph_export.argtypes = [VP, I32, VP, VP, VP, VP, I32, VP]
     L.fj_graph_colour.argtypes = [VP, I32, VP, ctypes.POINTER(I32), I32, VP]
+    L.fj_graph_order.argtypes = [VP, I32, VP, ctypes.POINTER(I64), VP, VP, I32, VP]
+    L.fj_wait_selftest.argtypes = [I64, VP]
+    L.fj_debug_fail_allocation.argtypes = [I64]
+    L.fj_debug_fail_allocation.restype = None
     L.fj_solve.argtypes = [VP, VP, ctypes.POINTER(fj_solve_opts), VP, VP, I32]
     L.fj_solve_warm.argtypes = [VP, VP, VP, ctypes.POINTER(fj_solve_opts), VP, VP, I32]
     L.fj_solve_batch.argtypes = [VP, VP, I32, ctypes.POINTER(fj_solve_opts), VP, VP, I32]
+    L.fj_solve_batch_warm.argtypes = [VP, VP, VP, I32, ctypes.POINTER(fj_solve_opts), VP, VP, I32]
     L.fj_metrics.argtypes = [VP, VP, VP, VP, I32, VP]
     L.fj_graph_tune.argtypes = [VP, VP, ctypes.POINTER(fj_solve_opts), I32, ctypes.POINTER(fj_solve_opts),
                                 ctypes.POINTER(D), I32]
@@ -115,6 +124,7 @@ def lib():
     L.fj_mpnn_adam_step.argtypes = [VP, D, VP]
     for name in EXPORTED:
         if name not in ("fj_solve_opts_default", "fj_graph_destroy", "fj_status_string", "fj_last_error",
+                        "fj_debug_fail_allocation",
                         "fj_graph_tune", "fj_graph_tune_batch", "fj_mpnn_param_count", "fj_mpnn_destroy"):
             getattr(L, name).restype = st
     _lib = L
@@ -297,6 +307,18 @@ class Graph:
                                      current_stream()), "fj_graph_colour")
         return out, k.value
 
+    def order(self, palette=16):
+        """fj_graph_order: (perm, nhub, hub_row, class_row) of the multicolour row order."""
+        _, k = self.colour(palette)
+        n = self.info()["n"]
+        perm = np.empty(n, np.int32)
+        nhub = ctypes.c_int64()
+        hub_row = np.empty(k + 1, np.int64)
+        class_row = np.empty(k + 1, np.int64)
+        _check(lib().fj_graph_order(self._h, int(palette), _ptr(perm), ctypes.byref(nhub), _ptr(hub_row),
+                                    _ptr(class_row), FJ_MEM_HOST, current_stream()), "fj_graph_order")
+        return perm, nhub.value, hub_row, class_row
+
     # ------------------------------------------------------------ compute
     def solve(self, s, out=None, z0=None, allow_unconverged=False, **opts):
         """fj_solve / fj_solve_warm.  Returns (z, [fj_solve_info per graph], status)."""
@@ -341,22 +363,29 @@ class Graph:
         _check(st, "fj_solve_trace")
         return out, [i.as_dict() for i in infos], st, rows[:count.value].copy()
 
-    def solve_batch(self, S, out=None, allow_unconverged=False, **opts):
-        """fj_solve_batch on node-major S[n, k].  Returns (Z, [info per vector], status)."""
+    def solve_batch(self, S, out=None, Z0=None, allow_unconverged=False, **opts):
+        """fj_solve_batch (fj_solve_batch_warm with Z0) on node-major S[n, k].
+        Returns (Z, [info per vector], status)."""
         o = default_opts(**opts)
         k = int(S.shape[1])
         infos = (fj_solve_info * k)()
-        mem = _mem_of(S, out)
+        mem = _mem_of(S, out, Z0)
         if out is None:
             if mem == FJ_MEM_DEVICE:
                 import torch
                 out = torch.empty_like(S)
             else:
                 out = np.empty_like(S)
-        st = lib().fj_solve_batch(self._h, _ptr(S, np.float64), k, ctypes.byref(o), _ptr(out, np.float64),
-                                  infos, mem)
+        if Z0 is None:
+            st = lib().fj_solve_batch(self._h, _ptr(S, np.float64), k, ctypes.byref(o), _ptr(out, np.float64),
+                                      infos, mem)
+            where = "fj_solve_batch"
+        else:
+            st = lib().fj_solve_batch_warm(self._h, _ptr(S, np.float64), _ptr(Z0, np.float64), k, ctypes.byref(o),
+                                           _ptr(out, np.float64), infos, mem)
+            where = "fj_solve_batch_warm"
         allow = (FJ_ERR_NOT_CONVERGED, FJ_ERR_DIVERGED) if allow_unconverged else ()
-        _check(st, "fj_solve_batch", allow)
+        _check(st, where, allow)
         return out, [i.as_dict() for i in infos], st
 
     def metrics(self, s, z):

@@ -17,6 +17,16 @@ namespace fj {
 void set_error(const char *fmt, ...);
 fj_status cuda_fail(cudaError_t e, const char *what, const char *file, int line);
 
+// Every device allocation of the library goes through dev_malloc, so that a
+// test can make one fail on the host (fj_debug_fail_allocation) as a full
+// device would, without touching the GPU.
+cudaError_t dev_malloc_raw(void **p, size_t bytes);
+template <typename T>
+inline cudaError_t dev_malloc(T **p, size_t bytes)
+{
+    return dev_malloc_raw(reinterpret_cast<void **>(p), bytes);
+}
+
 #define FJ_CUDA(...)                                                                       \
     do {                                                                                   \
         cudaError_t fj_e_ = (__VA_ARGS__);                                                 \
@@ -215,6 +225,7 @@ struct Counters {
     double nonfinite;                 // set when a residual became NaN/Inf
     unsigned int ticket;              // next work item of the running sweep
     unsigned int pad;
+    unsigned long long fedges;        // residual updates of the FP64 frontier push rounds
 };
 
 // Launch helper: grid size for a grid-stride loop over `work` items.

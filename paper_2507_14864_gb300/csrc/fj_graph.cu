@@ -4,7 +4,10 @@
 // arcs), ragged block-diagonal batches, and the Jones-Plassmann colouring that
 // gives the Gauss-Seidel order of the multicolour schedule.
 #include <algorithm>
+#include <atomic>
+#include <climits>
 #include <cstring>
+#include <functional>
 #include <string>
 
 #include "fj_internal.cuh"
@@ -34,12 +37,31 @@ void dev_free(void *p)
     if (p) cudaFree(p);
 }
 
+// Allocation-failure injection: -1 disarmed, else the number of allocations
+// that still succeed before one fails.
+static std::atomic<long long> g_fail_alloc_after{-1};
+
+cudaError_t dev_malloc_raw(void **p, size_t bytes)
+{
+    long long left = g_fail_alloc_after.load();
+    while (left >= 0) {
+        if (g_fail_alloc_after.compare_exchange_weak(left, left - 1)) {
+            if (left == 0) {
+                *p = nullptr;
+                return cudaErrorMemoryAllocation;
+            }
+            break;
+        }
+    }
+    return cudaMalloc(p, bytes);
+}
+
 template <typename T>
 static cudaError_t dalloc(T **p, int64_t count)
 {
     *p = nullptr;
     if (count <= 0) count = 1;
-    return cudaMalloc(reinterpret_cast<void **>(p), sizeof(T) * (size_t)count);
+    return dev_malloc(reinterpret_cast<void **>(p), sizeof(T) * (size_t)count);
 }
 
 fj_status ws_status(Workspace &ws, int64_t tiles)
@@ -384,7 +406,7 @@ static fj_status graph_alloc_shell(int64_t n, int directed, fj_graph **out)
     cudaGetDevice(&g->device);
     g->directed = directed ? 1 : 0;
     g->csr.n = n;
-    cudaError_t e = cudaMalloc(&g->err, sizeof(int));
+    cudaError_t e = dev_malloc(&g->err, sizeof(int));
     if (e == cudaSuccess) e = cudaMallocHost(&g->err_host, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(g->err, 0, sizeof(int));
     if (e != cudaSuccess) {
@@ -698,7 +720,7 @@ void fj_graph_destroy(fj_graph *g)
         dev_free(ip->cnt);
     }
     Workspace &ws = g->ws;
-    dev_free(ws.r); dev_free(ws.h); dev_free(ws.da); dev_free(ws.db); dev_free(ws.om); dev_free(ws.prod);
+    dev_free(ws.r); dev_free(ws.h); dev_free(ws.da); dev_free(ws.db); dev_free(ws.om); dev_free(ws.judge);
     dev_free(ws.zhat); dev_free(ws.sp); dev_free(ws.sin); dev_free(ws.zout); dev_free(ws.r64); dev_free(ws.zs);
     dev_free(ws.gstat); dev_free(ws.ctr); dev_free(ws.status); dev_free(ws.tile_ctr); dev_free(ws.zmax);
     dev_free(ws.list); dev_free(ws.count); dev_free(ws.partial);
@@ -899,23 +921,30 @@ __global__ void k_perm_node_arrays(int64_t n, const int32_t *__restrict__ perm, 
     }
 }
 
+// A forced block start wherever the range key (sorted key >> shift: the hub
+// flag and the colour) or, in a ragged batch, the graph changes.
 struct SegStartPred {
-    const uint32_t *colour_sorted;
+    const uint32_t *key_sorted;
     const int32_t *graph;
+    int shift;
     __device__ bool operator()(int64_t i) const
     {
-        return i == 0 || colour_sorted[i] != colour_sorted[i - 1] || (graph && graph[i] != graph[i - 1]);
+        return i == 0 || (key_sorted[i] >> shift) != (key_sorted[i - 1] >> shift) ||
+               (graph && graph[i] != graph[i - 1]);
     }
 };
 
 // Sort key of the colour permutation: the colour, and when indeg is given,
-// below it the in-degree descending (22 bits, clamped), so that inside a
-// class the nodes most rows gather from sit together (their increments share
-// cache sectors); ties keep id order (the sort is stable).
+// above it a flag that is 0 for hubs (in-degree >= hub_min) and below it the
+// in-degree descending (22 bits, clamped).  So the hubs come first, ordered
+// by class, then every class's other nodes; inside each range the nodes most
+// rows gather from sit together (their increments share cache sectors, and
+// the hubs' fit the sweep's shared-memory table).  Ties keep id order (the
+// sort is stable).
 constexpr int kDegKeyBits = 22;
 
 __global__ void k_colour_keys(int64_t n, const int32_t *__restrict__ colour, const int32_t *__restrict__ indeg,
-                              uint32_t *__restrict__ key)
+                              int32_t hub_min, uint32_t *__restrict__ key)
 {
     constexpr uint32_t dmax = (1u << kDegKeyBits) - 1u;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -923,9 +952,23 @@ __global__ void k_colour_keys(int64_t n, const int32_t *__restrict__ colour, con
             key[i] = (uint32_t)colour[i];
         } else {
             const uint32_t d = (uint32_t)min(max(indeg[i], 0), (int32_t)dmax);
-            key[i] = ((uint32_t)colour[i] << kDegKeyBits) | (dmax - d);
+            const uint32_t cold = indeg[i] >= hub_min ? 0u : 1u;
+            key[i] = (cold << 31) | ((uint32_t)colour[i] << kDegKeyBits) | (dmax - d);
         }
     }
+}
+
+// Smallest in-degree threshold whose hub set {v : indeg_v >= t} holds at most
+// kHubMax nodes (every node when n <= kHubMax).
+static int32_t hub_threshold(const int32_t *indeg_host, int64_t n)
+{
+    if (n <= kHubMax) return INT32_MIN;
+    std::vector<int32_t> d(indeg_host, indeg_host + n);
+    std::nth_element(d.begin(), d.begin() + (kHubMax - 1), d.end(), std::greater<int32_t>());
+    const int32_t v = d[(size_t)kHubMax - 1];
+    int64_t ge = 0;
+    for (int64_t i = 0; i < n; ++i) ge += indeg_host[i] >= v;
+    return ge <= kHubMax ? v : v + 1;
 }
 
 // Data-driven greedy colouring (the same colours as the sequential greedy in
@@ -1249,25 +1292,50 @@ fj_status ensure_colouring(fj_graph *g, int palette, cudaStream_t st)
     FJ_CUDA(dalloc(&v1, n));
     // in-degree order inside classes: one graph and a bounded palette (colours
     // then fit the key's top 10 bits)
-    const bool deg_key = g->ngraphs == 1 && palette > 0 && palette <= 1024;
-    k_colour_keys<<<grid_for(n, 256), 256, 0, st>>>(n, cl.colour, deg_key ? c.indeg : nullptr, k0);
+    const bool deg_key = g->ngraphs == 1 && palette > 0 && palette <= 32;
+    int32_t hub_min = INT32_MAX;
+    if (deg_key) {
+        std::vector<int32_t> hd((size_t)n);
+        FJ_CUDA(cudaMemcpyAsync(hd.data(), c.indeg, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st));
+        FJ_CUDA(cudaStreamSynchronize(st));
+        hub_min = hub_threshold(hd.data(), n);
+    }
+    k_colour_keys<<<grid_for(n, 256), 256, 0, st>>>(n, cl.colour, deg_key ? c.indeg : nullptr, hub_min, k0);
     k_iota<<<grid_for(n, 256), 256, 0, st>>>(n, v0);
     FJ_CUDA(cudaGetLastError());
     bool in1 = false;
     FJ_CUDA(sort_pairs(n, 32, k0, v0, k1, v1, g->sort, g->err, st, &in1));
     uint32_t *sk = in1 ? k1 : k0, *sv = in1 ? v1 : v0;
-    // class boundaries from the sorted colours
+    // range boundaries from the sorted keys: hubs by colour, then the rest by colour
     const int kshift = deg_key ? kDegKeyBits : 0;
     std::vector<uint32_t> hk((size_t)n);
     FJ_CUDA(cudaMemcpyAsync(hk.data(), sk, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, st));
     FJ_CUDA(cudaStreamSynchronize(st));
     for (auto &x : hk) x >>= kshift;
-    cl.ncolours = (int)hk[(size_t)n - 1] + 1;
+    constexpr uint32_t kColdBit = 1u << (31 - kDegKeyBits);
+    auto colour_at = [&](int64_t i) -> uint32_t {
+        return deg_key ? (hk[(size_t)i] & (kColdBit - 1u)) : hk[(size_t)i];
+    };
+    uint32_t maxc = 0;
+    int64_t nhub = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        maxc = std::max(maxc, colour_at(i));
+        if (deg_key && !(hk[(size_t)i] & kColdBit)) ++nhub;
+    }
+    cl.ncolours = (int)maxc + 1;
+    cl.nhub = nhub;
+    // class c's hub rows start at the first hub of colour >= c, its other rows at
+    // the first non-hub of colour >= c (the ranges of an absent colour are empty)
+    cl.hub_row.assign((size_t)cl.ncolours + 1, nhub);
     cl.class_row.assign((size_t)cl.ncolours + 1, n);
-    cl.class_row[0] = 0;
-    for (int64_t i = 1; i < n; ++i)
-        if (hk[(size_t)i] != hk[(size_t)i - 1])
-            for (uint32_t cc = hk[(size_t)i - 1] + 1; cc <= hk[(size_t)i]; ++cc) cl.class_row[cc] = i;
+    for (int64_t i = 0, cc = 0; cc < cl.ncolours; ++cc) {
+        while (i < nhub && colour_at(i) < (uint32_t)cc) ++i;
+        cl.hub_row[(size_t)cc] = i;
+    }
+    for (int64_t i = nhub, cc = 0; cc < cl.ncolours; ++cc) {
+        while (i < n && colour_at(i) < (uint32_t)cc) ++i;
+        cl.class_row[(size_t)cc] = i;
+    }
     if (!cl.perm) FJ_CUDA(dalloc(&cl.perm, n));
     if (!cl.iperm) FJ_CUDA(dalloc(&cl.iperm, n));
     k_inverse_perm<<<grid_for(n, 256), 256, 0, st>>>(n, sv, cl.perm, cl.iperm);
@@ -1313,7 +1381,7 @@ fj_status ensure_colouring(fj_graph *g, int palette, cudaStream_t st)
     // change of graph inside a class, so that each row block lies in one
     // class of one graph
     int32_t *starts = reinterpret_cast<int32_t *>(in1 ? v0 : v1);  // free value buffer
-    FJ_CUDA(compact<256, 8>(n, SegStartPred{sk, p.graph_of}, starts, g->ws.count, g->ws.status, g->ws.tile_ctr,
+    FJ_CUDA(compact<256, 8>(n, SegStartPred{sk, p.graph_of, kshift}, starts, g->ws.count, g->ws.status, g->ws.tile_ctr,
                             g->err, st));
     long long nseg = 0;
     FJ_CUDA(cudaMemcpyAsync(&nseg, g->ws.count, sizeof(long long), cudaMemcpyDeviceToHost, st));
@@ -1326,11 +1394,6 @@ fj_status ensure_colouring(fj_graph *g, int palette, cudaStream_t st)
     FJ_CHECK(build_blocks(p, segs, g->ws, g->err, st, kTileBlock));
     FJ_CHECK(build_blocks(p, segs, g->ws, g->err, st, kTileWarp));
     FJ_CHECK(build_blocks(p, segs, g->ws, g->err, st, kTileSweep));
-    cl.class_blk.assign((size_t)cl.ncolours + 1, p.nblocks);
-    for (int k = 0; k < cl.ncolours; ++k) {
-        size_t at = (size_t)(std::lower_bound(segs.begin(), segs.end(), cl.class_row[k]) - segs.begin());
-        cl.class_blk[k] = p.seg_blk[at];
-    }
     cl.built = true;
     return read_dev_error(g, st);
 }
@@ -1351,4 +1414,30 @@ extern "C" fj_status fj_graph_colour(fj_graph *g, int palette, int32_t *colour, 
     FJ_CUDA(cudaStreamSynchronize(st));
     if (ncolours) *ncolours = g->colr.ncolours;
     return FJ_OK;
+}
+
+extern "C" fj_status fj_graph_order(fj_graph *g, int palette, int32_t *perm, int64_t *nhub, int64_t *hub_row,
+                                    int64_t *class_row, int mem, void *stream)
+{
+    FJ_ARG(g != nullptr, "graph is NULL");
+    FJ_ARG(mem == FJ_MEM_HOST || mem == FJ_MEM_DEVICE, "mem must be FJ_MEM_HOST or FJ_MEM_DEVICE");
+    FJ_ARG(palette >= 0 && palette <= 32, "palette must be 0 (unbounded) or 1..32");
+    cudaStream_t st = (cudaStream_t)stream;
+    FJ_CHECK(fj::ensure_colouring(g, palette, st));
+    const fj::Colouring &cl = g->colr;
+    if (perm)
+        FJ_CUDA(cudaMemcpyAsync(perm, cl.perm, sizeof(int32_t) * g->csr.n,
+                                mem == FJ_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    FJ_CUDA(cudaStreamSynchronize(st));
+    if (nhub) *nhub = cl.nhub;
+    for (int c = 0; c <= cl.ncolours; ++c) {
+        if (hub_row) hub_row[c] = cl.hub_row[(size_t)c];
+        if (class_row) class_row[c] = cl.class_row[(size_t)c];
+    }
+    return FJ_OK;
+}
+
+extern "C" void fj_debug_fail_allocation(int64_t after)
+{
+    fj::g_fail_alloc_after.store(after < 0 ? -1 : (long long)after);
 }

@@ -61,9 +61,14 @@ struct Colouring {
     int32_t *colour = nullptr;  // by original id
     int32_t *perm = nullptr;    // new id -> original id
     int32_t *iperm = nullptr;   // original id -> new id
-    std::vector<int64_t> class_row;  // host: rows of class c are [class_row[c], class_row[c+1])
+    // host: the non-hub rows of class c are [class_row[c], class_row[c+1]) and its
+    // hub rows [hub_row[c], hub_row[c+1]); the nhub hubs (nodes of largest
+    // in-degree) come first, ordered by class, so hub_row[ncolours] = nhub =
+    // class_row[0].  Without hubs every class is the one range of class_row.
+    std::vector<int64_t> class_row;
+    std::vector<int64_t> hub_row;
+    int64_t nhub = 0;
     DevCSR pcsr;                     // permuted CSR, blocks never straddle a class
-    std::vector<int64_t> class_blk;  // host: blocks of class c are [class_blk[c], class_blk[c+1])
     // directed graphs, built on first use: in-neighbour lists in the permuted
     // order (row i lists the new ids of the nodes that listen to perm[i])
     int64_t *tptr = nullptr;
@@ -80,8 +85,13 @@ struct Item {
     int32_t r0, r1;
     int32_t lo;
     int32_t slot;
+    int32_t hlo;   // first hub row of the item's class (hub ids below it are in earlier classes)
+    int32_t nhub;  // number of hubs (ids below it are hubs); 0 without a hub prefix
     int64_t k0, k1;
 };
+// Largest hub prefix of the colour order: the fused sweep's hot table holds
+// this many FP32 increments in shared memory.
+constexpr int kHubMax = 49152;
 constexpr int kChunkNnz = 2048;
 
 struct ItemPlan {
@@ -95,15 +105,7 @@ struct ItemPlan {
     int32_t *cnt = nullptr;         // device: chunks finished per long row
     int64_t nparts = 0;
     std::vector<int64_t> class_item;  // host: items of class c are [class_item[c], class_item[c+1])
-    std::vector<int64_t> class_k;     // host: nonzeros of class c are [class_k[c], class_k[c+1])
-    // host: sweep segments, classes cut at item boundaries into runs of at most
-    // kSegNnz nonzeros (so one segment's products stay in L2): segment s covers
-    // items [seg_item[s], seg_item[s+1]) and nonzeros [seg_k[s], seg_k[s+1]) of
-    // class seg_class[s]
-    std::vector<int64_t> seg_item, seg_k;
-    std::vector<int32_t> seg_class;
 };
-constexpr int64_t kSegNnz = int64_t(1) << 24;
 
 // Solve scratch, grown on demand and kept by the handle.
 struct Workspace {
@@ -114,8 +116,8 @@ struct Workspace {
     void *da = nullptr;     // push increments (current)
     void *db = nullptr;     // push increments (second buffer)
     void *om = nullptr;     // per-node relaxation factor
-    void *prod = nullptr;   // per-nonzero products a_k delta_col(k) of the running class
-    int64_t cap_prod = 0;
+    double *judge = nullptr;  // per-block residual and opinion sums of the warm-start judge
+    int64_t cap_judge = 0;
     double *zhat = nullptr; // estimate of z' (FP64)
     double *sp = nullptr;   // s' = s + c_eff (FP64)
     double *sin = nullptr;  // caller's s, z0 or z staged on the device

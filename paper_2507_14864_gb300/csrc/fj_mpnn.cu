@@ -863,7 +863,7 @@ fj_status grow(T **p, int64_t count)
 {
     dev_free(*p);
     *p = nullptr;
-    FJ_CUDA(cudaMalloc(p, sizeof(T) * (size_t)std::max<int64_t>(count, 1)));
+    FJ_CUDA(dev_malloc(p, sizeof(T) * (size_t)std::max<int64_t>(count, 1)));
     return FJ_OK;
 }
 

@@ -30,6 +30,18 @@ __device__ __forceinline__ unsigned long long st_read(const unsigned long long *
     return w;
 }
 
+// Polls a tile's status word until the tile has published it (flag bits
+// set), at most `limit` times; false when it gave up.
+__device__ __forceinline__ bool wait_published(const unsigned long long *st, long long limit, unsigned long long &w)
+{
+    for (long long spins = 0;; ++spins) {
+        w = st_read(st);
+        if (w >> kStFlagShift) return true;
+        if (spins >= limit) return false;
+        __nanosleep(32);
+    }
+}
+
 // Called by one thread per tile.  Publishes the tile aggregate, walks back to
 // the nearest inclusive prefix and returns this tile's exclusive prefix.
 static __device__ __noinline__ long long lookback_prefix(unsigned long long *status, int tile, long long agg,
@@ -44,16 +56,9 @@ static __device__ __noinline__ long long lookback_prefix(unsigned long long *sta
     int p = tile - 1;
     while (p >= 0) {
         unsigned long long w;
-        long long spins = 0;
-        for (;;) {
-            w = st_read(&status[p]);
-            if (w >> kStFlagShift) break;
-            if (++spins > kSpinLimit) {
-                dev_error(err, DEV_SPIN_TIMEOUT);
-                w = kStPrefix;  // give up: treat as a zero prefix
-                break;
-            }
-            __nanosleep(32);
+        if (!wait_published(&status[p], kSpinLimit, w)) {
+            dev_error(err, DEV_SPIN_TIMEOUT);
+            w = kStPrefix;  // give up: treat as a zero prefix
         }
         excl += (long long)(w & kStValMask);
         if ((w >> kStFlagShift) == 2) break;

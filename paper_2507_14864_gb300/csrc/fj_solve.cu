@@ -14,6 +14,7 @@
 // step in pull form: when row x is visited it adds sum_j a_xj delta_j over
 // its row.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -200,113 +201,107 @@ __device__ long long g_fj_dbg[4];
                 ? (g_fj_dbg[1] = blockIdx.x, g_fj_dbg[2] = (long long)(idx), g_fj_dbg[3] = (long long)(lim), false) \
                 : false))
 
-// Products of a colour class: prod[k] = a_k * delta_{col[k]} for the class's
-// nonzeros [k0, k1), with delta taken from dcur for an earlier class (column
-// below lo) and from dprev otherwise.  An elementwise pass over the class's
-// nonzeros at full occupancy with several gathers in flight per thread: the
-// random 4-byte gathers bound the whole sweep, and this shape keeps the most
-// of them in flight.
-template <typename T, bool W>
-__global__ void __launch_bounds__(256)
-k_products(int64_t k0, int64_t k1, const int32_t *__restrict__ col, const float *__restrict__ w, int lo,
-           const T *__restrict__ dcur, const T *__restrict__ dprev, T *__restrict__ prod, int64_t n_rows,
-           const Counters *ctr)
-{
-    if (*reinterpret_cast<const volatile int *>(&ctr->done)) return;
-    constexpr int U = 4;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = k0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; base < k1; base += stride * U) {
-        int32_t j[U];
-        T a[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int64_t k = base + u * stride;
-            j[u] = -1;
-            a[u] = T(0);
-            if (k < k1) {
-                j[u] = __ldg(col + k);
-                a[u] = arc_w<T, W>(w, k);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int64_t k = base + u * stride;
-            if (k < k1) {
-                T x = T(0);
-                if (FJ_IDX_OK(15, j[u], n_rows)) x = (j[u] < lo) ? __ldg(dcur + j[u]) : __ldg(dprev + j[u]);
-                prod[k] = a[u] * x;
-            }
-        }
-    }
-}
+// ============================================================== fused sweep
 
 // One colour class of a sweep (Theorem 2's Gauss-Seidel order realised by
 // colour classes taken in turn; the whole graph as one class is a synchronous
-// round).  For every row x of the class:
+// round) in one pass: for every row x of the class,
 //   r_x += sum_j a_xj delta_j, then if |r_x| > h_x push x (Eqs. sor1-sor3):
 //   delta = omega_x r_x / (1 + d_x), zhat_x += delta, r_x <- (1 - omega_x) r_x.
 // delta_j is node j's latest increment in the sweep order: for j in an
-// earlier class (j < lo; those classes ran in earlier launches of this sweep)
-// the one made in this sweep, in dcur; for j in this or a later class the one
+// earlier class (those classes ran in earlier launches of this sweep) the
+// one made in this sweep, in dcur; for j in this or a later class the one
 // made in the previous sweep, in dprev.  Every row writes its own increment
 // (0 when it does not push) into dcur.
 //
-// The grid is persistent (as many blocks as can be resident); warp w of W
-// takes the class's work items w, w + W, ...: a tile of at most 2 * kSweepNnz
-// nonzeros (32 per lane) and kSweepRows rows (two per lane), a lane walking
-// each of its rows (the warp together for rows over 32 nonzeros), or a
-// kSweepChunk chunk of a long row whose
-// last chunk to finish sums the chunks' partials and applies the update.
-// The products a_xj delta_j come precomputed (k_products); while a warp works
-// on one item, the products of its next item stream into shared memory by
-// asynchronous 16-byte copies (cp.async), so the stream does not pause
-// between items.
-constexpr int kWE = 2 * kSweepNnz / 32;            // nonzeros per lane of a tile
-constexpr int kWR = kSweepRows / 32;               // rows per lane of a tile
-// warps per block: four, two for FP64 (static shared memory stays under 48 KB)
-template <typename T>
-constexpr int sweep_warps() { return sizeof(T) == 8 ? 2 : 4; }
-constexpr int kStage = 2 * kSweepNnz + 8;          // staged elements per item (tile rounded out to granules)
-static_assert(kSweepChunk <= 2 * kSweepNnz, "a chunk is staged like a tile");
+// A persistent warp takes the class's sweep tiles (at most 64 rows and 1024
+// nonzeros; a longer row is cut into 1024-nonzero chunks) in a fixed order.
+// For a tile, lane l handles elements e = 32 c + l: it loads all of its
+// columns at once (coalesced), then issues every increment gather as a 4- or
+// 8-byte asynchronous copy (cp.async) into the warp's value buffer in shared
+// memory, so a lane has up to 32 gathers in flight without holding them in
+// registers.  While they fly, the warp loads its rows' state and builds the
+// tile's start map (bit e set where a non-empty row begins).  Then the row
+// sums come from a segmented inclusive scan of each 32-element chunk across
+// the warp; the lane that ends a segment adds it to its row's accumulator in
+// shared memory.  The chunks are taken in order, so every row sum is formed
+// in one fixed order (deterministic).  Finally lane l applies the update to
+// rows r0 + l and r0 + l + 32.  Weights (weighted graphs) are copied into a
+// second buffer by 16-byte asynchronous copies.
+//
+// Hot table: node ids below nhot (the hub prefix of the colour order: the
+// nodes of largest in-degree, ordered by class) have their increments staged
+// in shared memory when the block starts, from this sweep's buffer for ids
+// below hlo (hubs of earlier classes) and the previous sweep's otherwise, so
+// that the gathers most rows make (a few percent of the nodes draw about a
+// third of the gathers on an R-MAT graph) are shared-memory loads.
+constexpr int kTileNnz = 2 * kSweepNnz;  // largest tile or chunk (1024)
+static_assert(kSweepChunk <= kTileNnz, "a chunk fits the value buffer");
+constexpr int kFusedSmemBudget = 227 * 1024 - 4096;  // dynamic shared memory of a block
 
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+template <typename T, bool W>
+__host__ __device__ constexpr int fused_warps() { return sizeof(T) == 4 ? 20 : 12; }
+
+// Per-warp shared memory of the fused sweep: values, weights (weighted
+// graphs, with one 16-byte granule of slack), start map, row accumulators.
+template <typename T, bool W>
+__host__ __device__ constexpr int fused_warp_bytes()
+{
+    return kTileNnz * (int)sizeof(T) + (W ? (kTileNnz + 4) * 4 : 0) + 32 * 4 + kSweepRows * (int)sizeof(T);
+}
+
+template <typename T, bool W>
+__host__ __device__ constexpr int fused_hot_cap()
+{
+    return (kFusedSmemBudget - fused_warps<T, W>() * fused_warp_bytes<T, W>()) / (int)sizeof(T);
+}
+
+__device__ __forceinline__ int32_t ld_stream_i32(const int32_t *p)
+{
+    int32_t v;
+    asm("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
+template <int N>
+__device__ __forceinline__ void cp_async_ca(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(s), "l"(gmem), "n"(N) : "memory");
+}
+__device__ __forceinline__ void cp_async_cg16(void *smem, const void *gmem)
 {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait()
-{
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
-// Copy the products of [k0, k1) into a stage in 16-byte granules from k0
-// rounded down to a granule; element k lands at index k - kb.
-template <typename T>
-__device__ __forceinline__ void stage_item(int64_t k0, int64_t k1, const T *__restrict__ prod, T *sp, int lane)
-{
-    constexpr int G = 16 / (int)sizeof(T);  // elements per granule
-    const int64_t kb = k0 & ~int64_t(G - 1);
-    const int ng = (int)((k1 - kb + G - 1) / G);
-    for (int g = lane; g < ng; g += 32) cp_async16(sp + G * g, prod + kb + G * g);
-}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 template <typename T, bool W>
-__global__ void __launch_bounds__(32 * sweep_warps<T>())
-k_sweep(const Item *__restrict__ items, int64_t item0, int64_t nitems, const int64_t *__restrict__ rp,
-        const T *__restrict__ prod, T *dcur, T *__restrict__ r, const T *__restrict__ h, const T *__restrict__ inv,
-        double *__restrict__ zhat, const int32_t *__restrict__ indeg, const T *__restrict__ om,
-        const int32_t *__restrict__ slot_first, const int32_t *__restrict__ slot_nchunk, double *part, int32_t *cnt,
-        Counters *ctr, int64_t n_rows)
+__global__ void __launch_bounds__(32 * fused_warps<T, W>(), 1)
+k_sweep_fused(const Item *__restrict__ items, int64_t item0, int64_t nitems, const int64_t *__restrict__ rp,
+              const int32_t *__restrict__ col, const float *__restrict__ w, int lo, int nhot, int nhub, int hlo,
+              const T *dcur_in, const T *__restrict__ dprev, T *dcur, T *__restrict__ r, const T *__restrict__ h,
+              const T *__restrict__ inv, double *__restrict__ zhat, const int32_t *__restrict__ indeg,
+              const T *__restrict__ om, const int32_t *__restrict__ slot_first,
+              const int32_t *__restrict__ slot_nchunk, double *part, int32_t *cnt, Counters *ctr, int64_t n_rows)
 {
-    constexpr int kSweepWarps = sweep_warps<T>();
-    constexpr int G = 16 / (int)sizeof(T);
-    __shared__ __align__(16) T sprod[kSweepWarps][2][kStage];
-    __shared__ unsigned long long red[2][kSweepWarps];
+    constexpr int NW = fused_warps<T, W>();
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr int NCH = kTileNnz / 32;  // chunks of a full tile
+    __shared__ unsigned long long red[2][NW];
     __shared__ int sbad;
+    extern __shared__ __align__(16) unsigned char fused_dyn[];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    unsigned char *mine = fused_dyn + (size_t)wl * fused_warp_bytes<T, W>();
+    T *vals = reinterpret_cast<T *>(mine);
+    float *wts = reinterpret_cast<float *>(mine + kTileNnz * sizeof(T));
+    unsigned *sbits = reinterpret_cast<unsigned *>(mine + kTileNnz * sizeof(T) + (W ? (kTileNnz + 4) * 4 : 0));
+    T *sacc = reinterpret_cast<T *>(sbits + 32);
+    T *hot = reinterpret_cast<T *>(fused_dyn + (size_t)NW * fused_warp_bytes<T, W>());
     if (*reinterpret_cast<volatile int *>(&ctr->done)) return;
+    for (int i = threadIdx.x; i < nhot; i += blockDim.x) hot[i] = i < hlo ? dcur_in[i] : dprev[i];
+    __syncthreads();
     unsigned long long my_push = 0, my_edges = 0;
     bool bad = false;
 
@@ -314,7 +309,7 @@ k_sweep(const Item *__restrict__ items, int64_t item0, int64_t nitems, const int
         T dx = T(0);
         if (abs_t(rx) > hx) {
             dx = ox * rx * ix;
-            zhat[x] += (double)dx;  // read only when the row pushes
+            zhat[x] += (double)dx;
             rx = (T(1) - ox) * rx;
             my_push += 1;
             my_edges += (unsigned long long)dgx;
@@ -323,139 +318,166 @@ k_sweep(const Item *__restrict__ items, int64_t item0, int64_t nitems, const int
         r[x] = rx;
         dcur[x] = dx;
     };
+    // where node j's increment is: this sweep's buffer for an earlier class,
+    // else the previous sweep's (hub ids are ordered by class among
+    // themselves, so a hub is in an earlier class when it is below hlo)
+    auto src_of = [&](int32_t j) -> const T * {
+        const bool earlier = j < nhub ? j < hlo : j < lo;
+        return (earlier ? dcur_in : dprev) + j;
+    };
 
-    const int64_t nwarps = (int64_t)gridDim.x * kSweepWarps;
+    const int64_t nwarps = (int64_t)gridDim.x * NW;
     const int64_t iend = item0 + nitems;
-    int64_t ii = item0 + (int64_t)blockIdx.x * kSweepWarps + wl;
-    int s = 0;
-    Item cur;
-    if (ii < iend) {
-        cur = items[ii];
-        stage_item<T>(cur.k0, cur.k1, prod, sprod[wl][0], lane);
-    }
-    cp_async_commit();
+    int64_t ii = item0 + (int64_t)blockIdx.x * NW + wl;
+    Item nxt;
+    if (ii < iend) nxt = items[ii];
     for (; ii < iend; ii += nwarps) {
-        // stream the next item in while this one is processed
-        const int64_t in = ii + nwarps;
-        Item nxt = cur;
-        if (in < iend) {
-            nxt = items[in];
-            stage_item<T>(nxt.k0, nxt.k1, prod, sprod[wl][s ^ 1], lane);
-        }
-        cp_async_commit();
-        cp_async_wait<1>();
-        __syncwarp();
-        const Item it = cur;
+        const Item it = nxt;
+        if (ii + nwarps < iend) nxt = items[ii + nwarps];
         const int64_t r0 = it.r0, r1 = it.r1, k0 = it.k0;
         const int nz = (int)(it.k1 - k0);
-        const int off = (int)(k0 & (G - 1));
         const bool ok = FJ_IDX_OK(11, r0, n_rows) && FJ_IDX_OK(12, r1, n_rows + 1) &&
-                        FJ_IDX_OK(13, r1 - r0, kSweepRows + 1) && FJ_IDX_OK(17, nz, kStage - 3);
-        if (ok) {
-            const T *sc = sprod[wl][s] + off;
-            if (it.slot < 0) {
-                // ---- tile: a lane owns rows r0 + lane and r0 + lane + 32 and walks
-                // each one through the staged columns; rows longer than 32
-                // nonzeros are reduced by the whole warp
-                const int64_t kb = k0 & ~int64_t(G - 1);
-                const T *spb = sprod[wl][s];
-                int ra[kWR], re[kWR];
-                T rr[kWR], rh[kWR], ri[kWR], ro[kWR], acc[kWR];
-                int32_t rd[kWR];
+                        FJ_IDX_OK(13, r1 - r0, kSweepRows + 1) && FJ_IDX_OK(17, nz, kTileNnz + 1);
+        if (!ok) continue;
+        const int nch = (nz + 31) >> 5;
+        // ---- columns, then every gather as an asynchronous copy into vals
+        const int woff = (int)(k0 & 3);
+        if constexpr (W) {
+            const int64_t kb = k0 - woff;
+            const int ng = (woff + nz + 3) >> 2;
+            for (int gi = lane; gi < ng; gi += 32) cp_async_cg16(wts + 4 * gi, w + kb + 4 * gi);
+        }
+        {
+            int32_t jj[NCH];
 #pragma unroll
-                for (int q = 0; q < kWR; ++q) {
-                    const int64_t x = r0 + lane + 32 * q;
-                    ra[q] = re[q] = 0;
-                    rr[q] = rh[q] = ri[q] = ro[q] = acc[q] = T(0);
-                    rd[q] = 0;
-                    if (x < r1) {
-                        ra[q] = (int)(rp[x] - kb);
-                        re[q] = (int)(rp[x + 1] - kb);
-                        rr[q] = r[x];
-                        rh[q] = h[x];
-                        ri[q] = inv[x];
-                        ro[q] = om[x];
-                        rd[q] = indeg[x];
-                    }
+            for (int c = 0; c < NCH; ++c) {
+                if (c < nch) {
+                    const int e = 32 * c + lane;
+                    jj[c] = e < nz ? ld_stream_i32(col + k0 + e) : -1;
                 }
-                auto term = [&](int k) -> T { return spb[k]; };
-                unsigned longrows = 0;  // bit q: this lane's row q is reduced by the warp
+            }
 #pragma unroll
-                for (int q = 0; q < kWR; ++q) {
-                    const int len = re[q] - ra[q];
-                    if (len > 32) {
-                        longrows |= 1u << q;
-                    } else if (len > 0 && FJ_IDX_OK(16, re[q], kStage + 1) && FJ_IDX_OK(18, ra[q], kStage)) {
-                        T s0 = T(0), s1 = T(0);
-                        int k = ra[q];
-                        for (; k + 1 < re[q]; k += 2) {
-                            s0 += term(k);
-                            s1 += term(k + 1);
-                        }
-                        if (k < re[q]) s0 += term(k);
-                        acc[q] = s0 + s1;
-                    }
+            for (int c = 0; c < NCH; ++c) {
+                if (c < nch) {
+                    const int e = 32 * c + lane;
+                    const int32_t j = jj[c];
+                    if ((unsigned)j < (unsigned)nhot) vals[e] = hot[j];
+                    else if (j >= 0 && FJ_IDX_OK(15, j, n_rows)) cp_async_ca<(int)sizeof(T)>(vals + e, src_of(j));
+                    else vals[e] = T(0);
                 }
+            }
+            cp_async_commit();
+        }
+        if (it.slot < 0) {
+            // ---- tile: row state, start map and ranks while the gathers fly
+            int ra[2], re[2], rk[2];
+            T rr[2], rh[2], ri[2], ro[2];
+            int32_t rd[2];
+            sbits[lane] = 0u;
+            sacc[lane] = T(0);
+            sacc[lane + 32] = T(0);
+            __syncwarp();
 #pragma unroll
-                for (int q = 0; q < kWR; ++q) {
-                    unsigned m = __ballot_sync(0xffffffffu, (longrows >> q) & 1u);
-                    while (m) {
-                        const int src = __ffs(m) - 1;
-                        m &= m - 1;
-                        const int a = __shfl_sync(0xffffffffu, ra[q], src);
-                        const int e = __shfl_sync(0xffffffffu, re[q], src);
-                        T part_sum = T(0);
-                        if (FJ_IDX_OK(19, e, kStage + 1))
-                            for (int k = a + lane; k < e; k += 32) part_sum += term(k);
-                        part_sum = warp_sum(part_sum);
-                        if (lane == src) acc[q] = part_sum;
-                    }
+            for (int q = 0; q < 2; ++q) {
+                const int64_t x = r0 + lane + 32 * q;
+                ra[q] = re[q] = 0;
+                rk[q] = -1;
+                rr[q] = rh[q] = ri[q] = ro[q] = T(0);
+                rd[q] = 0;
+                if (x < r1) {
+                    ra[q] = (int)(rp[x] - k0);
+                    re[q] = (int)(rp[x + 1] - k0);
+                    rr[q] = r[x];
+                    rh[q] = h[x];
+                    ri[q] = inv[x];
+                    ro[q] = om[x];
+                    rd[q] = indeg[x];
+                    if (re[q] > ra[q] && FJ_IDX_OK(18, ra[q], nz) && FJ_IDX_OK(16, re[q], nz + 1))
+                        atomicOr(&sbits[ra[q] >> 5], 1u << (ra[q] & 31));
+                    else
+                        re[q] = ra[q];  // empty (or rejected) row: no sum
                 }
+            }
+            __syncwarp();
+            const unsigned myword = sbits[lane];
+            // exclusive prefix of the start counts over the 32 words (lane = word)
+            int incl = __popc(myword);
 #pragma unroll
-                for (int q = 0; q < kWR; ++q) {
-                    const int64_t x = r0 + lane + 32 * q;
-                    if (x < r1) apply(x, rr[q] + acc[q], rh[q], ri[q], ro[q], rd[q]);
-                }
-            } else {
-                // ---- chunk of a long row: partial sum; the last chunk applies the update
-                T acc = T(0);
+            for (int d = 1; d < 32; d <<= 1) {
+                const int y = __shfl_up_sync(FULL, incl, d);
+                if (lane >= d) incl += y;
+            }
+            const int wpre = incl - __popc(myword);
 #pragma unroll
-                for (int e = 0; e < kWE; ++e) {
-                    const int i = lane + 32 * e;
-                    if (i < nz) acc += sc[i];
+            for (int q = 0; q < 2; ++q) {
+                const int wsrc = (ra[q] >> 5) & 31;
+                const int base = __shfl_sync(FULL, wpre, wsrc);
+                if (re[q] > ra[q]) rk[q] = base + __popc(sbits[wsrc] & ((1u << (ra[q] & 31)) - 1u));
+            }
+            cp_async_wait_all();
+            __syncwarp();
+            // ---- segmented sums, chunk by chunk
+            for (int c = 0; c < nch; ++c) {
+                const int e = 32 * c + lane;
+                T x = vals[e];
+                if constexpr (W) x = e < nz ? x * (T)wts[e + woff] : T(0);  // past nz the weight slot is unset
+                const unsigned word = sbits[c];
+                const unsigned le = word & (FULL >> (31 - lane));
+                const int ss = le ? 31 - __clz(le) : 0;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const T y = __shfl_up_sync(FULL, x, d);
+                    if (lane - d >= ss) x += y;
                 }
-                acc = warp_sum(acc);
-                const int slot = it.slot;
-                const int first = slot_first[slot], nch = slot_nchunk[slot];
-                int last = 0;
+                const int rank = __shfl_sync(FULL, wpre, c) + __popc(le) - 1;
+                const bool end = lane == 31 || ((word >> (lane + 1)) & 1u);
+                if (end && FJ_IDX_OK(19, rank, kSweepRows)) sacc[rank] += x;
+                __syncwarp();
+            }
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int64_t x = r0 + lane + 32 * q;
+                if (x < r1) apply(x, rr[q] + (rk[q] >= 0 ? sacc[rk[q]] : T(0)), rh[q], ri[q], ro[q], rd[q]);
+            }
+        } else {
+            // ---- chunk of a long row: partial sum; the last chunk applies the update
+            cp_async_wait_all();
+            __syncwarp();
+            T acc = T(0);
+            for (int c = 0; c < nch; ++c) {
+                const int e = 32 * c + lane;
+                T x = vals[e];
+                if constexpr (W) x = e < nz ? x * (T)wts[e + woff] : T(0);  // past nz the weight slot is unset
+                acc += x;
+            }
+            acc = warp_sum(acc);
+            const int slot = it.slot;
+            const int first = slot_first[slot], nchunk = slot_nchunk[slot];
+            int last = 0;
+            if (lane == 0) {
+                const int ci = (int)((k0 - rp[r0]) / kSweepChunk);
+                part[first + ci] = (double)acc;
+                __threadfence();
+                last = atomicAdd(&cnt[slot], 1) == nchunk - 1;
+            }
+            last = __shfl_sync(FULL, last, 0);
+            if (last) {
+                __threadfence();
+                double sum = 0.0;
+                for (int c = lane; c < nchunk; c += 32) sum += __ldcg(part + first + c);
+                sum = warp_sum(sum);
                 if (lane == 0) {
-                    const int ci = (int)((k0 - rp[r0]) / kSweepChunk);
-                    part[first + ci] = (double)acc;
-                    __threadfence();
-                    last = atomicAdd(&cnt[slot], 1) == nch - 1;
-                }
-                last = __shfl_sync(0xffffffffu, last, 0);
-                if (last) {
-                    __threadfence();
-                    double sum = 0.0;
-                    for (int c = lane; c < nch; c += 32) sum += __ldcg(part + first + c);
-                    sum = warp_sum(sum);
-                    if (lane == 0) {
-                        cnt[slot] = 0;
-                        apply(r0, r[r0] + (T)sum, h[r0], inv[r0], om[r0], indeg[r0]);
-                    }
+                    cnt[slot] = 0;
+                    apply(r0, r[r0] + (T)sum, h[r0], inv[r0], om[r0], indeg[r0]);
                 }
             }
         }
-        __syncwarp();  // the stage of this item is refilled two items from now
-        cur = nxt;
-        s ^= 1;
+        __syncwarp();  // the buffers are refilled by the next item
     }
-    cp_async_wait<0>();
     // block totals -> three atomics per block
     my_push = warp_sum(my_push);
     my_edges = warp_sum(my_edges);
-    const unsigned anybad = __ballot_sync(0xffffffffu, bad);
+    const unsigned anybad = __ballot_sync(FULL, bad);
     if (threadIdx.x == 0) sbad = 0;
     __syncthreads();
     if (lane == 0) {
@@ -466,7 +488,7 @@ k_sweep(const Item *__restrict__ items, int64_t item0, int64_t nitems, const int
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned long long pp = 0, ee = 0;
-        for (int i = 0; i < kSweepWarps; ++i) {
+        for (int i = 0; i < NW; ++i) {
             pp += red[0][i];
             ee += red[1][i];
         }
@@ -898,7 +920,7 @@ k_frontier_push(const int32_t *__restrict__ list, const long long *__restrict__ 
         if (lane == 0) my_edges += (unsigned long long)(a1 - a0);
     }
     my_edges = warp_sum(my_edges);
-    if (lane == 0 && my_edges) atomicAdd(&ctr->edges, my_edges);
+    if (lane == 0 && my_edges) atomicAdd(&ctr->fedges, my_edges);
 }
 
 // ============================================================== frontier
@@ -928,6 +950,93 @@ __global__ void k_residual(int64_t n, const int64_t *__restrict__ rp, const int3
     }
 }
 
+// ============================================================== warm-start judge
+
+// The zero start is the judge of a warm start (its fallback).  The push's
+// work is driven down by the residual sum (the running-time argument of
+// Section 5.1.2, Theorem 1), so a start z0 is kept only when its exact
+// residual sum, sum_v |r_v| of r = s' - (I + L)(z0 + c_eff), is below the
+// zero start's, sum_v s'_v.  Per right-hand side j (node-major [n][k]),
+// block b writes its two sums to part[(j * gridDim.x + b) * 2 + {0, 1}], each
+// in a fixed order; the host adds the blocks in order (deterministic).
+constexpr int kJudgeBlocks = 256;
+
+__global__ void __launch_bounds__(256)
+k_warm_judge(int64_t n, int k, const double *__restrict__ r64, const double *__restrict__ sp, double *__restrict__ part)
+{
+    __shared__ double sa[8], sb[8];
+    const int j = blockIdx.y;
+    double a = 0.0, b = 0.0;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        a += fabs(r64[v * k + j]);
+        b += sp[v * k + j];
+    }
+    a = warp_sum(a);
+    b = warp_sum(b);
+    if ((threadIdx.x & 31) == 0) {
+        sa[threadIdx.x >> 5] = a;
+        sb[threadIdx.x >> 5] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ta = 0.0, tb = 0.0;
+        for (int i = 0; i < 8; ++i) {
+            ta += sa[i];
+            tb += sb[i];
+        }
+        part[((int64_t)j * gridDim.x + blockIdx.x) * 2] = ta;
+        part[((int64_t)j * gridDim.x + blockIdx.x) * 2 + 1] = tb;
+    }
+}
+
+// Right-hand sides whose start lost to the zero start restart from zero: the
+// state a zero start's initialisation gives (zhat' = 0, r = s').
+template <typename T>
+__global__ void k_zero_start_cols(int64_t n, int k, const int *__restrict__ cold, const double *__restrict__ sp,
+                                  double *__restrict__ zhat, T *__restrict__ r, double *__restrict__ r64,
+                                  T *__restrict__ da, T *__restrict__ db)
+{
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n * k;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(idx % k);
+        if (!cold[j]) continue;
+        zhat[idx] = 0.0;
+        r[idx] = (T)sp[idx];
+        r64[idx] = sp[idx];
+        da[idx] = T(0);
+        db[idx] = T(0);
+    }
+}
+
+// keep[j] = 1 when start j beats the zero start (see k_warm_judge).
+static fj_status warm_judge(fj_graph *g, int64_t n, int k, const double *r64, const double *sp, cudaStream_t st,
+                            std::vector<int> &keep)
+{
+    Workspace &ws = g->ws;
+    const int64_t need = (int64_t)kJudgeBlocks * k * 2;
+    if (need + 64 > ws.cap_judge) {  // the sums, then room for 64 restart flags
+        dev_free(ws.judge);
+        ws.judge = nullptr;
+        FJ_CUDA(dev_malloc(&ws.judge, sizeof(double) * (size_t)(need + 64)));
+        ws.cap_judge = need + 64;
+    }
+    k_warm_judge<<<dim3(kJudgeBlocks, k), 256, 0, st>>>(n, k, r64, sp, ws.judge);
+    FJ_CUDA(cudaGetLastError());
+    std::vector<double> h((size_t)need);
+    FJ_CUDA(cudaMemcpyAsync(h.data(), ws.judge, sizeof(double) * (size_t)need, cudaMemcpyDeviceToHost, st));
+    FJ_CUDA(cudaStreamSynchronize(st));
+    keep.assign((size_t)k, 0);
+    for (int j = 0; j < k; ++j) {
+        double a = 0.0, b = 0.0;
+        for (int bl = 0; bl < kJudgeBlocks; ++bl) {
+            a += h[((size_t)j * kJudgeBlocks + bl) * 2];
+            b += h[((size_t)j * kJudgeBlocks + bl) * 2 + 1];
+        }
+        keep[(size_t)j] = (std::isfinite(a) && a < b) ? 1 : 0;
+    }
+    return FJ_OK;
+}
+
 // ============================================================== host driver
 
 template <typename T>
@@ -939,20 +1048,20 @@ static fj_status ws_grow(fj_graph *g, int64_t entries, int ngraphs)
         for (void **p : bufs) {
             dev_free(*p);
             *p = nullptr;
-            FJ_CUDA(cudaMalloc(p, sizeof(double) * (size_t)entries));
+            FJ_CUDA(dev_malloc(p, sizeof(double) * (size_t)entries));
         }
         double **dbufs[] = {&ws.zhat, &ws.sp, &ws.sin, &ws.zout, &ws.r64};
         for (double **p : dbufs) {
             dev_free(*p);
             *p = nullptr;
-            FJ_CUDA(cudaMalloc(p, sizeof(double) * (size_t)entries));
+            FJ_CUDA(dev_malloc(p, sizeof(double) * (size_t)entries));
         }
         dev_free(ws.list);
         ws.list = nullptr;
-        FJ_CUDA(cudaMalloc(&ws.list, sizeof(int32_t) * (size_t)entries));
+        FJ_CUDA(dev_malloc(&ws.list, sizeof(int32_t) * (size_t)entries));
         dev_free(ws.zs);
         ws.zs = nullptr;
-        FJ_CUDA(cudaMalloc(&ws.zs, sizeof(float2) * (size_t)entries));
+        FJ_CUDA(dev_malloc(&ws.zs, sizeof(float2) * (size_t)entries));
         ws.cap_n = entries;
         ws.gen++;
     }
@@ -961,23 +1070,15 @@ static fj_status ws_grow(fj_graph *g, int64_t entries, int ngraphs)
         ws.gstat = nullptr;
         if (ws.gstat_host) cudaFreeHost(ws.gstat_host);
         ws.gstat_host = nullptr;
-        FJ_CUDA(cudaMalloc(&ws.gstat, sizeof(double) * kGs * ngraphs));
+        FJ_CUDA(dev_malloc(&ws.gstat, sizeof(double) * kGs * ngraphs));
         FJ_CUDA(cudaMallocHost(&ws.gstat_host, sizeof(double) * kGs * ngraphs));
         ws.cap_graphs = ngraphs;
     }
-    const int64_t need_prod = g->csr.nnz + kNnzPad;
-    if (need_prod > ws.cap_prod) {
-        dev_free(ws.prod);
-        ws.prod = nullptr;
-        FJ_CUDA(cudaMalloc(&ws.prod, sizeof(double) * (size_t)need_prod));
-        ws.cap_prod = need_prod;
-        ws.gen++;
-    }
     if (!ws.ctr) {
-        FJ_CUDA(cudaMalloc(&ws.ctr, sizeof(Counters)));
+        FJ_CUDA(dev_malloc(&ws.ctr, sizeof(Counters)));
         FJ_CUDA(cudaMallocHost(&ws.ctr_host, sizeof(Counters)));
     }
-    if (!ws.zmax) FJ_CUDA(cudaMalloc(&ws.zmax, sizeof(unsigned long long)));
+    if (!ws.zmax) FJ_CUDA(dev_malloc(&ws.zmax, sizeof(unsigned long long)));
     return FJ_OK;
 }
 
@@ -1061,11 +1162,14 @@ __global__ void k_gather_rp(int64_t nb, const int32_t *__restrict__ blk_row, con
         out[b] = rp[blk_row[b]];
 }
 
-// Work items of a CSR in row order: every row block, with rows longer than
-// two staged tiles cut into kChunkNnz chunks.  class_row (multicolour) gives
-// each item the first row of its colour class; without it every item gets 0.
-static fj_status build_items(fj_graph *g, const DevCSR &c, const std::vector<int64_t> *class_row, ItemPlan &ip,
-                             cudaStream_t st, TileKind kind)
+// Work items of a CSR: every row block, with rows longer than two tiles cut
+// into chunks, grouped by colour class (items of class c are
+// [class_item[c], class_item[c+1]), in row order inside the class: first the
+// class's hub rows, then its other rows).  With a colouring (multicolour)
+// each item carries the first row of its class, the first hub row of its
+// class and the hub count; without one every item is in the one class 0.
+static fj_status build_items(fj_graph *g, const DevCSR &c, const Colouring *cl, ItemPlan &ip, cudaStream_t st,
+                             TileKind kind)
 {
     const bool sweep_tiles = kind == kTileSweep, warp_tiles = kind == kTileWarp;
     const int64_t nb = sweep_tiles ? c.nsblocks : (warp_tiles ? c.nwblocks : c.nblocks);
@@ -1075,7 +1179,7 @@ static fj_status build_items(fj_graph *g, const DevCSR &c, const std::vector<int
     std::vector<int32_t> br((size_t)nb + 1);
     std::vector<long long> bk((size_t)nb + 1);
     long long *bk_d = nullptr;
-    FJ_CUDA(cudaMalloc(&bk_d, sizeof(long long) * (nb + 1)));
+    FJ_CUDA(dev_malloc(&bk_d, sizeof(long long) * (nb + 1)));
     k_gather_rp<<<grid_for(nb + 1, 256), 256, 0, st>>>(nb, blk_row, c.row_ptr, bk_d);
     FJ_CUDA(cudaGetLastError());
     FJ_CUDA(cudaMemcpyAsync(br.data(), blk_row, sizeof(int32_t) * (nb + 1), cudaMemcpyDeviceToHost, st));
@@ -1083,18 +1187,28 @@ static fj_status build_items(fj_graph *g, const DevCSR &c, const std::vector<int
     FJ_CUDA(cudaStreamSynchronize(st));
     dev_free(bk_d);
     std::vector<Item> items;
+    std::vector<int32_t> icls;  // class of every item
     std::vector<int32_t> sfirst, snch;
     items.reserve((size_t)nb + 16);
     int64_t nparts = 0;
-    size_t cls = 0;
+    const int ncls = cl ? cl->ncolours : 1;
+    auto class_of = [&](int64_t x) -> int {
+        if (!cl) return 0;
+        const std::vector<int64_t> &bnd = x < cl->nhub ? cl->hub_row : cl->class_row;
+        return (int)(std::upper_bound(bnd.begin(), bnd.end(), x) - bnd.begin()) - 1;
+    };
     for (int64_t b = 0; b < nb; ++b) {
         Item it;
         it.r0 = br[(size_t)b];
         it.r1 = br[(size_t)b + 1];
         it.lo = 0;
-        if (class_row) {
-            while (cls + 1 < class_row->size() && (*class_row)[cls + 1] <= it.r0) ++cls;
-            it.lo = (int32_t)(*class_row)[cls];
+        it.hlo = 0;
+        it.nhub = 0;
+        const int cls = std::min(std::max(class_of(it.r0), 0), ncls - 1);
+        if (cl) {
+            it.lo = (int32_t)cl->class_row[(size_t)cls];
+            it.nhub = (int32_t)cl->nhub;
+            it.hlo = cl->nhub > 0 ? (int32_t)cl->hub_row[(size_t)cls] : 0;
         }
         const int64_t k0 = bk[(size_t)b], k1 = bk[(size_t)b + 1];
         if (k1 - k0 > long_row) {
@@ -1107,56 +1221,34 @@ static fj_status build_items(fj_graph *g, const DevCSR &c, const std::vector<int
                 it.k0 = k0 + ch * chunk;
                 it.k1 = std::min(k1, it.k0 + chunk);
                 items.push_back(it);
+                icls.push_back(cls);
             }
         } else {
             it.slot = -1;
             it.k0 = k0;
             it.k1 = k1;
             items.push_back(it);
+            icls.push_back(cls);
         }
     }
     ip.nitems = (int64_t)items.size();
     ip.nslots = (int64_t)sfirst.size();
-    // first item of every colour class (the items are in row order, the rows in class order)
-    ip.class_item.clear();
-    if (class_row) {
-        size_t at = 0;
-        for (size_t k = 0; k + 1 < class_row->size(); ++k) {
-            while (at < items.size() && items[at].r0 < (*class_row)[k]) ++at;
-            ip.class_item.push_back((int64_t)at);
-        }
-    } else {
-        ip.class_item.push_back(0);
+    // group by class, stable (a class's hub items come before its other items)
+    ip.class_item.assign((size_t)ncls + 1, 0);
+    for (int32_t k : icls) ++ip.class_item[(size_t)k + 1];
+    for (int k = 0; k < ncls; ++k) ip.class_item[(size_t)k + 1] += ip.class_item[(size_t)k];
+    {
+        std::vector<int64_t> at(ip.class_item.begin(), ip.class_item.end() - 1);
+        std::vector<Item> grouped(items.size());
+        for (size_t i = 0; i < items.size(); ++i) grouped[(size_t)at[(size_t)icls[i]]++] = items[i];
+        items.swap(grouped);
     }
-    ip.class_item.push_back(ip.nitems);
-    ip.class_k.assign(ip.class_item.size(), bk.empty() ? 0 : bk.back());
-    for (size_t k = 0; k + 1 < ip.class_item.size(); ++k)
-        ip.class_k[k] = ip.class_item[k] < ip.nitems ? items[(size_t)ip.class_item[k]].k0 : bk.back();
-    // sweep segments: each class cut into item runs of at most kSegNnz nonzeros
-    ip.seg_item.clear();
-    ip.seg_k.clear();
-    ip.seg_class.clear();
-    for (size_t c = 0; c + 1 < ip.class_item.size(); ++c) {
-        int64_t i = ip.class_item[c];
-        const int64_t iend = ip.class_item[c + 1];
-        while (i < iend) {
-            const int64_t kstart = items[(size_t)i].k0;
-            int64_t j = i + 1;
-            while (j < iend && items[(size_t)j].k1 - kstart <= kSegNnz) ++j;
-            ip.seg_item.push_back(i);
-            ip.seg_k.push_back(kstart);
-            ip.seg_class.push_back((int32_t)c);
-            i = j;
-        }
-    }
-    ip.seg_item.push_back(ip.nitems);
-    ip.seg_k.push_back(ip.nitems > 0 ? items.back().k1 : 0);
     ip.nparts = nparts;
-    FJ_CUDA(cudaMalloc(&ip.items, sizeof(Item) * std::max<size_t>(items.size(), 1)));
-    FJ_CUDA(cudaMalloc(&ip.slot_first, sizeof(int32_t) * std::max<size_t>(sfirst.size(), 1)));
-    FJ_CUDA(cudaMalloc(&ip.slot_nchunk, sizeof(int32_t) * std::max<size_t>(snch.size(), 1)));
-    FJ_CUDA(cudaMalloc(&ip.cnt, sizeof(int32_t) * std::max<size_t>(sfirst.size(), 1)));
-    FJ_CUDA(cudaMalloc(&ip.part, 2 * sizeof(double) * std::max<int64_t>(nparts, 1)));
+    FJ_CUDA(dev_malloc(&ip.items, sizeof(Item) * std::max<size_t>(items.size(), 1)));
+    FJ_CUDA(dev_malloc(&ip.slot_first, sizeof(int32_t) * std::max<size_t>(sfirst.size(), 1)));
+    FJ_CUDA(dev_malloc(&ip.slot_nchunk, sizeof(int32_t) * std::max<size_t>(snch.size(), 1)));
+    FJ_CUDA(dev_malloc(&ip.cnt, sizeof(int32_t) * std::max<size_t>(sfirst.size(), 1)));
+    FJ_CUDA(dev_malloc(&ip.part, 2 * sizeof(double) * std::max<int64_t>(nparts, 1)));
     FJ_CUDA(cudaMemcpyAsync(ip.items, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice, st));
     if (!sfirst.empty()) {
         FJ_CUDA(cudaMemcpyAsync(ip.slot_first, sfirst.data(), sizeof(int32_t) * sfirst.size(), cudaMemcpyHostToDevice,
@@ -1184,9 +1276,8 @@ static fj_status make_plan(fj_graph *g, const fj_solve_opts *o, cudaStream_t st,
     FJ_CHECK(ensure_colouring(g, o->palette, st));
     p.c = &g->colr.pcsr;
     p.perm = g->colr.perm;
-    if (!g->wplan_pcsr.built) FJ_CHECK(build_items(g, g->colr.pcsr, &g->colr.class_row, g->wplan_pcsr, st, kTileWarp));
-    if (!g->splan_pcsr.built)
-        FJ_CHECK(build_items(g, g->colr.pcsr, &g->colr.class_row, g->splan_pcsr, st, kTileSweep));
+    if (!g->wplan_pcsr.built) FJ_CHECK(build_items(g, g->colr.pcsr, &g->colr, g->wplan_pcsr, st, kTileWarp));
+    if (!g->splan_pcsr.built) FJ_CHECK(build_items(g, g->colr.pcsr, &g->colr, g->splan_pcsr, st, kTileSweep));
     p.wip = &g->wplan_pcsr;
     p.sip = &g->splan_pcsr;
     return FJ_OK;
@@ -1201,72 +1292,71 @@ fj_status plain_items(fj_graph *g, cudaStream_t st, const ItemPlan **out)
     return FJ_OK;
 }
 
-// Resident blocks of the sweep kernel on this device (persistent grid size).
-template <typename T>
-static int64_t sweep_blocks(bool weighted)
+// Resident blocks of the fused sweep kernel on this device for dyn bytes of
+// dynamic shared memory (persistent grid size).  The first call per kernel
+// instance also allows it the whole shared-memory budget.
+template <typename T, bool W>
+static int64_t sweep_blocks(int dyn)
 {
-    static int cached[2] = {0, 0};
-    int &nres = cached[weighted ? 1 : 0];
-    if (nres == 0) {
-        int dev = 0, sms = 0, per = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess) return 152;
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        constexpr int kSweepWarps = sweep_warps<T>();
-        if (weighted) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep<T, true>, 32 * kSweepWarps, 0);
-        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep<T, false>, 32 * kSweepWarps, 0);
-        nres = std::max(1, sms * std::max(1, per));
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_sweep_fused<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFusedSmemBudget);
+        attr = true;
     }
-    return nres;
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep_fused<T, W>, 32 * fused_warps<T, W>(), dyn);
+    return std::max(1, sms * std::max(1, per));
 }
 
-// One sweep (multicolour: one launch per colour class, in order) or round
-// (Jacobi: one launch), then the stop test.  The two increment buffers swap
-// roles every sweep.
-template <typename T>
-static fj_status launch_sweep(fj_graph *g, const Plan &p, cudaStream_t st, Run &run, int64_t sweep)
+template <typename T, bool W>
+static fj_status launch_fused(fj_graph *g, const Plan &p, cudaStream_t st, Run &run, T *dcur, const T *dprev)
 {
     Workspace &ws = g->ws;
     const DevCSR &c = *p.c;
     const ItemPlan &wp = *p.sip;
-    T *bufs[2] = {reinterpret_cast<T *>(ws.da), reinterpret_cast<T *>(ws.db)};
-    T *dcur = bufs[sweep & 1];
-    const T *dprev = bufs[(sweep - 1) & 1];
     T *r = reinterpret_cast<T *>(ws.r);
     const T *h = reinterpret_cast<const T *>(ws.h);
     const T *inv;
     if constexpr (sizeof(T) == 4) inv = reinterpret_cast<const T *>(c.inv32);
     else inv = reinterpret_cast<const T *>(c.inv64);
     const T *om = reinterpret_cast<const T *>(ws.om);
-    T *prod = reinterpret_cast<T *>(ws.prod);
-    // segment by segment (a class cut into runs whose products stay in L2)
-    for (size_t sg = 0; sg + 1 < wp.seg_item.size(); ++sg) {
-        const int64_t i0 = wp.seg_item[sg], ni = wp.seg_item[sg + 1] - i0;
+    constexpr int NW = fused_warps<T, W>();
+    // hub prefix of the colour order (multicolour only): its first nhot ids go to the hot table
+    const int nhub = p.mc ? (int)g->colr.nhub : 0;
+    const int nhot = std::max(0, std::min<int>(nhub, fused_hot_cap<T, W>()));
+    const int dyn = NW * fused_warp_bytes<T, W>() + nhot * (int)sizeof(T);
+    const int64_t nres = sweep_blocks<T, W>(dyn);
+    for (size_t cl = 0; cl + 1 < wp.class_item.size(); ++cl) {
+        const int64_t i0 = wp.class_item[cl], ni = wp.class_item[cl + 1] - i0;
         if (ni <= 0) continue;
-        const int64_t kk0 = wp.seg_k[sg], kk1 = wp.seg_k[sg + 1];
-        // the class's first row: every column below it belongs to an earlier class
-        const int lo = p.mc ? (int)g->colr.class_row[(size_t)wp.seg_class[sg]] : 0;
-        const unsigned pgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(kk1 - kk0, 256 * 4), 152 * 8));
+        // the class's first row (first hub row): every column below it belongs to an earlier class
+        const int lo = p.mc ? (int)g->colr.class_row[cl] : 0;
+        const int hlo = nhub > 0 ? (int)g->colr.hub_row[cl] : 0;
+        const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(ni, NW), nres);
         FJ_CHECK(run.before(st));
-        if (c.w)
-            k_products<T, true><<<pgrid, 256, 0, st>>>(kk0, kk1, c.col, c.w, lo, dcur, dprev, prod, c.n, ws.ctr);
-        else
-            k_products<T, false><<<pgrid, 256, 0, st>>>(kk0, kk1, c.col, c.w, lo, dcur, dprev, prod, c.n, ws.ctr);
-        FJ_CUDA(cudaGetLastError());
-        constexpr int kSweepWarps = sweep_warps<T>();
-        const unsigned grid =
-            (unsigned)std::min<int64_t>(ceil_div(ni, kSweepWarps), sweep_blocks<T>(c.w != nullptr));
-        if (c.w)
-            k_sweep<T, true><<<grid, 32 * kSweepWarps, 0, st>>>(wp.items, i0, ni, c.row_ptr, prod, dcur, r, h, inv,
-                                                                ws.zhat, c.indeg, om, wp.slot_first, wp.slot_nchunk,
-                                                                wp.part, wp.cnt, ws.ctr, c.n);
-        else
-            k_sweep<T, false><<<grid, 32 * kSweepWarps, 0, st>>>(wp.items, i0, ni, c.row_ptr, prod, dcur, r, h, inv,
-                                                                 ws.zhat, c.indeg, om, wp.slot_first, wp.slot_nchunk,
-                                                                 wp.part, wp.cnt, ws.ctr, c.n);
+        k_sweep_fused<T, W><<<grid, 32 * NW, dyn, st>>>(wp.items, i0, ni, c.row_ptr, c.col, c.w, lo, nhot, nhub, hlo,
+                                                        dcur, dprev, dcur, r, h, inv, ws.zhat, c.indeg, om,
+                                                        wp.slot_first, wp.slot_nchunk, wp.part, wp.cnt, ws.ctr, c.n);
         FJ_CUDA(cudaGetLastError());
         FJ_CHECK(run.after(st));
-        ++run.launches;  // the products launch
     }
+    return FJ_OK;
+}
+
+// One sweep (multicolour: one launch per colour class, in order) or round
+// (Jacobi: one launch over all rows), then the stop test.  The two increment
+// buffers swap roles every sweep.
+template <typename T>
+static fj_status launch_sweep(fj_graph *g, const Plan &p, cudaStream_t st, Run &run, int64_t sweep)
+{
+    Workspace &ws = g->ws;
+    T *bufs[2] = {reinterpret_cast<T *>(ws.da), reinterpret_cast<T *>(ws.db)};
+    T *dcur = bufs[sweep & 1];
+    const T *dprev = bufs[(sweep - 1) & 1];
+    if (p.c->w) FJ_CHECK((launch_fused<T, true>(g, p, st, run, dcur, dprev)));
+    else FJ_CHECK((launch_fused<T, false>(g, p, st, run, dcur, dprev)));
     k_end_sweep<<<1, 1, 0, st>>>(ws.ctr);
     FJ_CUDA(cudaGetLastError());
     ++run.launches;
@@ -1463,6 +1553,7 @@ template <typename T>
 static fj_status solve_t(fj_graph *g, const double *s, const double *z0, const fj_solve_opts *o, double *z_out,
                          fj_solve_info *info, int mem, Trace *tr = nullptr)
 {
+    const auto t_start = std::chrono::steady_clock::now();
     cudaStream_t st = (cudaStream_t)o->stream;
     const int64_t n = g->csr.n;
     const int ng = g->ngraphs;
@@ -1499,7 +1590,22 @@ static fj_status solve_t(fj_graph *g, const double *s, const double *z0, const f
     Run run;
     run.profile = o->profile != 0;
     run.launches += 4;  // gstat reset, min s, shift, init
-    if (z0) FJ_CHECK(launch_certify<T>(g, p, epsp, st, run));  // warm start: exact FP64 residual of z0
+    int warm = z0 ? 1 : -1;
+    if (z0) {
+        // warm start: exact FP64 residual of z0, judged against the zero start
+        FJ_CHECK(launch_certify<T>(g, p, epsp, st, run));
+        std::vector<int> keep;
+        FJ_CHECK(warm_judge(g, n, 1, ws.r64, ws.sp, st, keep));
+        run.launches += 1;
+        if (!keep[0]) {
+            warm = 0;
+            k_init<T><<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(n, sd, nullptr, p.perm, c.graph_of, gs, epsp,
+                                                                 o->omega, c.deg64, din, ws.sp, ws.zhat, r, h, da,
+                                                                 db, reinterpret_cast<T *>(ws.om));
+            FJ_CUDA(cudaGetLastError());
+            run.launches += 1;
+        }
+    }
 
     // profiling times every sweep launch, so no sweep may run past the stop flag;
     // otherwise sweeps run in captured batches of an even count
@@ -1640,7 +1746,8 @@ static fj_status solve_t(fj_graph *g, const double *s, const double *z0, const f
             std::memset(&f, 0, sizeof(f));
             f.sweeps = ws.ctr_host->sweeps;
             f.pushes = (int64_t)ws.ctr_host->pushes;
-            f.edges = (int64_t)ws.ctr_host->edges;
+            f.edges = (int64_t)(ws.ctr_host->edges + ws.ctr_host->fedges);
+            f.frontier_edges = (int64_t)ws.ctr_host->fedges;
             f.refine_passes = refine;
             f.c_eff = q[1];
             f.eps_prime = epsp;
@@ -1648,6 +1755,8 @@ static fj_status solve_t(fj_graph *g, const double *s, const double *z0, const f
             f.resid_rel_max = q[3];
             f.z_inf = q[4];
             f.err_bound = q[2];
+            f.cert_rel_err = q[4] > q[2] ? q[2] / (q[4] - q[2]) : INFINITY;
+            f.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
             f.converged = (q[5] == 0.0 && result == FJ_OK) ? 1 : 0;
             f.launches = run.launches;
             f.push_launches = run.push_launches;
@@ -1656,9 +1765,12 @@ static fj_status solve_t(fj_graph *g, const double *s, const double *z0, const f
             const double tb = (double)sizeof(T);
             const double per_sweep = (double)c.nnz * (4.0 + (c.w ? 4.0 : 0.0) + tb) + (double)c.n * (8.0 + 5.0 * tb);
             f.push_bytes = (double)ws.ctr_host->sweeps * per_sweep + (double)ws.ctr_host->pushes * 20.0;
+            f.method_bytes = (double)ws.ctr_host->edges * (4.0 + (c.w ? 4.0 : 0.0) + tb) +
+                             (double)ws.ctr_host->pushes * 32.0;
             f.frontier_rounds = f_rounds;
             f.frontier_pushes = f_pushes;
             f.omega_used = o->omega;
+            f.warm_start = warm;
         }
     }
     return result;
@@ -2028,8 +2140,11 @@ k_sweep_batch(const Item *__restrict__ items, int64_t item0, int64_t nitems, con
         if (!FJ_IDX_OK(11, r0, n_rows) || !FJ_IDX_OK(12, r1, n_rows + 1) ||
             (it.slot < 0 && !FJ_IDX_OK(13, r1 - r0, kWarpRows + 1)))
             continue;
-        const int32_t lo = it.lo;
-        auto src = [&](int32_t c) -> const T * { return (c < lo ? (const T *)dcur : dprev) + (int64_t)c * k; };
+        const int32_t lo = it.lo, hlo = it.hlo, nhub = it.nhub;
+        auto src = [&](int32_t c) -> const T * {
+            const bool earlier = c < nhub ? c < hlo : c < lo;
+            return (earlier ? (const T *)dcur : dprev) + (int64_t)c * k;
+        };
         auto add = [](T &acc, float a, T v) { acc += (T)a * v; };
         if (it.slot < 0) {
             warp_tile_k<T, T, W, D>(r0, r1, it.k0, it.k1, false, rp, col, w, begin, src, add, apply_row, lane,
@@ -2340,8 +2455,8 @@ k_sweep_batch_bulk(const Item *__restrict__ items, int64_t item0, int64_t nitems
 
     // Walk of [k0, k1): rows r0.. (a tile) or one chunk of row r0.  Returns
     // false after a wait that timed out (the warp then stops).
-    auto walk = [&](int64_t r0, int64_t r1, int64_t k0, int64_t k1, bool chunk, int32_t lo, float &o1,
-                    float &o2) -> bool {
+    auto walk = [&](int64_t r0, int64_t r1, int64_t k0, int64_t k1, bool chunk, int32_t lo, int32_t hlo,
+                    int32_t nhub, float &o1, float &o2) -> bool {
         int64_t e_lo = k1, e_hi = k1;
         if (!chunk) {
             if (r0 + lane < r1) e_lo = rp[r0 + lane + 1];
@@ -2391,7 +2506,8 @@ k_sweep_batch_bulk(const Item *__restrict__ items, int64_t item0, int64_t nitems
             if (lane == 0) mbar_expect_tx(&bars[wl][s], m * row_bytes);
             __syncwarp();
             if (in) {
-                const float *srcp = (cl < lo ? (const float *)dcur : dprev) + (int64_t)cl * k;
+                const bool earlier = cl < nhub ? cl < hlo : cl < lo;
+                const float *srcp = (earlier ? (const float *)dcur : dprev) + (int64_t)cl * k;
                 bulk_g2s(ring + ((size_t)s * kBulkRows + lane) * k, srcp, row_bytes, &bars[wl][s]);
             }
             return al;
@@ -2433,7 +2549,7 @@ k_sweep_batch_bulk(const Item *__restrict__ items, int64_t item0, int64_t nitems
             (it.slot < 0 && !FJ_IDX_OK(13, r1 - r0, kWarpRows + 1)))
             continue;
         float o1 = 0.f, o2 = 0.f;
-        if (!walk(r0, r1, it.k0, it.k1, it.slot >= 0, it.lo, o1, o2)) {
+        if (!walk(r0, r1, it.k0, it.k1, it.slot >= 0, it.lo, it.hlo, it.nhub, o1, o2)) {
             timed_out = true;
             break;
         }
@@ -2520,7 +2636,7 @@ static fj_status bws_grow(fj_graph *g, int k, int64_t nparts, int64_t nclasses)
     if (nclasses > b.cap_tick) {
         dev_free(b.tick);
         b.tick = nullptr;
-        FJ_CUDA(cudaMalloc(&b.tick, sizeof(unsigned int) * 2 * (size_t)nclasses));
+        FJ_CUDA(dev_malloc(&b.tick, sizeof(unsigned int) * 2 * (size_t)nclasses));
         FJ_CUDA(cudaMemset(b.tick, 0, sizeof(unsigned int) * 2 * (size_t)nclasses));
         b.cap_tick = nclasses;
     }
@@ -2530,31 +2646,31 @@ static fj_status bws_grow(fj_graph *g, int k, int64_t nparts, int64_t nclasses)
         for (void **p : vb) {
             dev_free(*p);
             *p = nullptr;
-            FJ_CUDA(cudaMalloc(p, sizeof(double) * (size_t)need));
+            FJ_CUDA(dev_malloc(p, sizeof(double) * (size_t)need));
         }
         double **db_[] = {&b.zhat, &b.sp, &b.sin, &b.zout, &b.r64};
         for (double **p : db_) {
             dev_free(*p);
             *p = nullptr;
-            FJ_CUDA(cudaMalloc(p, sizeof(double) * (size_t)need));
+            FJ_CUDA(dev_malloc(p, sizeof(double) * (size_t)need));
         }
         dev_free(b.list);
         b.list = nullptr;
-        FJ_CUDA(cudaMalloc(&b.list, sizeof(int32_t) * (size_t)need));
+        FJ_CUDA(dev_malloc(&b.list, sizeof(int32_t) * (size_t)need));
         b.cap = need;
     }
-    if (!b.om) FJ_CUDA(cudaMalloc(&b.om, sizeof(double) * (size_t)g->csr.n));
+    if (!b.om) FJ_CUDA(dev_malloc(&b.om, sizeof(double) * (size_t)g->csr.n));
     if (k > b.cap_k) {
         dev_free(b.gstat);
         if (b.gstat_host) cudaFreeHost(b.gstat_host);
-        FJ_CUDA(cudaMalloc(&b.gstat, sizeof(double) * kGs * k));
+        FJ_CUDA(dev_malloc(&b.gstat, sizeof(double) * kGs * k));
         FJ_CUDA(cudaMallocHost(&b.gstat_host, sizeof(double) * kGs * k));
         b.cap_k = k;
     }
     const int64_t np = 2 * std::max<int64_t>(nparts, 1) * k;
     if (np > b.cap_partk) {
         dev_free(b.partk);
-        FJ_CUDA(cudaMalloc(&b.partk, sizeof(double) * (size_t)np));
+        FJ_CUDA(dev_malloc(&b.partk, sizeof(double) * (size_t)np));
         b.cap_partk = np;
     }
     return FJ_OK;
@@ -2564,14 +2680,15 @@ template <typename T>
 static fj_status solve_batch_t(fj_graph *g, const double *S, const double *Z0, int k, const fj_solve_opts *o,
                                double *Z, fj_solve_info *info, int mem)
 {
+    const auto t_start = std::chrono::steady_clock::now();
     cudaStream_t st = (cudaStream_t)o->stream;
     const int64_t n = g->csr.n;
     Workspace &ws = g->ws;
     if (!ws.ctr) {
-        FJ_CUDA(cudaMalloc(&ws.ctr, sizeof(Counters)));
+        FJ_CUDA(dev_malloc(&ws.ctr, sizeof(Counters)));
         FJ_CUDA(cudaMallocHost(&ws.ctr_host, sizeof(Counters)));
     }
-    if (!ws.zmax) FJ_CUDA(cudaMalloc(&ws.zmax, sizeof(unsigned long long)));
+    if (!ws.zmax) FJ_CUDA(dev_malloc(&ws.zmax, sizeof(unsigned long long)));
     Plan p;
     FJ_CHECK(make_plan(g, o, st, p));
     const DevCSR &c = *p.c;
@@ -2624,7 +2741,29 @@ static fj_status solve_batch_t(fj_graph *g, const double *S, const double *Z0, i
         FJ_CUDA(cudaGetLastError());
         return FJ_OK;
     };
-    if (Z0) FJ_CHECK(certify());
+    std::vector<int> warm((size_t)k, Z0 ? 1 : -1);
+    if (Z0) {
+        // every vector's start is judged against its zero start; the losers restart from zero
+        FJ_CHECK(certify());
+        std::vector<int> keep;
+        FJ_CHECK(warm_judge(g, n, k, b.r64, b.sp, st, keep));
+        bool any = false;
+        for (int j = 0; j < k; ++j) {
+            warm[(size_t)j] = keep[(size_t)j];
+            any = any || !keep[(size_t)j];
+        }
+        if (any) {
+            std::vector<int> cold((size_t)k);
+            for (int j = 0; j < k; ++j) cold[(size_t)j] = keep[(size_t)j] ? 0 : 1;
+            // the flags go after the judge's sums (the buffer holds room for 64)
+            int *cold_d = reinterpret_cast<int *>(g->ws.judge + (size_t)kJudgeBlocks * k * 2);
+            FJ_CUDA(cudaMemcpyAsync(cold_d, cold.data(), sizeof(int) * k, cudaMemcpyHostToDevice, st));
+            k_zero_start_cols<T><<<grid_for(n * k, 256, 152 * 16), 256, 0, st>>>(n, k, cold_d, b.sp, b.zhat, r,
+                                                                                  b.r64, da, db);
+            FJ_CUDA(cudaGetLastError());
+            FJ_CUDA(cudaStreamSynchronize(st));
+        }
+    }
     Run run;
     run.profile = o->profile != 0;
     run.launches = 6;
@@ -2756,7 +2895,8 @@ static fj_status solve_batch_t(fj_graph *g, const double *S, const double *Z0, i
             std::memset(&f, 0, sizeof(f));
             f.sweeps = ws.ctr_host->sweeps;
             f.pushes = (int64_t)ws.ctr_host->pushes;
-            f.edges = (int64_t)ws.ctr_host->edges;
+            f.edges = (int64_t)(ws.ctr_host->edges + ws.ctr_host->fedges);
+            f.frontier_edges = (int64_t)ws.ctr_host->fedges;
             f.refine_passes = refine;
             f.c_eff = q[1];
             f.eps_prime = epsp;
@@ -2764,16 +2904,21 @@ static fj_status solve_batch_t(fj_graph *g, const double *S, const double *Z0, i
             f.resid_rel_max = q[3];
             f.z_inf = q[4];
             f.err_bound = q[2];
+            f.cert_rel_err = q[4] > q[2] ? q[2] / (q[4] - q[2]) : INFINITY;
+            f.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
             f.converged = (q[5] == 0.0 && result == FJ_OK) ? 1 : 0;
             f.launches = run.launches + 1;
             f.push_launches = run.push_launches;
             f.push_ms = run.push_ms;
             f.frontier_rounds = f_rounds;
             f.frontier_pushes = f_pushes;
+            f.warm_start = warm[(size_t)j];
             const double tb = (double)sizeof(T);
             // per sweep: columns and weights once, k increments per nonzero, k row records per row
             f.push_bytes = (double)ws.ctr_host->sweeps *
                            ((double)c.nnz * (4.0 + (c.w ? 4.0 : 0.0) + tb * k) + (double)c.n * (8.0 + 5.0 * tb * k));
+            f.method_bytes = (double)ws.ctr_host->sweeps * (double)c.nnz * (4.0 + (c.w ? 4.0 : 0.0)) +
+                             (double)ws.ctr_host->edges * tb + (double)ws.ctr_host->pushes * 32.0;
         }
     }
     return result;
@@ -2793,6 +2938,21 @@ extern "C" fj_status fj_solve_batch(fj_graph *g, const double *S, int k, const f
     return with_omega_fallback(opts, [&](const fj_solve_opts *o) {
         if (o->precision == FJ_PREC_FP32) return fj::solve_batch_t<float>(g, S, nullptr, k, o, Z_out, info, mem);
         return fj::solve_batch_t<double>(g, S, nullptr, k, o, Z_out, info, mem);
+    });
+}
+
+extern "C" fj_status fj_solve_batch_warm(fj_graph *g, const double *S, const double *Z0, int k,
+                                         const fj_solve_opts *opts, double *Z_out, fj_solve_info *info, int mem)
+{
+    FJ_ARG(g != nullptr, "graph is NULL");
+    FJ_ARG(S != nullptr && Z0 != nullptr && Z_out != nullptr, "S, Z0 or Z_out is NULL");
+    FJ_ARG(k >= 1 && k <= 64, "k must be in 1..64");
+    FJ_ARG(mem == FJ_MEM_HOST || mem == FJ_MEM_DEVICE, "mem must be FJ_MEM_HOST or FJ_MEM_DEVICE");
+    FJ_ARG(g->ngraphs == 1, "a ragged handle takes one opinion vector per graph (use fj_solve_warm)");
+    FJ_CHECK(fj::check_opts(opts));
+    return with_omega_fallback(opts, [&](const fj_solve_opts *o) {
+        if (o->precision == FJ_PREC_FP32) return fj::solve_batch_t<float>(g, S, Z0, k, o, Z_out, info, mem);
+        return fj::solve_batch_t<double>(g, S, Z0, k, o, Z_out, info, mem);
     });
 }
 
@@ -2927,10 +3087,10 @@ fj_status jacobi_radius(fj_graph *g, int iters, cudaStream_t st, double *mu)
     constexpr int kNb = 152 * 4;
     double *x = nullptr, *y = nullptr, *part = nullptr, *sums = nullptr;
     fj_status s = FJ_OK;
-    cudaError_t e = cudaMalloc(&x, sizeof(double) * n);
-    if (e == cudaSuccess) e = cudaMalloc(&y, sizeof(double) * n);
-    if (e == cudaSuccess) e = cudaMalloc(&part, sizeof(double) * kNb);
-    if (e == cudaSuccess) e = cudaMalloc(&sums, sizeof(double) * iters);
+    cudaError_t e = dev_malloc(&x, sizeof(double) * n);
+    if (e == cudaSuccess) e = dev_malloc(&y, sizeof(double) * n);
+    if (e == cudaSuccess) e = dev_malloc(&part, sizeof(double) * kNb);
+    if (e == cudaSuccess) e = dev_malloc(&sums, sizeof(double) * iters);
     if (e == cudaSuccess) {
         const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ip->nitems, 8), 152 * 8));
         k_fill<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(n, x, 1.0);
@@ -3042,7 +3202,7 @@ extern "C" fj_status fj_graph_tune(fj_graph *g, const double *s, const fj_solve_
     const int64_t n = g->csr.n;
     std::vector<double> zh;
     double *zd = nullptr;
-    if (mem == FJ_MEM_DEVICE) FJ_CUDA(cudaMalloc(&zd, sizeof(double) * std::max<int64_t>(n, 1)));
+    if (mem == FJ_MEM_DEVICE) FJ_CUDA(dev_malloc(&zd, sizeof(double) * std::max<int64_t>(n, 1)));
     else zh.resize((size_t)std::max<int64_t>(n, 1));
     double *z = mem == FJ_MEM_DEVICE ? zd : zh.data();
     double best_t = -1.0;
@@ -3088,7 +3248,7 @@ extern "C" fj_status fj_graph_tune_batch(fj_graph *g, const double *S, int k, co
     const int64_t n = g->csr.n;
     std::vector<double> zh;
     double *zd = nullptr;
-    if (mem == FJ_MEM_DEVICE) FJ_CUDA(cudaMalloc(&zd, sizeof(double) * std::max<int64_t>(n * k, 1)));
+    if (mem == FJ_MEM_DEVICE) FJ_CUDA(dev_malloc(&zd, sizeof(double) * std::max<int64_t>(n * k, 1)));
     else zh.resize((size_t)std::max<int64_t>(n * k, 1));
     double *z = mem == FJ_MEM_DEVICE ? zd : zh.data();
     double best_t = -1.0;
@@ -3125,3 +3285,49 @@ extern "C" fj_status fj_graph_tune_batch(fj_graph *g, const double *S, int k, co
     if (best_ms) *best_ms = best_t;
     return FJ_OK;
 }
+
+// ============================================================== failure-path self-test
+
+namespace fj {
+
+// The library's two kinds of bounded device wait, each on something that
+// nothing completes: the look-back's wait on a tile status word (zero: never
+// published) and the bulk-copy ring's wait on an mbarrier (no arrival).
+// Each must give up after `limit` polls and say so.
+__global__ void k_wait_selftest(const unsigned long long *word, long long limit, int *gave_up)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x != 0) return;
+    unsigned long long w;
+    if (!wait_published(word, limit, w)) gave_up[0] = 1;
+    tc::mbar_init(&bar, 1);
+    if (!tc::mbar_wait_bounded(&bar, 0, (uint32_t)limit)) gave_up[1] = 1;
+}
+
+}  // namespace fj
+
+extern "C" fj_status fj_wait_selftest(int64_t polls, void *stream)
+{
+    FJ_ARG(polls >= 1 && polls <= fj::kSpinLimit, "polls must be in 1..2^24");
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned long long *word = nullptr;
+    FJ_CUDA(fj::dev_malloc(&word, sizeof(unsigned long long) + 2 * sizeof(int)));
+    int *flags = reinterpret_cast<int *>(word + 1);
+    cudaError_t e = cudaMemsetAsync(word, 0, sizeof(unsigned long long) + 2 * sizeof(int), st);
+    if (e == cudaSuccess) {
+        fj::k_wait_selftest<<<1, 32, 0, st>>>(word, (long long)polls, flags);
+        e = cudaGetLastError();
+    }
+    int h[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, flags, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    fj::dev_free(word);
+    if (e != cudaSuccess) return fj::cuda_fail(e, "wait self-test", __FILE__, __LINE__);
+    if (h[0] && h[1]) {
+        fj::set_error("both bounded waits gave up after %lld polls", (long long)polls);
+        return FJ_ERR_TIMEOUT;
+    }
+    fj::set_error("a bounded wait returned although nothing completed it (status word %d, mbarrier %d)", h[0], h[1]);
+    return FJ_OK;
+}
+

@@ -113,11 +113,11 @@ inline cudaError_t sort_scratch_alloc(SortScratch &s, int64_t n)
     cudaFree(s.tile_ctr);
     s = SortScratch();
     cudaError_t e;
-    if ((e = cudaMalloc(&s.hist, sizeof(unsigned) * 256 * t)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&s.offs, sizeof(long long) * 256 * t)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&s.status, sizeof(unsigned long long) * scan_tiles(256 * t, 256 * 8))) != cudaSuccess)
+    if ((e = dev_malloc(&s.hist, sizeof(unsigned) * 256 * t)) != cudaSuccess) return e;
+    if ((e = dev_malloc(&s.offs, sizeof(long long) * 256 * t)) != cudaSuccess) return e;
+    if ((e = dev_malloc(&s.status, sizeof(unsigned long long) * scan_tiles(256 * t, 256 * 8))) != cudaSuccess)
         return e;
-    if ((e = cudaMalloc(&s.tile_ctr, sizeof(unsigned int))) != cudaSuccess) return e;
+    if ((e = dev_malloc(&s.tile_ctr, sizeof(unsigned int))) != cudaSuccess) return e;
     s.cap_tiles = t;
     return cudaSuccess;
 }

@@ -189,17 +189,21 @@ def test_replicas_on_two_streams_match_single_stream(capi):
     S = [np.ascontiguousarray(v) for v in g["S"]]
     opts = dict(eps=1e-6, omega=1.5, precision=capi.FJ_PREC_FP32)
     ref_h = capi.Graph.from_csr(n, *to_dev(rp, col, w), directed=False)
-    want = []
+    want, bound = [], []
     for v in S:
         z, info, st = ref_h.solve(v, **opts)
         assert st == capi.FJ_OK
         want.append(np.array(z))
+        # bit-identity holds when the atomics of the FP64 frontier cleanup did not run
+        bound.append(0.0 if info[0]["frontier_rounds"] == 0 else 2 * info[0]["err_bound"])
     streams = [torch.cuda.Stream(), torch.cuda.Stream()]
     handles = []
     for st_ in streams:
         with torch.cuda.stream(st_):
             handles.append(capi.Graph.from_csr(n, *to_dev(rp, col, w), directed=False, stream=st_.cuda_stream))
     got = [None] * len(S)
+    got_rounds = [0] * len(S)
+    got_bound = [0.0] * len(S)
     errors = []
 
     def replica(r):
@@ -207,6 +211,8 @@ def test_replicas_on_two_streams_match_single_stream(capi):
             for j in range(r, len(S), 2):
                 z, info, st = handles[r].solve(S[j], stream=streams[r].cuda_stream, **opts)
                 got[j] = np.array(z)
+                got_rounds[j] = info[0]["frontier_rounds"]
+                got_bound[j] = info[0]["err_bound"]
         except Exception as e:  # reported below, on the main thread
             errors.append(e)
 
@@ -217,4 +223,7 @@ def test_replicas_on_two_streams_match_single_stream(capi):
         t.join()
     assert not errors, errors
     for j in range(len(S)):
-        assert np.array_equal(got[j], want[j]), j
+        if bound[j] == 0.0 and got_rounds[j] == 0:
+            assert np.array_equal(got[j], want[j]), j
+        else:
+            assert np.max(np.abs(got[j] - want[j])) <= bound[j] + 2 * got_bound[j], j

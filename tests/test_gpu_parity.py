@@ -206,9 +206,15 @@ def test_repeat_solve_is_deterministic(capi, ba20k):
     g, rp, col, w, s, _ = ba20k
     G = capi.Graph.from_csr(g["n"], *to_dev(rp, col, w), directed=False)
     (s_d,) = to_dev(s)
-    a = G.solve(s_d, eps=1e-6, omega=1.2, precision=capi.FJ_PREC_FP32)[0].cpu().numpy()
-    b = G.solve(s_d, eps=1e-6, omega=1.2, precision=capi.FJ_PREC_FP32)[0].cpu().numpy()
-    assert np.array_equal(a, b)
+    za, ia, _ = G.solve(s_d, eps=1e-6, omega=1.2, precision=capi.FJ_PREC_FP32)
+    a = za.cpu().numpy()
+    zb, ib, _ = G.solve(s_d, eps=1e-6, omega=1.2, precision=capi.FJ_PREC_FP32)
+    b = zb.cpu().numpy()
+    if ia[0]["frontier_rounds"] == 0 and ib[0]["frontier_rounds"] == 0:
+        assert np.array_equal(a, b)  # sweeps and certificate sum in a fixed order
+    else:
+        # the FP64 frontier cleanup adds with atomics: equal to within the certificate
+        assert np.max(np.abs(a - b)) <= ia[0]["err_bound"] + ib[0]["err_bound"]
 
 
 # ------------------------------------------------------------ ragged batch

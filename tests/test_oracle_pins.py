@@ -664,3 +664,39 @@ def test_omega_opt_is_youngs_formula():
     # Eq. 17 written as 1 + (mu / (1 + sqrt(1 - mu^2)))^2 equals 2 / (1 + sqrt(1 - mu^2))
     for mu in (0.0, 0.3, 2.0 / 3.0, 0.9, 0.999):
         assert abs(oracle.omega_opt(mu) - 2.0 / (1.0 + np.sqrt(1.0 - mu * mu))) < 1e-15
+
+
+# ------------------------------------------------------------ multicolour row order
+
+@pytest.mark.parametrize("cap", [5, 12, 1000])
+def test_sweep_order_brute_force(monkeypatch, cap):
+    """The row order against a brute-force restatement: the hub set is the
+    largest in-degree threshold set of at most cap nodes, and every range is
+    sorted by (colour, in-degree descending, id)."""
+    monkeypatch.setattr(oracle, "HUB_CAPACITY", cap)
+    rng = np.random.default_rng(17)
+    n = 40
+    arcs = [(int(a), int(b)) for a, b in rng.integers(0, n, (160, 2)) if a != b]
+    rp, col, _ = csr(n, arcs)
+    colour = rng.integers(0, 4, n).astype(np.int32)
+    perm, nhub, hub_row, class_row = oracle.sweep_order(n, rp, col, colour, hubs=True)
+    indeg = [int(np.sum(col == v)) for v in range(n)]
+    assert sorted(perm.tolist()) == list(range(n))
+    if n <= cap:
+        hubs = set(range(n))
+    else:
+        hubs = None
+        for t in sorted(set(indeg)) + [max(indeg) + 1]:
+            cand = {v for v in range(n) if indeg[v] >= t}
+            if len(cand) <= cap:
+                hubs = cand
+                break
+    assert nhub == len(hubs) and set(perm[:nhub].tolist()) == hubs
+    key = lambda v: (colour[v], -indeg[v], v)
+    assert perm[:nhub].tolist() == sorted(hubs, key=key)
+    assert perm[nhub:].tolist() == sorted(set(range(n)) - hubs, key=key)
+    K = int(colour.max()) + 1
+    for c in range(K):
+        assert all(colour[v] == c for v in perm[hub_row[c]:hub_row[c + 1]])
+        assert all(colour[v] == c for v in perm[class_row[c]:class_row[c + 1]])
+    assert hub_row[K] == nhub == class_row[0] and class_row[K] == n
