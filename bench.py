@@ -127,16 +127,13 @@ def clocks_stop(p, path, device_index=0):
 
 
 # Name of the single-vector sweep kernel the roofline object reports.
-SWEEP_KERNEL = "k_products + k_sweep (one sweep segment of a colour class)"
+SWEEP_KERNEL = "k_sweep_gather + k_sweep_apply (one colour class)"
 
 # DRAM bytes (read + write) per launch of the single-vector sweep, as a
 # multiple of the dense bytes it streams, from one ncu capture per graph kind
 # (key: generator, single vector).  Filled in from captures listed under
 # profiles/; a kind without a capture reports traffic null.
-SWEEP_TRAFFIC_RATIO = {
-    ("rmat_dir", True): (31.09 / 28.53, "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_products + k_sweep "
-                         "over one sweep of directed R-MAT s20 (1.090 x its dense bytes), scaled to this launch"),
-}
+SWEEP_TRAFFIC_RATIO = {}
 
 
 def roofline_of(p, kernel, traffic_key=None):

@@ -271,7 +271,7 @@ fj_status build_blocks(DevCSR &c, const std::vector<int64_t> &seg_rows, Workspac
 {
     const int64_t n = c.n;
     const bool warp_tiles = kind != kTileBlock;
-    int32_t *&blk = kind == kTileSweep ? c.sblk_row : (warp_tiles ? c.wblk_row : c.blk_row);
+    int32_t *&blk = warp_tiles ? c.wblk_row : c.blk_row;
     dev_free(blk);
     blk = nullptr;
     FJ_CUDA(dalloc(&blk, n + 2));
@@ -282,8 +282,8 @@ fj_status build_blocks(DevCSR &c, const std::vector<int64_t> &seg_rows, Workspac
     if (!seg.empty())
         FJ_CUDA(cudaMemcpyAsync(seg_d, seg.data(), sizeof(int64_t) * seg.size(), cudaMemcpyHostToDevice, st));
     FJ_CHECK(ws_status(ws, scan_tiles(n, 256 * 8)));
-    const int64_t bucket = kind == kTileSweep ? kSweepNnz : (warp_tiles ? kWarpNnz : kBlockNnz);
-    const int64_t max_rows = kind == kTileSweep ? kSweepRows : (warp_tiles ? kWarpRows : kBlockRows);
+    const int64_t bucket = warp_tiles ? kWarpNnz : kBlockNnz;
+    const int64_t max_rows = warp_tiles ? kWarpRows : kBlockRows;
     FJ_CUDA(compact<256, 8>(n, BlockStartPred{c.row_ptr, seg_d, (int)seg.size(), bucket, max_rows}, blk, ws.count,
                             ws.status, ws.tile_ctr, err, st));
     long long nb = 0;
@@ -291,11 +291,6 @@ fj_status build_blocks(DevCSR &c, const std::vector<int64_t> &seg_rows, Workspac
     FJ_CUDA(cudaStreamSynchronize(st));
     k_set_i32<<<1, 1, 0, st>>>(blk + nb, (int32_t)n);
     FJ_CUDA(cudaGetLastError());
-    if (kind == kTileSweep) {
-        c.nsblocks = nb;
-        dev_free(seg_d);
-        return FJ_OK;
-    }
     if (warp_tiles) {
         c.nwblocks = nb;
         dev_free(seg_d);
@@ -331,7 +326,6 @@ static void csr_free(DevCSR &c)
     dev_free(c.graph_of);
     dev_free(c.blk_row);
     dev_free(c.wblk_row);
-    dev_free(c.sblk_row);
     c = DevCSR();
 }
 
@@ -383,7 +377,6 @@ static fj_status derive_arrays(fj_graph *g, DevCSR &c, bool transpose, const std
     }
     FJ_CHECK(build_blocks(c, segs, g->ws, g->err, st, kTileBlock));
     FJ_CHECK(build_blocks(c, segs, g->ws, g->err, st, kTileWarp));
-    FJ_CHECK(build_blocks(c, segs, g->ws, g->err, st, kTileSweep));
     return FJ_OK;
 }
 
@@ -712,15 +705,18 @@ void fj_graph_destroy(fj_graph *g)
     dev_free(g->colr.tcol);
     dev_free(g->colr.tw);
     csr_free(g->colr.pcsr);
-    for (ItemPlan *ip : {&g->wplan_csr, &g->wplan_pcsr, &g->splan_csr, &g->splan_pcsr}) {
+    for (ItemPlan *ip : {&g->wplan_csr, &g->wplan_pcsr}) {
         dev_free(ip->items);
         dev_free(ip->slot_first);
         dev_free(ip->slot_nchunk);
         dev_free(ip->part);
         dev_free(ip->cnt);
     }
+    chunk_plan_free(g->cplan_csr);
+    chunk_plan_free(g->cplan_pcsr);
     Workspace &ws = g->ws;
     dev_free(ws.r); dev_free(ws.h); dev_free(ws.da); dev_free(ws.db); dev_free(ws.om); dev_free(ws.judge);
+    dev_free(ws.rsum); dev_free(ws.carry);
     dev_free(ws.zhat); dev_free(ws.sp); dev_free(ws.sin); dev_free(ws.zout); dev_free(ws.r64); dev_free(ws.zs);
     dev_free(ws.gstat); dev_free(ws.ctr); dev_free(ws.status); dev_free(ws.tile_ctr); dev_free(ws.zmax);
     dev_free(ws.list); dev_free(ws.count); dev_free(ws.partial);
@@ -1195,6 +1191,15 @@ static void item_plan_free(ItemPlan &ip)
     ip = ItemPlan();
 }
 
+void chunk_plan_free(ChunkPlan &cp)
+{
+    dev_free(cp.starts);
+    dev_free(cp.endbase);
+    dev_free(cp.rank);
+    dev_free(cp.long_rows);
+    cp = ChunkPlan();
+}
+
 static void colouring_free(fj_graph *g)
 {
     Colouring &cl = g->colr;
@@ -1208,7 +1213,7 @@ static void colouring_free(fj_graph *g)
     csr_free(cl.pcsr);
     cl = Colouring();
     item_plan_free(g->wplan_pcsr);
-    item_plan_free(g->splan_pcsr);
+    chunk_plan_free(g->cplan_pcsr);
     g->ws.gen++;
 }
 
@@ -1393,7 +1398,6 @@ fj_status ensure_colouring(fj_graph *g, int palette, cudaStream_t st)
     dev_free(k0); dev_free(v0); dev_free(k1); dev_free(v1);
     FJ_CHECK(build_blocks(p, segs, g->ws, g->err, st, kTileBlock));
     FJ_CHECK(build_blocks(p, segs, g->ws, g->err, st, kTileWarp));
-    FJ_CHECK(build_blocks(p, segs, g->ws, g->err, st, kTileSweep));
     cl.built = true;
     return read_dev_error(g, st);
 }

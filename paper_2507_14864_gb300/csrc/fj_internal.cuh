@@ -16,20 +16,16 @@ constexpr int kBlockRows = 512;
 // Warp tiles of the sweep: rows whose nonzeros fit in 2 * kWarpNnz (sixteen
 // per lane), at most kWarpRows rows (two per lane); a longer row is cut into
 // chunks of kWarpChunk nonzeros (sixteen per lane: one batch of loads).
-// Column and weight arrays carry kNnzPad spare entries, so that 16-byte
+// Column and weight arrays carry kNnzPad spare entries, so that the sweep's
+// 256-nonzero chunks (16-byte loads of eight entries per lane) and 16-byte
 // asynchronous copies of a tile rounded out to 4-element granules stay inside
-// the allocation.
-constexpr int kNnzPad = 4;
+// the allocation.  The spare entries are never used as values.
+constexpr int kNnzPad = 256;
 constexpr int kWarpNnz = 256;
 constexpr int kWarpRows = 64;
 constexpr int kWarpChunk = 512;
-// Tiles of the single-vector sweep: as warp tiles, twice the nonzeros (32 per
-// lane); fewer, larger tiles spread the per-tile cost of the row kernel.
-constexpr int kSweepNnz = 512;
-constexpr int kSweepRows = 64;
-constexpr int kSweepChunk = 1024;
-// Tilings of a CSR: metric blocks, warp tiles, sweep tiles.
-enum TileKind { kTileBlock = 0, kTileWarp = 1, kTileSweep = 2 };
+// Tilings of a CSR: metric blocks, warp tiles.
+enum TileKind { kTileBlock = 0, kTileWarp = 1 };
 
 // One CSR resident on the device plus the per-row arrays the push needs.
 struct DevCSR {
@@ -46,8 +42,6 @@ struct DevCSR {
     int64_t nblocks = 0;
     int32_t *wblk_row = nullptr;  // nwblocks + 1 entries (warp tiles)
     int64_t nwblocks = 0;
-    int32_t *sblk_row = nullptr;  // nsblocks + 1 entries (sweep tiles)
-    int64_t nsblocks = 0;
     std::vector<int64_t> seg_blk;  // host: block ranges of forced segments (classes / graphs)
 };
 
@@ -107,6 +101,24 @@ struct ItemPlan {
     std::vector<int64_t> class_item;  // host: items of class c are [class_item[c], class_item[c+1])
 };
 
+// Chunk plan of a CSR for the single-vector sweep: the nonzeros cut into
+// 256-element chunks (chunk C holds nonzeros 256C .. 256C + 255).
+constexpr int kChunkE = 256;
+struct ChunkPlan {
+    bool built = false;
+    int64_t nch = 0;              // chunks
+    uint32_t *starts = nullptr;   // 8 (nch + 1) words: bit b of word i set when nonzero 32i + b is the first
+                                  // of a non-empty row; one more start at nonzero nnz closes the last row
+    int32_t *endbase = nullptr;   // nch entries: non-empty rows that end before chunk C
+    int32_t *rank = nullptr;      // n entries: non-empty rows before row x (row x's slot in the row sums)
+    // per class: rows [row0[2c], row1[2c]) (hubs) and [row0[2c+1], row1[2c+1]) (the rest); nonzeros
+    // [k0[i], k1[i]) of range i
+    std::vector<int64_t> row0, row1, k0, k1;
+    int32_t *long_rows = nullptr;  // rows over kLongChunks chunks, grouped by class
+    std::vector<int64_t> long_off;  // class c's long rows: long_rows[long_off[c] .. long_off[c + 1])
+};
+constexpr int kLongChunks = 16;  // a row over this many chunks is combined by a warp
+
 // Solve scratch, grown on demand and kept by the handle.
 struct Workspace {
     int64_t cap_n = 0;      // nodes x right-hand sides the buffers hold
@@ -116,6 +128,9 @@ struct Workspace {
     void *da = nullptr;     // push increments (current)
     void *db = nullptr;     // push increments (second buffer)
     void *om = nullptr;     // per-node relaxation factor
+    void *rsum = nullptr;   // single-vector sweep: row sums of the gathered increments, by row rank
+    void *carry = nullptr;  // single-vector sweep: partial sum of the row that crosses each chunk's end
+    int64_t cap_carry = 0;
     double *judge = nullptr;  // per-block residual and opinion sums of the warm-start judge
     int64_t cap_judge = 0;
     double *zhat = nullptr; // estimate of z' (FP64)
@@ -180,7 +195,7 @@ struct fj_graph {
     int64_t *node_off_d = nullptr;
     fj::Colouring colr;
     fj::ItemPlan wplan_csr, wplan_pcsr;  // warp-tile items (certificate, batch sweep, network)
-    fj::ItemPlan splan_csr, splan_pcsr;  // sweep-tile items (single-vector sweep)
+    fj::ChunkPlan cplan_csr, cplan_pcsr;  // chunk plans (single-vector sweep)
     fj::Workspace ws;
     fj::BatchWorkspace bws;
     fj::SortScratch sort;
@@ -201,5 +216,6 @@ fj_status plain_items(fj_graph *g, cudaStream_t st, const ItemPlan **out);
 fj_status ws_status(Workspace &ws, int64_t tiles);
 fj_status read_dev_error(fj_graph *g, cudaStream_t st);
 void dev_free(void *p);
+void chunk_plan_free(ChunkPlan &cp);
 
 }  // namespace fj

@@ -201,11 +201,11 @@ __device__ long long g_fj_dbg[4];
                 ? (g_fj_dbg[1] = blockIdx.x, g_fj_dbg[2] = (long long)(idx), g_fj_dbg[3] = (long long)(lim), false) \
                 : false))
 
-// ============================================================== fused sweep
+// ============================================================== sweep: gather and apply
 
 // One colour class of a sweep (Theorem 2's Gauss-Seidel order realised by
 // colour classes taken in turn; the whole graph as one class is a synchronous
-// round) in one pass: for every row x of the class,
+// round): for every row x of the class,
 //   r_x += sum_j a_xj delta_j, then if |r_x| > h_x push x (Eqs. sor1-sor3):
 //   delta = omega_x r_x / (1 + d_x), zhat_x += delta, r_x <- (1 - omega_x) r_x.
 // delta_j is node j's latest increment in the sweep order: for j in an
@@ -214,47 +214,35 @@ __device__ long long g_fj_dbg[4];
 // made in the previous sweep, in dprev.  Every row writes its own increment
 // (0 when it does not push) into dcur.
 //
-// A persistent warp takes the class's sweep tiles (at most 64 rows and 1024
-// nonzeros; a longer row is cut into 1024-nonzero chunks) in a fixed order.
-// For a tile, lane l handles elements e = 32 c + l: it loads all of its
-// columns at once (coalesced), then issues every increment gather as a 4- or
-// 8-byte asynchronous copy (cp.async) into the warp's value buffer in shared
-// memory, so a lane has up to 32 gathers in flight without holding them in
-// registers.  While they fly, the warp loads its rows' state and builds the
-// tile's start map (bit e set where a non-empty row begins).  Then the row
-// sums come from a segmented inclusive scan of each 32-element chunk across
-// the warp; the lane that ends a segment adds it to its row's accumulator in
-// shared memory.  The chunks are taken in order, so every row sum is formed
-// in one fixed order (deterministic).  Finally lane l applies the update to
-// rows r0 + l and r0 + l + 32.  Weights (weighted graphs) are copied into a
-// second buffer by 16-byte asynchronous copies.
+// Two kernels per class.  k_sweep_gather streams the class's nonzeros in
+// 32-element chunks, lane l of a warp taking element 32 C + l of chunk C with
+// several chunks' gathers in flight per thread, and sums every row's products
+// inside each chunk by a segmented inclusive scan across the warp (segments
+// start where the chunk plan's start bits say a row begins).  A segment that
+// ends its row is written to the row sums at the row's rank (its slot among
+// the non-empty rows); the segment of a row that goes on into the next chunk
+// is the chunk's carry.  k_sweep_apply then gives every row of the class its
+// sum, the carries of the chunks it crosses in chunk order and then its last
+// segment (a fixed order: deterministic), and applies the push.  Rows over
+// kLongChunks chunks are combined by a warp each.
 //
 // Hot table: node ids below nhot (the hub prefix of the colour order: the
 // nodes of largest in-degree, ordered by class) have their increments staged
-// in shared memory when the block starts, from this sweep's buffer for ids
-// below hlo (hubs of earlier classes) and the previous sweep's otherwise, so
-// that the gathers most rows make (a few percent of the nodes draw about a
-// third of the gathers on an R-MAT graph) are shared-memory loads.
-constexpr int kTileNnz = 2 * kSweepNnz;  // largest tile or chunk (1024)
-static_assert(kSweepChunk <= kTileNnz, "a chunk fits the value buffer");
-constexpr int kFusedSmemBudget = 227 * 1024 - 4096;  // dynamic shared memory of a block
-
-template <typename T, bool W>
-__host__ __device__ constexpr int fused_warps() { return sizeof(T) == 4 ? 20 : 12; }
-
-// Per-warp shared memory of the fused sweep: values, weights (weighted
-// graphs, with one 16-byte granule of slack), start map, row accumulators.
-template <typename T, bool W>
-__host__ __device__ constexpr int fused_warp_bytes()
-{
-    return kTileNnz * (int)sizeof(T) + (W ? (kTileNnz + 4) * 4 : 0) + 32 * 4 + kSweepRows * (int)sizeof(T);
-}
-
-template <typename T, bool W>
-__host__ __device__ constexpr int fused_hot_cap()
-{
-    return (kFusedSmemBudget - fused_warps<T, W>() * fused_warp_bytes<T, W>()) / (int)sizeof(T);
-}
+// in shared memory when a gather block starts, from this sweep's buffer for
+// ids below hlo (hubs of earlier classes) and the previous sweep's otherwise,
+// so that the gathers most rows make (a few percent of the nodes draw a third
+// of the gathers on an R-MAT graph) are shared-memory loads.
+// Launch shape of the gather kernel and size of its hot table (tuning knobs;
+// the defaults give one block per SM holding every hub's FP32 increment).
+#ifndef FJ_GATHER_THREADS
+#define FJ_GATHER_THREADS 1024
+#endif
+#ifndef FJ_HOT_KB
+#define FJ_HOT_KB 192
+#endif
+constexpr int kGatherThreads = FJ_GATHER_THREADS;
+constexpr int kHotBytes = FJ_HOT_KB * 1024;
+static_assert(kHotBytes <= kHubMax * 4 + 1024, "the hot table holds at most the hub prefix");
 
 __device__ __forceinline__ int32_t ld_stream_i32(const int32_t *p)
 {
@@ -262,222 +250,248 @@ __device__ __forceinline__ int32_t ld_stream_i32(const int32_t *p)
     asm("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(v) : "l"(p));
     return v;
 }
+__device__ __forceinline__ float ld_stream_f32(const float *p)
+{
+    float v;
+    asm("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
 
-template <int N>
-__device__ __forceinline__ void cp_async_ca(void *smem, const void *gmem)
+// L2 policy for the increments: kept in L2 ahead of the streams around them
+// (columns, weights and row state are read with evict-first loads).
+__device__ __forceinline__ uint64_t l2_keep_policy()
 {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(s), "l"(gmem), "n"(N) : "memory");
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
 }
-__device__ __forceinline__ void cp_async_cg16(void *smem, const void *gmem)
+__device__ __forceinline__ float ld_keep(const float *ptr, uint64_t pol)
 {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+    float v;
+    asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(ptr), "l"(pol));
+    return v;
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ double ld_keep(const double *ptr, uint64_t pol)
+{
+    double v;
+    asm("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(ptr), "l"(pol));
+    return v;
+}
 
 template <typename T, bool W>
-__global__ void __launch_bounds__(32 * fused_warps<T, W>(), 1)
-k_sweep_fused(const Item *__restrict__ items, int64_t item0, int64_t nitems, const int64_t *__restrict__ rp,
-              const int32_t *__restrict__ col, const float *__restrict__ w, int lo, int nhot, int nhub, int hlo,
-              const T *dcur_in, const T *__restrict__ dprev, T *dcur, T *__restrict__ r, const T *__restrict__ h,
-              const T *__restrict__ inv, double *__restrict__ zhat, const int32_t *__restrict__ indeg,
-              const T *__restrict__ om, const int32_t *__restrict__ slot_first,
-              const int32_t *__restrict__ slot_nchunk, double *part, int32_t *cnt, Counters *ctr, int64_t n_rows)
+__global__ void __launch_bounds__(kGatherThreads, kHotBytes > 110 * 1024 ? 1 : 2048 / kGatherThreads)
+k_sweep_gather(int64_t ka0, int64_t ka1, int64_t kb0, int64_t kb1, const int32_t *__restrict__ col,
+               const float *__restrict__ w, const uint32_t *__restrict__ starts, const int32_t *__restrict__ endbase,
+               int lo, int nhot, int nhub, int hlo, const T *__restrict__ dcur, const T *__restrict__ dprev,
+               T *__restrict__ rsum, T *__restrict__ carry, const Counters *ctr, int64_t n_rows, int64_t n_ranks)
 {
-    constexpr int NW = fused_warps<T, W>();
     constexpr unsigned FULL = 0xffffffffu;
-    constexpr int NCH = kTileNnz / 32;  // chunks of a full tile
-    __shared__ unsigned long long red[2][NW];
-    __shared__ int sbad;
-    extern __shared__ __align__(16) unsigned char fused_dyn[];
-    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    unsigned char *mine = fused_dyn + (size_t)wl * fused_warp_bytes<T, W>();
-    T *vals = reinterpret_cast<T *>(mine);
-    float *wts = reinterpret_cast<float *>(mine + kTileNnz * sizeof(T));
-    unsigned *sbits = reinterpret_cast<unsigned *>(mine + kTileNnz * sizeof(T) + (W ? (kTileNnz + 4) * 4 : 0));
-    T *sacc = reinterpret_cast<T *>(sbits + 32);
-    T *hot = reinterpret_cast<T *>(fused_dyn + (size_t)NW * fused_warp_bytes<T, W>());
-    if (*reinterpret_cast<volatile int *>(&ctr->done)) return;
-    for (int i = threadIdx.x; i < nhot; i += blockDim.x) hot[i] = i < hlo ? dcur_in[i] : dprev[i];
+    extern __shared__ __align__(16) unsigned char gather_dyn[];
+    T *hot = reinterpret_cast<T *>(gather_dyn);
+    if (*reinterpret_cast<const volatile int *>(&ctr->done)) return;
+    // stage the hot table, eight independent loads in flight per thread
+    for (int i0 = threadIdx.x; i0 < nhot; i0 += 8 * blockDim.x) {
+        T v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = i0 + u * (int)blockDim.x;
+            v[u] = i < nhot ? (i < hlo ? dcur[i] : dprev[i]) : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = i0 + u * (int)blockDim.x;
+            if (i < nhot) hot[i] = v[u];
+        }
+    }
     __syncthreads();
+    const int lane = threadIdx.x & 31;
+    // chunks of the two ranges, numbered 0 .. na + nb - 1
+    const int64_t ca0 = ka0 / kChunkE, cb0 = kb0 / kChunkE;
+    const int64_t na = ka1 > ka0 ? (ka1 - 1) / kChunkE - ca0 + 1 : 0;
+    const int64_t nb = kb1 > kb0 ? (kb1 - 1) / kChunkE - cb0 + 1 : 0;
+    const int64_t total = na + nb;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const uint64_t keep = l2_keep_policy();
+    auto delta = [&](int32_t j) -> T {
+        if ((unsigned)j < (unsigned)nhot) return hot[j];
+        if (!FJ_IDX_OK(15, j, n_rows)) return T(0);
+        const bool earlier = j < nhub ? j < hlo : j < lo;
+        return ld_keep((earlier ? dcur : dprev) + j, keep);
+    };
+    // one chunk per warp iteration; the next chunk's columns and plan words
+    // load while this chunk's gathers are in flight (the weights, needed only
+    // after the gathers, load beside them)
+    struct ChunkRegs {
+        int64_t C, e0;
+        unsigned inm;
+        int4 c0, c1;
+        uint32_t word, word_next;
+        int32_t ebase;
+    };
+    auto load_chunk = [&](int64_t t, ChunkRegs &q) {
+        const bool first = t < na;
+        q.C = first ? ca0 + t : cb0 + (t - na);
+        q.e0 = q.C * kChunkE + lane * 8;  // this lane's eight nonzeros
+        // which of them lie in the range (the range is whole rows)
+        const int64_t lo_off = (first ? ka0 : kb0) - q.e0, hi_off = (first ? ka1 : kb1) - q.e0;
+        unsigned inm = 0xFFu;
+        if (lo_off > 0) inm = lo_off >= 8 ? 0u : (inm << lo_off) & 0xFFu;
+        if (hi_off < 8) inm &= hi_off <= 0 ? 0u : (0xFFu >> (8 - hi_off));
+        q.inm = inm;
+        q.c0 = __ldcs(reinterpret_cast<const int4 *>(col + q.e0));
+        q.c1 = __ldcs(reinterpret_cast<const int4 *>(col + q.e0 + 4));
+        q.word = __ldg(starts + q.C * 8 + (lane >> 2));
+        q.word_next = lane == 31 ? __ldg(starts + (q.C + 1) * 8) : 0u;
+        q.ebase = __ldg(endbase + q.C);
+    };
+    ChunkRegs nxt;
+    if (warp < total) load_chunk(warp, nxt);
+    for (int64_t t = warp; t < total; t += nwarps) {
+        const ChunkRegs q = nxt;
+        if (t + nwarps < total) load_chunk(t + nwarps, nxt);
+        const int64_t C = q.C;
+        const unsigned inm = q.inm;
+        T v[8];
+        {
+            const int32_t jj[8] = {q.c0.x, q.c0.y, q.c0.z, q.c0.w, q.c1.x, q.c1.y, q.c1.z, q.c1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i) v[i] = ((inm >> i) & 1u) ? delta(jj[i]) : T(0);
+            if constexpr (W) {
+                const float4 w0 = __ldcs(reinterpret_cast<const float4 *>(w + q.e0));
+                const float4 w1 = __ldcs(reinterpret_cast<const float4 *>(w + q.e0 + 4));
+                v[0] *= (T)w0.x; v[1] *= (T)w0.y; v[2] *= (T)w0.z; v[3] *= (T)w0.w;
+                v[4] *= (T)w1.x; v[5] *= (T)w1.y; v[6] *= (T)w1.z; v[7] *= (T)w1.w;
+            }
+        }
+        // start bits of the lane's elements (sb) and end bits (eb: element i ends its row)
+        const unsigned sb = (q.word >> ((lane & 3) * 8)) & 0xFFu;
+        unsigned nx = __shfl_down_sync(FULL, sb, 1) & 1u;
+        if (lane == 31) nx = q.word_next & 1u;
+        const unsigned eb = (sb >> 1) | (nx << 7);
+        // ranks: row ends before this lane in the chunk
+        const int nend = __popc(eb);
+        int ecl = nend;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(FULL, ecl, d);
+            if (lane >= d) ecl += y;
+        }
+        const int64_t rbase = (int64_t)q.ebase + (ecl - nend);
+        // the lane's own pass: segments that start and end in the lane are
+        // written now; the one open at its start (started in an earlier lane)
+        // waits for the carry-in
+        T run = T(0), open_part = T(0);
+        bool seen = false;
+        int ei = 0, open_i = -1;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            if ((sb >> i) & 1u) {
+                seen = true;
+                run = T(0);
+            }
+            run += v[i];
+            if ((eb >> i) & 1u) {
+                if (seen) {
+                    if (((inm >> i) & 1u) && FJ_IDX_OK(19, rbase + ei, n_ranks)) rsum[rbase + ei] = run;
+                } else {
+                    open_i = i;
+                    open_part = run;
+                }
+                ++ei;
+            }
+        }
+        // carry across lanes: a lane's outgoing value is its open tail, or (no
+        // start and no end in it) the incoming value plus all eight elements
+        const bool closed = (eb >> 7) & 1u;
+        unsigned f = (seen || closed) ? 1u : 0u;
+        T x = closed ? T(0) : run;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const T y = __shfl_up_sync(FULL, x, d);
+            const unsigned g = __shfl_up_sync(FULL, f, d);
+            if (lane >= d && !f) {
+                x += y;
+                f |= g;
+            }
+        }
+        T in = __shfl_up_sync(FULL, x, 1);
+        if (lane == 0) in = T(0);  // the chunk's first segment: earlier chunks reach it through their carries
+        if (open_i >= 0) {
+            const int64_t rk = rbase;  // the open segment's end is the lane's first end
+            if (((inm >> open_i) & 1u) && FJ_IDX_OK(19, rk, n_ranks)) rsum[rk] = in + open_part;
+        }
+        if (lane == 31 && !closed && ((inm >> 7) & 1u)) carry[C] = x;
+    }
+}
+
+// Combines and applies the sums of the class's rows: rows [xa0, xa1) and
+// [xb0, xb1) one thread each (a row over kLongChunks chunks is left to the
+// warps below), then the class's long rows one warp each, in blocks from
+// first_long_block on.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_sweep_apply(int64_t xa0, int64_t xa1, int64_t xb0, int64_t xb1, const int32_t *__restrict__ long_rows,
+              int64_t nlong, unsigned first_long_block, const int64_t *__restrict__ rp,
+              const int32_t *__restrict__ rank, const T *__restrict__ rsum, const T *__restrict__ carry, T *dcur,
+              T *__restrict__ r, const T *__restrict__ h, const T *__restrict__ inv, double *__restrict__ zhat,
+              const int32_t *__restrict__ indeg, const T *__restrict__ om, Counters *ctr, int64_t n_rows)
+{
+    __shared__ unsigned long long red[2][8];
+    __shared__ int sbad;
+    if (*reinterpret_cast<volatile int *>(&ctr->done)) return;
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     unsigned long long my_push = 0, my_edges = 0;
     bool bad = false;
-
-    auto apply = [&](int64_t x, T rx, T hx, T ix, T ox, int32_t dgx) {
+    // row state streams through L2 with evict-first loads and stores, so that
+    // the increments the gathers read stay resident
+    auto apply = [&](int64_t x, T acc) {
+        T rx = __ldcs(r + x) + acc;
         T dx = T(0);
-        if (abs_t(rx) > hx) {
-            dx = ox * rx * ix;
-            zhat[x] += (double)dx;
+        if (abs_t(rx) > __ldcs(h + x)) {
+            const T ox = __ldcs(om + x);
+            dx = ox * rx * __ldcs(inv + x);
+            __stcs(zhat + x, __ldcs(zhat + x) + (double)dx);
             rx = (T(1) - ox) * rx;
             my_push += 1;
-            my_edges += (unsigned long long)dgx;
+            my_edges += (unsigned long long)__ldcs(indeg + x);
         }
         if (!isfinite(rx)) bad = true;
-        r[x] = rx;
+        __stcs(r + x, rx);
         dcur[x] = dx;
     };
-    // where node j's increment is: this sweep's buffer for an earlier class,
-    // else the previous sweep's (hub ids are ordered by class among
-    // themselves, so a hub is in an earlier class when it is below hlo)
-    auto src_of = [&](int32_t j) -> const T * {
-        const bool earlier = j < nhub ? j < hlo : j < lo;
-        return (earlier ? dcur_in : dprev) + j;
-    };
-
-    const int64_t nwarps = (int64_t)gridDim.x * NW;
-    const int64_t iend = item0 + nitems;
-    int64_t ii = item0 + (int64_t)blockIdx.x * NW + wl;
-    Item nxt;
-    if (ii < iend) nxt = items[ii];
-    for (; ii < iend; ii += nwarps) {
-        const Item it = nxt;
-        if (ii + nwarps < iend) nxt = items[ii + nwarps];
-        const int64_t r0 = it.r0, r1 = it.r1, k0 = it.k0;
-        const int nz = (int)(it.k1 - k0);
-        const bool ok = FJ_IDX_OK(11, r0, n_rows) && FJ_IDX_OK(12, r1, n_rows + 1) &&
-                        FJ_IDX_OK(13, r1 - r0, kSweepRows + 1) && FJ_IDX_OK(17, nz, kTileNnz + 1);
-        if (!ok) continue;
-        const int nch = (nz + 31) >> 5;
-        // ---- columns, then every gather as an asynchronous copy into vals
-        const int woff = (int)(k0 & 3);
-        if constexpr (W) {
-            const int64_t kb = k0 - woff;
-            const int ng = (woff + nz + 3) >> 2;
-            for (int gi = lane; gi < ng; gi += 32) cp_async_cg16(wts + 4 * gi, w + kb + 4 * gi);
-        }
-        {
-            int32_t jj[NCH];
-#pragma unroll
-            for (int c = 0; c < NCH; ++c) {
-                if (c < nch) {
-                    const int e = 32 * c + lane;
-                    jj[c] = e < nz ? ld_stream_i32(col + k0 + e) : -1;
-                }
-            }
-#pragma unroll
-            for (int c = 0; c < NCH; ++c) {
-                if (c < nch) {
-                    const int e = 32 * c + lane;
-                    const int32_t j = jj[c];
-                    if ((unsigned)j < (unsigned)nhot) vals[e] = hot[j];
-                    else if (j >= 0 && FJ_IDX_OK(15, j, n_rows)) cp_async_ca<(int)sizeof(T)>(vals + e, src_of(j));
-                    else vals[e] = T(0);
-                }
-            }
-            cp_async_commit();
-        }
-        if (it.slot < 0) {
-            // ---- tile: row state, start map and ranks while the gathers fly
-            int ra[2], re[2], rk[2];
-            T rr[2], rh[2], ri[2], ro[2];
-            int32_t rd[2];
-            sbits[lane] = 0u;
-            sacc[lane] = T(0);
-            sacc[lane + 32] = T(0);
-            __syncwarp();
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const int64_t x = r0 + lane + 32 * q;
-                ra[q] = re[q] = 0;
-                rk[q] = -1;
-                rr[q] = rh[q] = ri[q] = ro[q] = T(0);
-                rd[q] = 0;
-                if (x < r1) {
-                    ra[q] = (int)(rp[x] - k0);
-                    re[q] = (int)(rp[x + 1] - k0);
-                    rr[q] = r[x];
-                    rh[q] = h[x];
-                    ri[q] = inv[x];
-                    ro[q] = om[x];
-                    rd[q] = indeg[x];
-                    if (re[q] > ra[q] && FJ_IDX_OK(18, ra[q], nz) && FJ_IDX_OK(16, re[q], nz + 1))
-                        atomicOr(&sbits[ra[q] >> 5], 1u << (ra[q] & 31));
-                    else
-                        re[q] = ra[q];  // empty (or rejected) row: no sum
-                }
-            }
-            __syncwarp();
-            const unsigned myword = sbits[lane];
-            // exclusive prefix of the start counts over the 32 words (lane = word)
-            int incl = __popc(myword);
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const int y = __shfl_up_sync(FULL, incl, d);
-                if (lane >= d) incl += y;
-            }
-            const int wpre = incl - __popc(myword);
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const int wsrc = (ra[q] >> 5) & 31;
-                const int base = __shfl_sync(FULL, wpre, wsrc);
-                if (re[q] > ra[q]) rk[q] = base + __popc(sbits[wsrc] & ((1u << (ra[q] & 31)) - 1u));
-            }
-            cp_async_wait_all();
-            __syncwarp();
-            // ---- segmented sums, chunk by chunk
-            for (int c = 0; c < nch; ++c) {
-                const int e = 32 * c + lane;
-                T x = vals[e];
-                if constexpr (W) x = e < nz ? x * (T)wts[e + woff] : T(0);  // past nz the weight slot is unset
-                const unsigned word = sbits[c];
-                const unsigned le = word & (FULL >> (31 - lane));
-                const int ss = le ? 31 - __clz(le) : 0;
-#pragma unroll
-                for (int d = 1; d < 32; d <<= 1) {
-                    const T y = __shfl_up_sync(FULL, x, d);
-                    if (lane - d >= ss) x += y;
-                }
-                const int rank = __shfl_sync(FULL, wpre, c) + __popc(le) - 1;
-                const bool end = lane == 31 || ((word >> (lane + 1)) & 1u);
-                if (end && FJ_IDX_OK(19, rank, kSweepRows)) sacc[rank] += x;
-                __syncwarp();
-            }
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const int64_t x = r0 + lane + 32 * q;
-                if (x < r1) apply(x, rr[q] + (rk[q] >= 0 ? sacc[rk[q]] : T(0)), rh[q], ri[q], ro[q], rd[q]);
-            }
-        } else {
-            // ---- chunk of a long row: partial sum; the last chunk applies the update
-            cp_async_wait_all();
-            __syncwarp();
+    if (blockIdx.x < first_long_block) {
+        const int64_t na = xa1 - xa0, total = na + (xb1 - xb0);
+        for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+             t += (int64_t)first_long_block * blockDim.x) {
+            const int64_t x = t < na ? xa0 + t : xb0 + (t - na);
+            if (!FJ_IDX_OK(11, x, n_rows)) continue;
+            const int64_t a = __ldcs(rp + x), b = __ldcs(rp + x + 1);
             T acc = T(0);
-            for (int c = 0; c < nch; ++c) {
-                const int e = 32 * c + lane;
-                T x = vals[e];
-                if constexpr (W) x = e < nz ? x * (T)wts[e + woff] : T(0);  // past nz the weight slot is unset
-                acc += x;
+            if (b > a) {
+                const int64_t cs = a / kChunkE, ce = (b - 1) / kChunkE;
+                if (ce - cs > kLongChunks) continue;  // a warp combines it
+                for (int64_t c = cs; c < ce; ++c) acc += __ldcs(carry + c);
+                acc += __ldcs(rsum + __ldcs(rank + x));
             }
-            acc = warp_sum(acc);
-            const int slot = it.slot;
-            const int first = slot_first[slot], nchunk = slot_nchunk[slot];
-            int last = 0;
-            if (lane == 0) {
-                const int ci = (int)((k0 - rp[r0]) / kSweepChunk);
-                part[first + ci] = (double)acc;
-                __threadfence();
-                last = atomicAdd(&cnt[slot], 1) == nchunk - 1;
-            }
-            last = __shfl_sync(FULL, last, 0);
-            if (last) {
-                __threadfence();
-                double sum = 0.0;
-                for (int c = lane; c < nchunk; c += 32) sum += __ldcg(part + first + c);
-                sum = warp_sum(sum);
-                if (lane == 0) {
-                    cnt[slot] = 0;
-                    apply(r0, r[r0] + (T)sum, h[r0], inv[r0], om[r0], indeg[r0]);
-                }
-            }
+            apply(x, acc);
         }
-        __syncwarp();  // the buffers are refilled by the next item
+    } else {
+        const int64_t warp = ((int64_t)(blockIdx.x - first_long_block) * blockDim.x + threadIdx.x) >> 5;
+        const int64_t nwarps = ((int64_t)(gridDim.x - first_long_block) * blockDim.x) >> 5;
+        for (int64_t i = warp; i < nlong; i += nwarps) {
+            const int64_t x = long_rows[i];
+            if (!FJ_IDX_OK(12, x, n_rows)) continue;
+            const int64_t cs = rp[x] / kChunkE, ce = (rp[x + 1] - 1) / kChunkE;
+            T acc = T(0);
+            for (int64_t c = cs + lane; c < ce; c += 32) acc += carry[c];
+            acc = warp_sum(acc);
+            if (lane == 0) apply(x, acc + rsum[rank[x]]);
+        }
     }
-    // block totals -> three atomics per block
     my_push = warp_sum(my_push);
     my_edges = warp_sum(my_edges);
-    const unsigned anybad = __ballot_sync(FULL, bad);
+    const unsigned anybad = __ballot_sync(0xffffffffu, bad);
     if (threadIdx.x == 0) sbad = 0;
     __syncthreads();
     if (lane == 0) {
@@ -488,7 +502,7 @@ k_sweep_fused(const Item *__restrict__ items, int64_t item0, int64_t nitems, con
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned long long pp = 0, ee = 0;
-        for (int i = 0; i < NW; ++i) {
+        for (int i = 0; i < 8; ++i) {
             pp += red[0][i];
             ee += red[1][i];
         }
@@ -499,6 +513,40 @@ k_sweep_fused(const Item *__restrict__ items, int64_t item0, int64_t nitems, con
             atomicAdd(&ctr->edges, ee);
         }
     }
+}
+
+// ---- chunk plan construction
+
+__global__ void k_start_bits(int64_t n, int64_t nnz, const int64_t *__restrict__ rp, uint32_t *__restrict__ starts,
+                             int32_t *__restrict__ nonempty)
+{
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x <= n; x += (int64_t)gridDim.x * blockDim.x) {
+        if (x == n) {
+            atomicOr(&starts[nnz >> 5], 1u << (nnz & 31));  // closes the last row
+            continue;
+        }
+        const int64_t a = rp[x];
+        const bool ne = rp[x + 1] > a;
+        nonempty[x] = ne ? 1 : 0;
+        if (ne) atomicOr(&starts[a >> 5], 1u << (a & 31));
+    }
+}
+
+// rows that end in chunk C: its end bits are the start bits one position on
+struct EndCount {
+    const uint32_t *starts;
+    __device__ long long operator()(int64_t c) const
+    {
+        long long k = 0;
+        for (int64_t i = 8 * c; i < 8 * c + 8; ++i) k += __popc((starts[i] >> 1) | (starts[i + 1] << 31));
+        return k;
+    }
+};
+
+__global__ void k_narrow_i32(int64_t n, const long long *__restrict__ in, int32_t *__restrict__ out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (int32_t)in[i];
 }
 
 // ============================================================== FP64 certificate
@@ -1044,7 +1092,7 @@ static fj_status ws_grow(fj_graph *g, int64_t entries, int ngraphs)
 {
     Workspace &ws = g->ws;
     if (entries > ws.cap_n) {
-        void **bufs[] = {&ws.r, &ws.h, &ws.da, &ws.db, &ws.om};
+        void **bufs[] = {&ws.r, &ws.h, &ws.da, &ws.db, &ws.om, &ws.rsum};
         for (void **p : bufs) {
             dev_free(*p);
             *p = nullptr;
@@ -1086,7 +1134,7 @@ struct Plan {
     const DevCSR *c = nullptr;  // CSR the push runs on
     const int32_t *perm = nullptr;
     const ItemPlan *wip = nullptr;  // warp-tile items (certificate, batch sweep)
-    const ItemPlan *sip = nullptr;  // sweep-tile items (single-vector sweep)
+    const ChunkPlan *cp = nullptr;  // chunk plan (single-vector sweep)
     bool mc = false;
 };
 
@@ -1171,11 +1219,11 @@ __global__ void k_gather_rp(int64_t nb, const int32_t *__restrict__ blk_row, con
 static fj_status build_items(fj_graph *g, const DevCSR &c, const Colouring *cl, ItemPlan &ip, cudaStream_t st,
                              TileKind kind)
 {
-    const bool sweep_tiles = kind == kTileSweep, warp_tiles = kind == kTileWarp;
-    const int64_t nb = sweep_tiles ? c.nsblocks : (warp_tiles ? c.nwblocks : c.nblocks);
-    const int32_t *blk_row = sweep_tiles ? c.sblk_row : (warp_tiles ? c.wblk_row : c.blk_row);
-    const int64_t long_row = sweep_tiles ? 2 * kSweepNnz : (warp_tiles ? 2 * kWarpNnz : 2 * kBlockNnz);
-    const int64_t chunk = sweep_tiles ? kSweepChunk : (warp_tiles ? kWarpChunk : kChunkNnz);
+    const bool warp_tiles = kind == kTileWarp;
+    const int64_t nb = warp_tiles ? c.nwblocks : c.nblocks;
+    const int32_t *blk_row = warp_tiles ? c.wblk_row : c.blk_row;
+    const int64_t long_row = warp_tiles ? 2 * kWarpNnz : 2 * kBlockNnz;
+    const int64_t chunk = warp_tiles ? kWarpChunk : kChunkNnz;
     std::vector<int32_t> br((size_t)nb + 1);
     std::vector<long long> bk((size_t)nb + 1);
     long long *bk_d = nullptr;
@@ -1268,18 +1316,14 @@ static fj_status make_plan(fj_graph *g, const fj_solve_opts *o, cudaStream_t st,
     if (!p.mc) {
         p.c = &g->csr;
         if (!g->wplan_csr.built) FJ_CHECK(build_items(g, g->csr, nullptr, g->wplan_csr, st, kTileWarp));
-        if (!g->splan_csr.built) FJ_CHECK(build_items(g, g->csr, nullptr, g->splan_csr, st, kTileSweep));
         p.wip = &g->wplan_csr;
-        p.sip = &g->splan_csr;
         return FJ_OK;
     }
     FJ_CHECK(ensure_colouring(g, o->palette, st));
     p.c = &g->colr.pcsr;
     p.perm = g->colr.perm;
     if (!g->wplan_pcsr.built) FJ_CHECK(build_items(g, g->colr.pcsr, &g->colr, g->wplan_pcsr, st, kTileWarp));
-    if (!g->splan_pcsr.built) FJ_CHECK(build_items(g, g->colr.pcsr, &g->colr, g->splan_pcsr, st, kTileSweep));
     p.wip = &g->wplan_pcsr;
-    p.sip = &g->splan_pcsr;
     return FJ_OK;
 }
 
@@ -1292,62 +1336,187 @@ fj_status plain_items(fj_graph *g, cudaStream_t st, const ItemPlan **out)
     return FJ_OK;
 }
 
-// Resident blocks of the fused sweep kernel on this device for dyn bytes of
-// dynamic shared memory (persistent grid size).  The first call per kernel
-// instance also allows it the whole shared-memory budget.
+
+struct FlagLoad {
+    const int32_t *a;
+    __device__ long long operator()(int64_t i) const { return (long long)a[i]; }
+};
+
+struct LongRowPred {
+    const int64_t *rp;
+    __device__ bool operator()(int64_t x) const
+    {
+        const int64_t a = rp[x], b = rp[x + 1];
+        return b > a && (b - 1) / kChunkE - a / kChunkE > kLongChunks;
+    }
+};
+
+// Chunk plan of CSR c: start bits, ranks, per-class row and nonzero ranges
+// (cl = nullptr: the whole graph as one class), long rows grouped by class.
+static fj_status build_chunk_plan(fj_graph *g, const DevCSR &c, const Colouring *cl, ChunkPlan &cp, cudaStream_t st)
+{
+    const int64_t n = c.n, nnz = c.nnz;
+    cp.nch = std::max<int64_t>(1, ceil_div(nnz, kChunkE));
+    const int64_t nwords = 8 * (cp.nch + 1);
+    FJ_CUDA(dev_malloc(&cp.starts, sizeof(uint32_t) * (size_t)nwords));
+    FJ_CUDA(dev_malloc(&cp.endbase, sizeof(int32_t) * (size_t)cp.nch));
+    FJ_CUDA(dev_malloc(&cp.rank, sizeof(int32_t) * (size_t)std::max<int64_t>(n, 1)));
+    int32_t *nonempty = nullptr;
+    long long *excl = nullptr;
+    FJ_CUDA(dev_malloc(&nonempty, sizeof(int32_t) * (size_t)std::max<int64_t>(n, 1)));
+    FJ_CUDA(dev_malloc(&excl, sizeof(long long) * (size_t)(std::max(n, cp.nch) + 1)));
+    FJ_CUDA(cudaMemsetAsync(cp.starts, 0, sizeof(uint32_t) * (size_t)nwords, st));
+    k_start_bits<<<grid_for(n + 1, 256), 256, 0, st>>>(n, nnz, c.row_ptr, cp.starts, nonempty);
+    FJ_CUDA(cudaGetLastError());
+    Workspace &ws = g->ws;
+    FJ_CHECK(ws_status(ws, scan_tiles(std::max(n, cp.nch), 256 * 8)));
+    if (n > 0) {
+        FJ_CUDA(scan<256, 8>(n, FlagLoad{nonempty}, excl, ws.count, ws.status, ws.tile_ctr, g->err, st));
+        k_narrow_i32<<<grid_for(n, 256), 256, 0, st>>>(n, excl, cp.rank);
+    }
+    FJ_CUDA(scan<256, 8>(cp.nch, EndCount{cp.starts}, excl, ws.count, ws.status, ws.tile_ctr, g->err, st));
+    k_narrow_i32<<<grid_for(cp.nch, 256), 256, 0, st>>>(cp.nch, excl, cp.endbase);
+    FJ_CUDA(cudaGetLastError());
+    // class ranges
+    const int ncls = cl ? cl->ncolours : 1;
+    cp.row0.clear();
+    cp.row1.clear();
+    for (int k = 0; k < ncls; ++k) {
+        if (cl) {
+            const bool hubs = cl->nhub > 0;
+            cp.row0.push_back(hubs ? cl->hub_row[(size_t)k] : 0);
+            cp.row1.push_back(hubs ? cl->hub_row[(size_t)k + 1] : 0);
+            cp.row0.push_back(cl->class_row[(size_t)k]);
+            cp.row1.push_back(cl->class_row[(size_t)k + 1]);
+        } else {
+            cp.row0.push_back(0);
+            cp.row1.push_back(0);
+            cp.row0.push_back(0);
+            cp.row1.push_back(n);
+        }
+    }
+    std::vector<int64_t> hrp((size_t)n + 1);
+    FJ_CUDA(cudaMemcpyAsync(hrp.data(), c.row_ptr, sizeof(int64_t) * (size_t)(n + 1), cudaMemcpyDeviceToHost, st));
+    // long rows, in row order
+    int32_t *lr = nonempty;  // reused: the flags are no longer needed
+    FJ_CUDA(compact<256, 8>(n, LongRowPred{c.row_ptr}, lr, ws.count, ws.status, ws.tile_ctr, g->err, st));
+    long long nl = 0;
+    FJ_CUDA(cudaMemcpyAsync(&nl, ws.count, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    FJ_CUDA(cudaStreamSynchronize(st));
+    std::vector<int32_t> hl((size_t)nl);
+    if (nl > 0) FJ_CUDA(cudaMemcpy(hl.data(), lr, sizeof(int32_t) * (size_t)nl, cudaMemcpyDeviceToHost));
+    cp.k0.assign(cp.row0.size(), 0);
+    cp.k1.assign(cp.row0.size(), 0);
+    for (size_t i = 0; i < cp.row0.size(); ++i) {
+        cp.k0[i] = hrp[(size_t)cp.row0[i]];
+        cp.k1[i] = hrp[(size_t)cp.row1[i]];
+    }
+    // group the long rows by class (each class's two ranges)
+    std::vector<int32_t> grouped;
+    grouped.reserve(hl.size());
+    cp.long_off.assign((size_t)ncls + 1, 0);
+    for (int k = 0; k < ncls; ++k) {
+        for (int part = 0; part < 2; ++part) {
+            const int64_t a = cp.row0[(size_t)(2 * k + part)], b = cp.row1[(size_t)(2 * k + part)];
+            auto lo_it = std::lower_bound(hl.begin(), hl.end(), (int32_t)a);
+            for (auto it = lo_it; it != hl.end() && *it < b; ++it) grouped.push_back(*it);
+        }
+        cp.long_off[(size_t)k + 1] = (int64_t)grouped.size();
+    }
+    FJ_CUDA(dev_malloc(&cp.long_rows, sizeof(int32_t) * std::max<size_t>(grouped.size(), 1)));
+    if (!grouped.empty())
+        FJ_CUDA(cudaMemcpy(cp.long_rows, grouped.data(), sizeof(int32_t) * grouped.size(), cudaMemcpyHostToDevice));
+    dev_free(nonempty);
+    dev_free(excl);
+    cp.built = true;
+    return read_dev_error(g, st);
+}
+
+// Resident gather blocks per device for dyn bytes of hot table (persistent grid).
 template <typename T, bool W>
-static int64_t sweep_blocks(int dyn)
+static int64_t gather_blocks(int dyn)
 {
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_sweep_fused<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFusedSmemBudget);
+        cudaFuncSetAttribute(k_sweep_gather<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, kHotBytes);
         attr = true;
     }
     int dev = 0, sms = 0, per = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep_fused<T, W>, 32 * fused_warps<T, W>(), dyn);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep_gather<T, W>, kGatherThreads, dyn);
     return std::max(1, sms * std::max(1, per));
 }
 
+static int device_sms()
+{
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                      cudaSuccess)
+            sms = 152;
+    }
+    return sms;
+}
+
 template <typename T, bool W>
-static fj_status launch_fused(fj_graph *g, const Plan &p, cudaStream_t st, Run &run, T *dcur, const T *dprev)
+static fj_status launch_classes(fj_graph *g, const Plan &p, cudaStream_t st, Run &run, T *dcur, const T *dprev)
 {
     Workspace &ws = g->ws;
     const DevCSR &c = *p.c;
-    const ItemPlan &wp = *p.sip;
+    const ChunkPlan &cp = *p.cp;
     T *r = reinterpret_cast<T *>(ws.r);
     const T *h = reinterpret_cast<const T *>(ws.h);
     const T *inv;
     if constexpr (sizeof(T) == 4) inv = reinterpret_cast<const T *>(c.inv32);
     else inv = reinterpret_cast<const T *>(c.inv64);
     const T *om = reinterpret_cast<const T *>(ws.om);
-    constexpr int NW = fused_warps<T, W>();
+    T *rsum = reinterpret_cast<T *>(ws.rsum), *carry = reinterpret_cast<T *>(ws.carry);
     // hub prefix of the colour order (multicolour only): its first nhot ids go to the hot table
     const int nhub = p.mc ? (int)g->colr.nhub : 0;
-    const int nhot = std::max(0, std::min<int>(nhub, fused_hot_cap<T, W>()));
-    const int dyn = NW * fused_warp_bytes<T, W>() + nhot * (int)sizeof(T);
-    const int64_t nres = sweep_blocks<T, W>(dyn);
-    for (size_t cl = 0; cl + 1 < wp.class_item.size(); ++cl) {
-        const int64_t i0 = wp.class_item[cl], ni = wp.class_item[cl + 1] - i0;
-        if (ni <= 0) continue;
+    const int nhot = std::max(0, std::min<int>(nhub, kHotBytes / (int)sizeof(T)));
+    const int dyn = nhot * (int)sizeof(T);
+    const int64_t nres = gather_blocks<T, W>(dyn);
+    const int sms = device_sms();
+    const int ncls = (int)cp.long_off.size() - 1;
+    for (int cl = 0; cl < ncls; ++cl) {
+        const int64_t ka0 = cp.k0[(size_t)2 * cl], ka1 = cp.k1[(size_t)2 * cl];
+        const int64_t kb0 = cp.k0[(size_t)2 * cl + 1], kb1 = cp.k1[(size_t)2 * cl + 1];
+        const int64_t xa0 = cp.row0[(size_t)2 * cl], xa1 = cp.row1[(size_t)2 * cl];
+        const int64_t xb0 = cp.row0[(size_t)2 * cl + 1], xb1 = cp.row1[(size_t)2 * cl + 1];
+        const int64_t rows = (xa1 - xa0) + (xb1 - xb0);
+        if (rows <= 0) continue;
+        const int64_t chunks = (ka1 > ka0 ? ceil_div(ka1 - ka0, kChunkE) + 1 : 0) +
+                               (kb1 > kb0 ? ceil_div(kb1 - kb0, kChunkE) + 1 : 0);
         // the class's first row (first hub row): every column below it belongs to an earlier class
-        const int lo = p.mc ? (int)g->colr.class_row[cl] : 0;
-        const int hlo = nhub > 0 ? (int)g->colr.hub_row[cl] : 0;
-        const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(ni, NW), nres);
+        const int lo = p.mc ? (int)g->colr.class_row[(size_t)cl] : 0;
+        const int hlo = nhub > 0 ? (int)g->colr.hub_row[(size_t)cl] : 0;
         FJ_CHECK(run.before(st));
-        k_sweep_fused<T, W><<<grid, 32 * NW, dyn, st>>>(wp.items, i0, ni, c.row_ptr, c.col, c.w, lo, nhot, nhub, hlo,
-                                                        dcur, dprev, dcur, r, h, inv, ws.zhat, c.indeg, om,
-                                                        wp.slot_first, wp.slot_nchunk, wp.part, wp.cnt, ws.ctr, c.n);
+        if (chunks > 0) {
+            const unsigned grid =
+                (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(chunks, kGatherThreads / 32), nres));
+            k_sweep_gather<T, W><<<grid, kGatherThreads, dyn, st>>>(ka0, ka1, kb0, kb1, c.col, c.w, cp.starts,
+                                                                     cp.endbase, lo, nhot, nhub, hlo, dcur, dprev,
+                                                                     rsum, carry, ws.ctr, c.n, c.n);
+            FJ_CUDA(cudaGetLastError());
+        }
+        const int64_t nlong = cp.long_off[(size_t)cl + 1] - cp.long_off[(size_t)cl];
+        const unsigned rgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(rows, 256), (int64_t)sms * 8));
+        const unsigned lgrid = nlong > 0 ? (unsigned)std::min<int64_t>(ceil_div(nlong, 8), (int64_t)sms * 4) : 0;
+        k_sweep_apply<T><<<rgrid + lgrid, 256, 0, st>>>(xa0, xa1, xb0, xb1, cp.long_rows + cp.long_off[(size_t)cl],
+                                                        nlong, rgrid, c.row_ptr, cp.rank, rsum, carry, dcur, r, h,
+                                                        inv, ws.zhat, c.indeg, om, ws.ctr, c.n);
         FJ_CUDA(cudaGetLastError());
         FJ_CHECK(run.after(st));
+        ++run.launches;  // the gather launch
     }
     return FJ_OK;
 }
 
-// One sweep (multicolour: one launch per colour class, in order) or round
-// (Jacobi: one launch over all rows), then the stop test.  The two increment
-// buffers swap roles every sweep.
+// One sweep (multicolour: two launches per colour class, in order) or round
+// (Jacobi: the whole graph as one class), then the stop test.  The two
+// increment buffers swap roles every sweep.
 template <typename T>
 static fj_status launch_sweep(fj_graph *g, const Plan &p, cudaStream_t st, Run &run, int64_t sweep)
 {
@@ -1355,8 +1524,8 @@ static fj_status launch_sweep(fj_graph *g, const Plan &p, cudaStream_t st, Run &
     T *bufs[2] = {reinterpret_cast<T *>(ws.da), reinterpret_cast<T *>(ws.db)};
     T *dcur = bufs[sweep & 1];
     const T *dprev = bufs[(sweep - 1) & 1];
-    if (p.c->w) FJ_CHECK((launch_fused<T, true>(g, p, st, run, dcur, dprev)));
-    else FJ_CHECK((launch_fused<T, false>(g, p, st, run, dcur, dprev)));
+    if (p.c->w) FJ_CHECK((launch_classes<T, true>(g, p, st, run, dcur, dprev)));
+    else FJ_CHECK((launch_classes<T, false>(g, p, st, run, dcur, dprev)));
     k_end_sweep<<<1, 1, 0, st>>>(ws.ctr);
     FJ_CUDA(cudaGetLastError());
     ++run.launches;
@@ -1561,6 +1730,18 @@ static fj_status solve_t(fj_graph *g, const double *s, const double *z0, const f
     Workspace &ws = g->ws;
     Plan p;
     FJ_CHECK(make_plan(g, o, st, p));
+    {
+        ChunkPlan &cpl = p.mc ? g->cplan_pcsr : g->cplan_csr;
+        if (!cpl.built) FJ_CHECK(build_chunk_plan(g, *p.c, p.mc ? &g->colr : nullptr, cpl, st));
+        p.cp = &cpl;
+        if (cpl.nch > ws.cap_carry) {
+            dev_free(ws.carry);
+            ws.carry = nullptr;
+            FJ_CUDA(dev_malloc(&ws.carry, sizeof(double) * (size_t)cpl.nch));
+            ws.cap_carry = cpl.nch;
+            ws.gen++;
+        }
+    }
     const DevCSR &c = *p.c;
     const double epsp = o->sigma * o->eps / (o->c + o->sigma);
 
