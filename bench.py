@@ -133,7 +133,11 @@ SWEEP_KERNEL = "k_sweep_gather + k_sweep_apply (one colour class)"
 # multiple of the dense bytes it streams, from one ncu capture per graph kind
 # (key: generator, single vector).  Filled in from captures listed under
 # profiles/; a kind without a capture reports traffic null.
-SWEEP_TRAFFIC_RATIO = {}
+SWEEP_TRAFFIC_RATIO = {
+    ("rmat_und", True): (109.6 / 148.3, "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_sweep_gather + "
+                         "k_sweep_apply over the 16 class launches of one sweep of undirected R-MAT s23 (109.6 MB "
+                         "per class against 148.3 MB dense), scaled to this launch's dense bytes"),
+}
 
 
 def roofline_of(p, kernel, traffic_key=None):
@@ -164,18 +168,33 @@ def roofline_of(p, kernel, traffic_key=None):
     return r
 
 
+ARM_PARTS = {"0xd4f": "Arm Neoverse-V2 (NVIDIA Grace)", "0xd40": "Arm Neoverse-V1", "0xd0c": "Arm Neoverse-N1"}
+
+
 def host_cpu():
+    """Host CPU model (lscpu, else /proc/cpuinfo) and logical core count."""
     model = None
     try:
-        with open("/proc/cpuinfo") as f:
-            for line in f:
-                low = line.lower()
-                if low.startswith("model name") or low.startswith("cpu part") and model is None:
-                    model = line.split(":", 1)[1].strip()
-                    if low.startswith("model name"):
-                        break
-    except OSError:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
         pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    low = line.lower()
+                    if low.startswith("model name"):
+                        model = line.split(":", 1)[1].strip()
+                        break
+                    if low.startswith("cpu part") and model is None:
+                        part = line.split(":", 1)[1].strip()
+                        model = ARM_PARTS.get(part, "Arm CPU part " + part)
+        except OSError:
+            pass
     return {"model": model, "host_cores": os.cpu_count()}
 
 

@@ -342,7 +342,8 @@ k_sweep_gather(int64_t ka0, int64_t ka1, int64_t kb0, int64_t kb1, const int32_t
         q.c0 = __ldcs(reinterpret_cast<const int4 *>(col + q.e0));
         q.c1 = __ldcs(reinterpret_cast<const int4 *>(col + q.e0 + 4));
         q.word = __ldg(starts + q.C * 8 + (lane >> 2));
-        q.word_next = lane == 31 ? __ldg(starts + (q.C + 1) * 8) : 0u;
+        // the last lane of each word also needs the next word's first bit
+        q.word_next = (lane & 3) == 3 ? __ldg(starts + q.C * 8 + (lane >> 2) + 1) : 0u;
         q.ebase = __ldg(endbase + q.C);
     };
     ChunkRegs nxt;
@@ -366,18 +367,14 @@ k_sweep_gather(int64_t ka0, int64_t ka1, int64_t kb0, int64_t kb1, const int32_t
         }
         // start bits of the lane's elements (sb) and end bits (eb: element i ends its row)
         const unsigned sb = (q.word >> ((lane & 3) * 8)) & 0xFFu;
-        unsigned nx = __shfl_down_sync(FULL, sb, 1) & 1u;
-        if (lane == 31) nx = q.word_next & 1u;
+        const unsigned nx = (lane & 3) == 3 ? (q.word_next & 1u) : ((q.word >> ((lane & 3) * 8 + 8)) & 1u);
         const unsigned eb = (sb >> 1) | (nx << 7);
-        // ranks: row ends before this lane in the chunk
-        const int nend = __popc(eb);
-        int ecl = nend;
+        // ranks: row ends before this lane in the chunk, one ballot per element slot
+        const unsigned lt = lanemask_lt();
+        int ebefore = 0;
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const int y = __shfl_up_sync(FULL, ecl, d);
-            if (lane >= d) ecl += y;
-        }
-        const int64_t rbase = (int64_t)q.ebase + (ecl - nend);
+        for (int i = 0; i < 8; ++i) ebefore += __popc(__ballot_sync(FULL, (eb >> i) & 1u) & lt);
+        const int64_t rbase = (int64_t)q.ebase + ebefore;
         // the lane's own pass: segments that start and end in the lane are
         // written now; the one open at its start (started in an earlier lane)
         // waits for the carry-in
@@ -404,16 +401,15 @@ k_sweep_gather(int64_t ka0, int64_t ka1, int64_t kb0, int64_t kb1, const int32_t
         // carry across lanes: a lane's outgoing value is its open tail, or (no
         // start and no end in it) the incoming value plus all eight elements
         const bool closed = (eb >> 7) & 1u;
-        unsigned f = (seen || closed) ? 1u : 0u;
         T x = closed ? T(0) : run;
+        // segmented inclusive scan: a lane with a start or a closed end heads a
+        // segment (its value does not depend on earlier lanes)
+        const unsigned heads = __ballot_sync(FULL, seen || closed) & (lt | (1u << lane));
+        const int hs = heads ? 31 - __clz(heads) : 0;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             const T y = __shfl_up_sync(FULL, x, d);
-            const unsigned g = __shfl_up_sync(FULL, f, d);
-            if (lane >= d && !f) {
-                x += y;
-                f |= g;
-            }
+            if (lane - d >= hs) x += y;
         }
         T in = __shfl_up_sync(FULL, x, 1);
         if (lane == 0) in = T(0);  // the chunk's first segment: earlier chunks reach it through their carries
@@ -1475,9 +1471,8 @@ static fj_status launch_classes(fj_graph *g, const Plan &p, cudaStream_t st, Run
     T *rsum = reinterpret_cast<T *>(ws.rsum), *carry = reinterpret_cast<T *>(ws.carry);
     // hub prefix of the colour order (multicolour only): its first nhot ids go to the hot table
     const int nhub = p.mc ? (int)g->colr.nhub : 0;
-    const int nhot = std::max(0, std::min<int>(nhub, kHotBytes / (int)sizeof(T)));
-    const int dyn = nhot * (int)sizeof(T);
-    const int64_t nres = gather_blocks<T, W>(dyn);
+    const int hot_cap = std::max(0, std::min<int>(nhub, kHotBytes / (int)sizeof(T)));
+    const int64_t nres = gather_blocks<T, W>(hot_cap * (int)sizeof(T));
     const int sms = device_sms();
     const int ncls = (int)cp.long_off.size() - 1;
     for (int cl = 0; cl < ncls; ++cl) {
@@ -1496,6 +1491,12 @@ static fj_status launch_classes(fj_graph *g, const Plan &p, cudaStream_t st, Run
         if (chunks > 0) {
             const unsigned grid =
                 (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(chunks, kGatherThreads / 32), nres));
+            // a block stages the table only when its share of the class's
+            // gathers is large beside it (a small graph's increments stay in
+            // L2 anyway, and the copy would dominate its short launches)
+            const int64_t per_block = ((ka1 - ka0) + (kb1 - kb0)) / (int64_t)grid;
+            const int nhot = per_block >= 2 * (int64_t)hot_cap ? hot_cap : 0;
+            const int dyn = nhot * (int)sizeof(T);
             k_sweep_gather<T, W><<<grid, kGatherThreads, dyn, st>>>(ka0, ka1, kb0, kb1, c.col, c.w, cp.starts,
                                                                      cp.endbase, lo, nhot, nhub, hlo, dcur, dprev,
                                                                      rsum, carry, ws.ctr, c.n, c.n);
