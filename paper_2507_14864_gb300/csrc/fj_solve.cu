@@ -310,7 +310,8 @@ k_sweep_gather(int64_t ka0, int64_t ka1, int64_t kb0, int64_t kb1, const int32_t
     const int64_t na = ka1 > ka0 ? (ka1 - 1) / kChunkE - ca0 + 1 : 0;
     const int64_t nb = kb1 > kb0 ? (kb1 - 1) / kChunkE - cb0 + 1 : 0;
     const int64_t total = na + nb;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    // consecutive chunks go to consecutive blocks (a short class spreads over the SMs)
+    const int64_t warp = (int64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const uint64_t keep = l2_keep_policy();
     auto delta = [&](int32_t j) -> T {
@@ -856,35 +857,34 @@ k_certify(const Item *__restrict__ items, int64_t nitems, const int64_t *__restr
                 if (mine[half]) finish(x, rx[half], dec[half]);
             }
         } else {
-            FF acc{0.f, 0.f};
-            pair_terms(it.k0 + lane, it.k1, 32, acc);
-            acc = warp_ff_sum(acc);
+            // a chunk of a long row: its compensated (Dot2) partial; the last
+            // chunk to finish joins the chunks' partials and decides exactly.
+            // (A long row's pair-arithmetic bound grows with its length, so the
+            // FP32 decision would leave it open near convergence, and one warp
+            // re-summing a hub row of 10^5-10^6 nonzeros would serialise the
+            // certificate; the chunks share that work instead.)
+            DD acc{0.0, 0.0};
+            exact_terms(it.k0 + lane, it.k1, 32, acc);
+            acc = warp_dd_sum(acc);
             const int slot = it.slot;
             const int first = slot_first[slot], nch = slot_nchunk[slot];
             const int ci = (int)((it.k0 - rp[r0]) / kWarpChunk);
             int last = 0;
             if (lane == 0) {
-                part[2 * (first + ci)] = (double)acc.s + (double)acc.c;
+                part[2 * (first + ci)] = acc.hi;
+                part[2 * (first + ci) + 1] = acc.lo;
                 __threadfence();
                 last = atomicAdd(&cnt[slot], 1) == nch - 1;
             }
             last = __shfl_sync(FULL, last, 0);
             if (last) {
                 __threadfence();
-                double sum = 0.0;
-                for (int c = lane; c < nch; c += 32) sum += __ldcg(part + 2 * (first + c));
-                sum = warp_sum(sum);
-                const int64_t a = rp[r0], e = rp[r0 + 1];
+                DD d{0.0, 0.0};
+                for (int c = lane; c < nch; c += 32)
+                    d = dd_merge(d, DD{__ldcg(part + 2 * (first + c)), __ldcg(part + 2 * (first + c) + 1)});
+                d = warp_dd_sum(d);
                 int dec;
-                // per chunk: kWarpChunk / 32 pair terms per lane; the chunks'
-                // values are summed with at most nch + 64 FP64 roundings
-                double rx = pair_residual(r0, kWarpChunk / 32, (int64_t)nch + 64, sum, dec);
-                if (dec < 0) {
-                    DD d{0.0, 0.0};
-                    exact_terms(a + lane, e, 32, d);
-                    d = warp_dd_sum(d);
-                    rx = exact_residual(r0, d, dec);
-                }
+                const double rx = exact_residual(r0, d, dec);
                 if (lane == 0) {
                     cnt[slot] = 0;
                     finish(r0, rx, dec);
@@ -1489,13 +1489,15 @@ static fj_status launch_classes(fj_graph *g, const Plan &p, cudaStream_t st, Run
         const int hlo = nhub > 0 ? (int)g->colr.hub_row[(size_t)cl] : 0;
         FJ_CHECK(run.before(st));
         if (chunks > 0) {
-            const unsigned grid =
+            unsigned grid =
                 (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(chunks, kGatherThreads / 32), nres));
             // a block stages the table only when its share of the class's
             // gathers is large beside it (a small graph's increments stay in
-            // L2 anyway, and the copy would dominate its short launches)
+            // L2 anyway, and the copy would dominate its short launches);
+            // without it, a short class takes one chunk per SM at a time
             const int64_t per_block = ((ka1 - ka0) + (kb1 - kb0)) / (int64_t)grid;
             const int nhot = per_block >= 2 * (int64_t)hot_cap ? hot_cap : 0;
+            if (nhot == 0) grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(chunks, nres));
             const int dyn = nhot * (int)sizeof(T);
             k_sweep_gather<T, W><<<grid, kGatherThreads, dyn, st>>>(ka0, ka1, kb0, kb1, c.col, c.w, cp.starts,
                                                                      cp.endbase, lo, nhot, nhub, hlo, dcur, dprev,
