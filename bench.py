@@ -373,6 +373,8 @@ def run_gpu(args):
         return res
     if args.check_every:
         opts["check_every"] = args.check_every
+    if args.max_sweeps:
+        opts["max_sweeps"] = args.max_sweeps
 
     def barrier():
         if world > 1:
@@ -959,6 +961,7 @@ def main():
                     help="add one traced solve's [ms, sweeps, max|r|/s', kind] rows to detail (fj_solve_trace)")
     ap.add_argument("--schedule", type=int, default=2, help="1 Jacobi rounds, 2 multicolour")
     ap.add_argument("--check-every", type=int, default=0)
+    ap.add_argument("--max-sweeps", type=int, default=0, help="sweeps per pass before a refinement restart")
     ap.add_argument("--cpu-scale", type=int, default=None,
                     help="R-MAT scale of the CPU-baseline sample (default: the full workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -84,8 +84,11 @@ typedef struct {
     double sigma;        /* threshold sigma of Alg. 2 (default 1e-5) */
     int precision;       /* FJ_PREC_* */
     int schedule;        /* FJ_SCHED_* */
-    int64_t max_sweeps;  /* cap on rounds/sweeps per refinement pass (default 100000) */
-    int max_refine;      /* cap on FP64 certify-and-restart passes (default 8) */
+    int64_t max_sweeps;  /* cap on rounds/sweeps per pass (default 100000; FP32 passes also stop
+                            after 48): a pass that reaches it is certified and restarted from
+                            its FP64 residual like one that stopped pushing */
+    int max_refine;      /* cap on FP64 certify-and-restart passes that did not halve the
+                            certified relative residual (default 8) */
     int palette;         /* MULTICOLOUR: colours allowed (default 16; 0 = as many as greedy
                             colouring needs).  When the palette runs out a node joins the
                             class where its neighbours' weight is least; those same-class

@@ -241,6 +241,7 @@ __device__ long long g_fj_dbg[4];
 #define FJ_HOT_KB 192
 #endif
 constexpr int kGatherThreads = FJ_GATHER_THREADS;
+constexpr int64_t kFp32PassSweeps = 48;  // sweeps of an FP32 pass before a restart from the FP64 residual
 constexpr int kHotBytes = FJ_HOT_KB * 1024;
 static_assert(kHotBytes <= kHubMax * 4 + 1024, "the hot table holds at most the hub prefix");
 
@@ -1849,8 +1850,15 @@ static fj_status solve_t(fj_graph *g, const double *s, const double *z0, const f
                 if (e[i]) cudaEventDestroy(e[i]);
         }
     } ev_free{tev};
+    // FP32 passes are restarted from the exact FP64 residual every
+    // kFp32PassSweeps sweeps (iterative refinement): past that the FP32
+    // residual drifts from the true one and further sweeps stall (a capped
+    // pass on undirected R-MAT s24 cut the sweeps to certify from 163 to 96)
+    const int64_t pass_cap = sizeof(T) == 4 ? std::min<int64_t>(o->max_sweeps, kFp32PassSweeps) : o->max_sweeps;
+    double prev_rel = INFINITY, last_rel = INFINITY;
+    int strikes = 0;  // restarts that did not halve the relative residual (bounded by max_refine)
     for (;;) {
-        k_pass_reset<<<1, 1, 0, st>>>(ws.ctr, o->max_sweeps);
+        k_pass_reset<<<1, 1, 0, st>>>(ws.ctr, pass_cap);
         FJ_CUDA(cudaGetLastError());
         ++run.launches;
         for (;;) {
@@ -1885,6 +1893,7 @@ static fj_status solve_t(fj_graph *g, const double *s, const double *z0, const f
                 viol += ws.gstat_host[i * kGs + 5];
                 rel = std::max(rel, ws.gstat_host[i * kGs + 3]);
             }
+            last_rel = rel;
             return trace_row(rel, 1.0);
         };
         double viol = 0.0;
@@ -1900,15 +1909,26 @@ static fj_status solve_t(fj_graph *g, const double *s, const double *z0, const f
             if (!cleared) break;
         }
         if (viol == 0.0) break;
-        if (done == 2) {
-            result = FJ_ERR_NOT_CONVERGED;
-            set_error("sweep cap %lld reached", (long long)o->max_sweeps);
+        // a pass that reached its sweep cap is restarted from the FP64
+        // residual like one that stopped pushing (a refinement pass); an FP32
+        // pass stopped by its own length that at least halved the certified
+        // relative residual does not count against max_refine
+        const bool progress = done == 2 && pass_cap < o->max_sweeps && last_rel < 0.5 * prev_rel;
+        // over-relaxation that made the certified residual grow from one pass
+        // to the next is divergence (before the residual overflows)
+        if (o->omega > 1.0 && done == 2 && last_rel > 2.0 * prev_rel) {
+            result = FJ_ERR_DIVERGED;
+            set_error("residual grew from pass to pass (omega %.3f)", o->omega);
             break;
         }
-        if (refine >= o->max_refine) {
-            result = FJ_ERR_NOT_CONVERGED;
-            set_error("refinement cap %d reached with %.0f nodes above threshold", o->max_refine, viol);
-            break;
+        prev_rel = last_rel;
+        if (!progress) {
+            if (strikes >= o->max_refine) {
+                result = FJ_ERR_NOT_CONVERGED;
+                set_error("refinement cap %d reached with %.0f nodes above threshold", o->max_refine, viol);
+                break;
+            }
+            ++strikes;
         }
         ++refine;
     }
@@ -2967,11 +2987,14 @@ static fj_status solve_batch_t(fj_graph *g, const double *S, const double *Z0, i
     }
     int64_t sweep = 0;
     const int check = o->check_every > 0 ? o->check_every : 8;
+    const int64_t pass_cap = sizeof(T) == 4 ? std::min<int64_t>(o->max_sweeps, kFp32PassSweeps) : o->max_sweeps;
+    double prev_rel = INFINITY, last_rel = INFINITY;
+    int strikes = 0;
     int refine = 0, cleanups = 0;
     int64_t f_rounds = 0, f_pushes = 0;
     fj_status result = FJ_OK;
     for (;;) {
-        k_pass_reset<<<1, 1, 0, st>>>(ws.ctr, o->max_sweeps);
+        k_pass_reset<<<1, 1, 0, st>>>(ws.ctr, pass_cap);
         for (;;) {
             for (int jj = 0; jj < check; ++jj) {
                 ++sweep;
@@ -3042,7 +3065,11 @@ static fj_status solve_batch_t(fj_graph *g, const double *S, const double *Z0, i
             FJ_CUDA(cudaStreamSynchronize(st));
             FJ_CHECK(check_index_record());
             viol = 0.0;
-            for (int j = 0; j < k; ++j) viol += b.gstat_host[j * kGs + 5];
+            last_rel = 0.0;
+            for (int j = 0; j < k; ++j) {
+                viol += b.gstat_host[j * kGs + 5];
+                last_rel = std::max(last_rel, b.gstat_host[j * kGs + 3]);
+            }
             return FJ_OK;
         };
         double viol = 0.0;
@@ -3056,10 +3083,22 @@ static fj_status solve_batch_t(fj_graph *g, const double *S, const double *Z0, i
             if (!cleared) break;
         }
         if (viol == 0.0) break;
-        if (done == 2 || refine >= o->max_refine) {
-            result = FJ_ERR_NOT_CONVERGED;
-            set_error("batch did not certify (%.0f entries above threshold)", viol);
+        // as fj_solve: FP32 passes of kFp32PassSweeps, free restarts while the
+        // certified relative residual (largest over the vectors) halves
+        const bool progress = done == 2 && pass_cap < o->max_sweeps && last_rel < 0.5 * prev_rel;
+        if (o->omega > 1.0 && done == 2 && last_rel > 2.0 * prev_rel) {
+            result = FJ_ERR_DIVERGED;
+            set_error("residual grew from pass to pass (omega %.3f)", o->omega);
             break;
+        }
+        prev_rel = last_rel;
+        if (!progress) {
+            if (strikes >= o->max_refine) {
+                result = FJ_ERR_NOT_CONVERGED;
+                set_error("batch did not certify (%.0f entries above threshold)", viol);
+                break;
+            }
+            ++strikes;
         }
         ++refine;
         sweep = 0;
