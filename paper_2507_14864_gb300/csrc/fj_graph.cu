@@ -69,6 +69,7 @@ fj_status ws_status(Workspace &ws, int64_t tiles)
     if (tiles <= ws.cap_status && ws.status) return FJ_OK;
     dev_free(ws.status);
     ws.status = nullptr;
+    ws.cap_status = 0;
     int64_t cap = std::max<int64_t>(tiles, 1024);
     FJ_CUDA(dalloc(&ws.status, cap));
     ws.cap_status = cap;
@@ -716,7 +717,7 @@ void fj_graph_destroy(fj_graph *g)
     chunk_plan_free(g->cplan_pcsr);
     Workspace &ws = g->ws;
     dev_free(ws.r); dev_free(ws.h); dev_free(ws.da); dev_free(ws.db); dev_free(ws.om); dev_free(ws.judge);
-    dev_free(ws.rsum); dev_free(ws.carry);
+    dev_free(ws.rsum); dev_free(ws.carry); dev_free(ws.fdz);
     dev_free(ws.zhat); dev_free(ws.sp); dev_free(ws.sin); dev_free(ws.zout); dev_free(ws.r64); dev_free(ws.zs);
     dev_free(ws.gstat); dev_free(ws.ctr); dev_free(ws.status); dev_free(ws.tile_ctr); dev_free(ws.zmax);
     dev_free(ws.list); dev_free(ws.count); dev_free(ws.partial);

@@ -33,6 +33,7 @@ struct DevCSR {
     int64_t *row_ptr = nullptr;
     int32_t *col = nullptr;
     float *w = nullptr;        // nullptr = unit weights
+    mutable int wexp = INT32_MIN;  // max|w| < 2^wexp, set by the first certificate (weights are fixed)
     double *deg64 = nullptr;   // weighted out-degree d_u (FP64)
     float *inv32 = nullptr;    // float(1 / (1 + d_u))
     double *inv64 = nullptr;   // 1 / (1 + d_u)
@@ -131,6 +132,8 @@ struct Workspace {
     void *rsum = nullptr;   // single-vector sweep: row sums of the gathered increments, by row rank
     void *carry = nullptr;  // single-vector sweep: partial sum of the row that crosses each chunk's end
     int64_t cap_carry = 0;
+    char *fdz = nullptr;     // frontier push: count, entries and steps set aside for the long scatter
+    int64_t cap_fdz = 0;
     double *judge = nullptr;  // per-block residual and opinion sums of the warm-start judge
     int64_t cap_judge = 0;
     double *zhat = nullptr; // estimate of z' (FP64)

@@ -870,6 +870,7 @@ fj_status grow(T **p, int64_t count)
 fj_status ensure_fwd(fj_mpnn *m, int64_t n)
 {
     if (n <= m->cap) return FJ_OK;
+    m->cap = 0;  // stays 0 if an allocation fails, so the next call grows again
     FJ_CHECK(grow(&m->x, 4 * n));
     FJ_CHECK(grow(&m->g0, 4 * n));
     for (auto &p : m->h) FJ_CHECK(grow(&p, kHid * n));
@@ -884,6 +885,7 @@ fj_status ensure_fwd(fj_mpnn *m, int64_t n)
 fj_status ensure_bwd(fj_mpnn *m, int64_t n)
 {
     if (n <= m->cap_bwd) return FJ_OK;
+    m->cap_bwd = 0;
     FJ_CHECK(grow(&m->dh, kHid * n));
     FJ_CHECK(grow(&m->dg, kHid * n));
     m->cap_bwd = n;
@@ -898,6 +900,7 @@ fj_status stage(fj_mpnn *m, int64_t n, const double *src, double **dst_slot, con
         return FJ_OK;
     }
     if (n > m->cap_stage) {
+        m->cap_stage = 0;
         FJ_CHECK(grow(&m->sin, n));
         FJ_CHECK(grow(&m->zin, n));
         FJ_CHECK(grow(&m->zout, n));
@@ -917,6 +920,7 @@ fj_status forward(fj_mpnn *m, fj_graph *g, const double *sd, cudaStream_t st)
     const ItemPlan *ip = nullptr;
     FJ_CHECK(plain_items(g, st, &ip));
     if (ip->nparts * 64 > m->cap_part) {
+        m->cap_part = 0;
         FJ_CHECK(grow(&m->part, ip->nparts * 64));
         m->cap_part = ip->nparts * 64;
     }
@@ -1049,6 +1053,7 @@ fj_status fj_mpnn_predict(fj_mpnn *m, fj_graph *g, const double *s, double *z0, 
     double *dst = mem == FJ_MEM_DEVICE ? z0 : nullptr;
     if (!dst) {
         if (n > m->cap_stage) {
+            m->cap_stage = 0;
             FJ_CHECK(grow(&m->sin, n));
             FJ_CHECK(grow(&m->zin, n));
             FJ_CHECK(grow(&m->zout, n));

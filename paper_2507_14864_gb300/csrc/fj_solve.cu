@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -689,6 +690,77 @@ __global__ void k_split_absmax(int64_t n, const double *__restrict__ z, float2 *
     if ((threadIdx.x & 31) == 0) atomic_max_nonneg(reinterpret_cast<double *>(out), m);
 }
 
+// Fixed-point sums of the long-row certificate.  With |a zhat| < 2^E for
+// every product a zhat of the graph, a finite value t is taken as the integer
+// trunc(t 2^(94-E)) (below 2^94 in magnitude; the dropped part is under one
+// unit 2^(E-94)), and a row's integers are added exactly in 128 bits, within a
+// chunk and across its chunks (a row of up to 2^32 terms stays below 2^126).
+// The off-diagonal sum thus errs by under one unit per term, taken into the
+// decision as a bound, and no nonzero costs an FP64 operation beyond the
+// product of a weighted graph.  (GB300's FP64 rate is a small fraction of its
+// integer rate.)
+typedef unsigned __int128 u128;
+constexpr int kFixBits = 94;
+
+__device__ __forceinline__ void fix_add(u128 &acc, double t, int E, bool &bad)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(t);
+    const int e = (int)((b >> 52) & 0x7ffu);
+    const unsigned long long m = (b & 0xfffffffffffffull) | (e ? (1ull << 52) : 0ull);
+    const int sh = (e ? e : 1) - (1075 - kFixBits) - E;  // at most kFixBits - 53 when |t| < 2^E
+    bad |= (e == 0x7ff) | (sh > kFixBits - 52);
+    u128 q;
+    if (sh >= 0)
+        q = (u128)m << min(sh, kFixBits - 52);
+    else
+        q = sh > -64 ? (u128)(m >> -sh) : (u128)0;
+    acc = (long long)b < 0 ? acc - q : acc + q;
+}
+
+__device__ __forceinline__ u128 warp_u128_sum(u128 v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long lo = __shfl_xor_sync(0xffffffffu, (unsigned long long)v, o);
+        const unsigned long long hi = __shfl_xor_sync(0xffffffffu, (unsigned long long)(v >> 64), o);
+        v += ((u128)hi << 64) | (u128)lo;
+    }
+    return v;
+}
+
+// The exponent E of the fixed-point scale: max|zhat| < 2^Ez, max|a| < 2^Ew,
+// one bit more for the product's rounding; kept where the unit 2^(E-94) is a
+// normal double and a sum (below 2^(E+32)) is finite.  Out of range (a
+// non-finite or huge max): *bad.
+__device__ __forceinline__ int fix_exponent(double zmax, int ew, bool &bad)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(zmax);
+    const int e = (int)((b >> 52) & 0x7ffu);
+    int E = (e ? e : 1) - 1022 + ew + 1;
+    bad |= e == 0x7ff;
+    E = max(E, -900);
+    if (E > 950) {  // sums up to 2^(E+32) stay finite
+        bad = true;
+        E = 950;
+    }
+    return E;
+}
+
+// The signed 128-bit sum v (units 2^(E-94)) as a double-double: four 32-bit
+// limbs, each exact in FP64, joined largest first.
+__device__ __forceinline__ DD fix_value(u128 v, int E)
+{
+    const bool neg = (long long)(unsigned long long)(v >> 64) < 0;
+    const u128 a = neg ? (u128)0 - v : v;
+    const double unit = __longlong_as_double((long long)(E - kFixBits + 1023) << 52);
+    DD acc{(double)(unsigned)(a >> 96) * 0x1p96, 0.0};
+    dd_add(acc, (double)(unsigned)(a >> 64) * 0x1p64);
+    dd_add(acc, (double)(unsigned)(a >> 32) * 0x1p32);
+    dd_add(acc, (double)(unsigned)a);
+    const double sg = neg ? -unit : unit;
+    return DD{acc.hi * sg, acc.lo * sg};
+}
+
 template <typename T, bool W>
 __global__ void __launch_bounds__(256)
 k_certify(const Item *__restrict__ items, int64_t nitems, const int64_t *__restrict__ rp,
@@ -697,10 +769,13 @@ k_certify(const Item *__restrict__ items, int64_t nitems, const int64_t *__restr
           const int32_t *__restrict__ graph_of, double epsp, T *__restrict__ r, T *__restrict__ da,
           T *__restrict__ db, unsigned long long *gs, const int32_t *__restrict__ slot_first,
           const int32_t *__restrict__ slot_nchunk, double *part, int32_t *cnt, double *__restrict__ r64,
-          const unsigned long long *__restrict__ zmaxp, int64_t n_rows)
+          const unsigned long long *__restrict__ zmaxp, int wexp, int64_t n_rows)
 {
     constexpr unsigned FULL = 0xffffffffu;
-    const float zmaxf = (float)__longlong_as_double((long long)*zmaxp);
+    const double zmaxd = __longlong_as_double((long long)*zmaxp);
+    const float zmaxf = (float)zmaxd;
+    bool fix_bad = false;
+    const int fixE = fix_exponent(zmaxd, W ? wexp : 0, fix_bad);
     const float epsf = (float)epsp;
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -752,6 +827,21 @@ k_certify(const Item *__restrict__ items, int64_t nitems, const int64_t *__restr
         const float gap = arf - thrf;
         dec = gap > slack ? 1 : (-gap > slack ? 0 : -1);  // NaN or inf: undecided
         return rx;
+    };
+    auto fix_terms = [&](int64_t a, int64_t e, int64_t step, u128 &acc, bool &bad) {
+        for (int64_t k = a; k < e; k += step) {
+            const int32_t cj = __ldg(col + k);
+            if (!FJ_IDX_OK(4, cj, n_rows)) continue;
+            const double z = zhat[cj];
+            if (W) {
+                const double av = (double)__ldg(w + k);
+                const double pr = __dmul_rn(av, z);
+                fix_add(acc, pr, fixE, bad);
+                fix_add(acc, fma(av, z, -pr), fixE, bad);  // the product's rounding error, exactly
+            } else {
+                fix_add(acc, z, fixE, bad);
+            }
+        }
     };
     auto exact_residual = [&](int64_t x, DD acc, int &dec) -> double {
         dd_add(acc, sp[x]);
@@ -864,28 +954,47 @@ k_certify(const Item *__restrict__ items, int64_t nitems, const int64_t *__restr
             // FP32 decision would leave it open near convergence, and one warp
             // re-summing a hub row of 10^5-10^6 nonzeros would serialise the
             // certificate; the chunks share that work instead.)
-            DD acc{0.0, 0.0};
-            exact_terms(it.k0 + lane, it.k1, 32, acc);
-            acc = warp_dd_sum(acc);
+            u128 acc = 0;
+            bool bad = fix_bad;
+            fix_terms(it.k0 + lane, it.k1, 32, acc, bad);
+            acc = warp_u128_sum(acc);
+            bad = __any_sync(FULL, bad);
             const int slot = it.slot;
             const int first = slot_first[slot], nch = slot_nchunk[slot];
             const int ci = (int)((it.k0 - rp[r0]) / kWarpChunk);
+            unsigned long long *pw = reinterpret_cast<unsigned long long *>(part);
             int last = 0;
             if (lane == 0) {
-                part[2 * (first + ci)] = acc.hi;
-                part[2 * (first + ci) + 1] = acc.lo;
+                // a chunk's sum is below 2^104, so a top word of INT64_MIN marks a bad chunk
+                pw[2 * (first + ci)] = bad ? 0ull : (unsigned long long)acc;
+                pw[2 * (first + ci) + 1] = bad ? 0x8000000000000000ull : (unsigned long long)(acc >> 64);
                 __threadfence();
                 last = atomicAdd(&cnt[slot], 1) == nch - 1;
             }
             last = __shfl_sync(FULL, last, 0);
             if (last) {
                 __threadfence();
-                DD d{0.0, 0.0};
-                for (int c = lane; c < nch; c += 32)
-                    d = dd_merge(d, DD{__ldcg(part + 2 * (first + c)), __ldcg(part + 2 * (first + c) + 1)});
-                d = warp_dd_sum(d);
+                u128 d = 0;
+                bool dbad = false;
+                for (int c = lane; c < nch; c += 32) {
+                    const unsigned long long lo = __ldcg(pw + 2 * (first + c)), hi = __ldcg(pw + 2 * (first + c) + 1);
+                    dbad |= hi == 0x8000000000000000ull;
+                    d += ((u128)hi << 64) | (u128)lo;
+                }
+                d = warp_u128_sum(d);
+                dbad = __any_sync(FULL, dbad);
+                const int64_t len = rp[r0 + 1] - rp[r0];
+                const DD off = fix_value(d, fixE);
                 int dec;
-                const double rx = exact_residual(r0, d, dec);
+                double rx = exact_residual(r0, off, dec);
+                // under one unit per term (two for a weighted product), and
+                // the double-double steps' rounding, on the safe side
+                const double unit = __longlong_as_double((long long)(fixE - kFixBits + 1023) << 52);
+                const double slack = (double)((W ? 2 : 1) * len + 4) * unit +
+                                     0x1p-100 * (fabs(off.hi) + (1.0 + deg[r0]) * fabs(zhat[r0]) + fabs(sp[r0]));
+                if (dbad) rx = __longlong_as_double(0x7ff8000000000000ll);  // non-finite input: NaN
+                else if (!dec && fabs(rx) + slack > fmax(epsp * sp[r0], resid_floor(deg[r0], zhat[r0])))
+                    dec = 1;
                 if (lane == 0) {
                     cnt[slot] = 0;
                     finish(r0, rx, dec);
@@ -926,12 +1035,18 @@ struct CleanPred {
 // Pushes of one round run concurrently, so every residual update is an
 // atomic addition; an entry's own residual is read once and what was read is
 // what is moved (asynchronous relaxation of the diagonally dominant I + L).
+// An entry whose in-neighbour list is longer than long_min leaves its
+// scatter to k_frontier_push_long (a block per such entry), so a hub does not
+// serialise a round on one warp: the entry and its step are appended to
+// (lng_e, lng_dz), counted by *lng_n, which is zero when the kernel starts.
+
 template <bool W>
 __global__ void __launch_bounds__(256)
 k_frontier_push(const int32_t *__restrict__ list, const long long *__restrict__ count, int k,
                 const int64_t *__restrict__ tp, const int32_t *__restrict__ tc, const float *__restrict__ tw,
                 const double *__restrict__ deg, double *r64, double *__restrict__ zhat, Counters *ctr,
-                int64_t n_rows)
+                int64_t n_rows, int64_t long_min, unsigned long long *lng_n, int64_t *__restrict__ lng_e,
+                double *__restrict__ lng_dz)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -956,6 +1071,14 @@ k_frontier_push(const int32_t *__restrict__ list, const long long *__restrict__ 
         }
         dz = __shfl_sync(0xffffffffu, dz, 0);
         const int64_t a0 = tp[v], a1 = tp[v + 1];
+        if (a1 - a0 > long_min) {
+            if (lane == 0) {
+                const unsigned long long slot = atomicAdd(lng_n, 1ull);
+                lng_e[slot] = e;  // slot < cnt: one slot per list entry at most
+                lng_dz[slot] = dz;
+            }
+            continue;
+        }
         for (int64_t kk = a0 + lane; kk < a1; kk += 32) {
             const int32_t u = tc[kk];
             if (!FJ_IDX_OK(21, u, n_rows)) continue;
@@ -966,6 +1089,39 @@ k_frontier_push(const int32_t *__restrict__ list, const long long *__restrict__ 
     }
     my_edges = warp_sum(my_edges);
     if (lane == 0 && my_edges) atomicAdd(&ctr->fedges, my_edges);
+}
+
+// The scatter of the long entries of a frontier round: persistent blocks take
+// the entries k_frontier_push set aside in turn and a block spreads an entry's
+// in-neighbours over its threads (the step dz was computed and applied to the
+// entry itself by k_frontier_push).
+template <bool W>
+__global__ void __launch_bounds__(1024)
+k_frontier_push_long(const unsigned long long *__restrict__ lng_n, const int64_t *__restrict__ lng_e,
+                     const double *__restrict__ lng_dz, const long long *__restrict__ count, int k,
+                     const int64_t *__restrict__ tp, const int32_t *__restrict__ tc, const float *__restrict__ tw,
+                     double *r64, Counters *ctr, int64_t n_rows)
+{
+    const long long nl = (long long)*lng_n;
+    const long long cnt = *count;
+    const int64_t n_ent = n_rows * k;
+    unsigned long long my_edges = 0;
+    for (int64_t i = blockIdx.x; i < nl && i < cnt; i += gridDim.x) {
+        const int64_t e = lng_e[i];
+        if (!FJ_IDX_OK(22, e, n_ent)) continue;
+        const int64_t v = e / k;
+        const int j = (int)(e - v * k);
+        const int64_t a0 = tp[v], a1 = tp[v + 1];
+        const double dz = lng_dz[i];
+        for (int64_t kk = a0 + threadIdx.x; kk < a1; kk += blockDim.x) {
+            const int32_t u = tc[kk];
+            if (!FJ_IDX_OK(23, u, n_rows)) continue;
+            const double a = W ? (double)tw[kk] : 1.0;
+            atomicAdd(r64 + (int64_t)u * k + j, __dmul_rn(a, dz));
+        }
+        if (threadIdx.x == 0) my_edges += (unsigned long long)(a1 - a0);
+    }
+    if (threadIdx.x == 0 && my_edges) atomicAdd(&ctr->fedges, my_edges);
 }
 
 // ============================================================== frontier
@@ -1062,6 +1218,7 @@ static fj_status warm_judge(fj_graph *g, int64_t n, int k, const double *r64, co
     if (need + 64 > ws.cap_judge) {  // the sums, then room for 64 restart flags
         dev_free(ws.judge);
         ws.judge = nullptr;
+        ws.cap_judge = 0;  // stays 0 if the allocation fails
         FJ_CUDA(dev_malloc(&ws.judge, sizeof(double) * (size_t)(need + 64)));
         ws.cap_judge = need + 64;
     }
@@ -1089,6 +1246,7 @@ static fj_status ws_grow(fj_graph *g, int64_t entries, int ngraphs)
 {
     Workspace &ws = g->ws;
     if (entries > ws.cap_n) {
+        ws.cap_n = 0;  // stays 0 if an allocation fails, so the next call grows again
         void **bufs[] = {&ws.r, &ws.h, &ws.da, &ws.db, &ws.om, &ws.rsum};
         for (void **p : bufs) {
             dev_free(*p);
@@ -1111,6 +1269,7 @@ static fj_status ws_grow(fj_graph *g, int64_t entries, int ngraphs)
         ws.gen++;
     }
     if (ngraphs > ws.cap_graphs) {
+        ws.cap_graphs = 0;
         dev_free(ws.gstat);
         ws.gstat = nullptr;
         if (ws.gstat_host) cudaFreeHost(ws.gstat_host);
@@ -1574,6 +1733,38 @@ static fj_status sweep_graph(fj_graph *g, const Plan &p, int nsweeps, cudaGraphE
     return FJ_OK;
 }
 
+// max |w| over the nonzeros into *out (ordered bits of a non-negative double).
+__global__ void k_absmax_w(int64_t nnz, const float *__restrict__ w, unsigned long long *out)
+{
+    double m = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += (int64_t)gridDim.x * blockDim.x)
+        m = fmax(m, (double)fabsf(w[i]));
+    m = warp_max(m);
+    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(reinterpret_cast<double *>(out), m);
+}
+
+// Ew with max|w| < 2^Ew for the certificate's fixed-point scale; computed on
+// the first certificate of a weighted CSR and kept (the weights are fixed).
+static fj_status weight_exponent(const DevCSR &c, Workspace &ws, cudaStream_t st, int *ew)
+{
+    if (c.wexp == INT32_MIN) {
+        FJ_CUDA(cudaMemsetAsync(ws.zmax, 0, sizeof(unsigned long long), st));
+        k_absmax_w<<<grid_for(c.nnz, 256, 152 * 8), 256, 0, st>>>(c.nnz, c.w, ws.zmax);
+        FJ_CUDA(cudaGetLastError());
+        unsigned long long bits = 0;
+        FJ_CUDA(cudaMemcpyAsync(&bits, ws.zmax, sizeof(bits), cudaMemcpyDeviceToHost, st));
+        FJ_CUDA(cudaStreamSynchronize(st));
+        double wm = 0.0;
+        std::memcpy(&wm, &bits, sizeof(wm));
+        if (!std::isfinite(wm)) return FJ_ERR_INVALID_ARG;
+        int e = 0;
+        std::frexp(wm, &e);  // wm < 2^e
+        c.wexp = wm > 0.0 ? e : -126;
+    }
+    *ew = c.wexp;
+    return FJ_OK;
+}
+
 template <typename T>
 static fj_status launch_certify(fj_graph *g, const Plan &p, double epsp, cudaStream_t st, Run &run)
 {
@@ -1585,17 +1776,19 @@ static fj_status launch_certify(fj_graph *g, const Plan &p, double epsp, cudaStr
     T *r = reinterpret_cast<T *>(ws.r), *da = reinterpret_cast<T *>(ws.da), *db = reinterpret_cast<T *>(ws.db);
     unsigned long long *gs = reinterpret_cast<unsigned long long *>(ws.gstat);
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ip.nitems, 8), 152 * 8));
+    int wexp = 0;
+    if (c.w) FJ_CHECK(weight_exponent(c, ws, st, &wexp));
     FJ_CUDA(cudaMemsetAsync(ws.zmax, 0, sizeof(unsigned long long), st));
     k_split_absmax<<<grid_for(c.n, 256, 152 * 8), 256, 0, st>>>(c.n, ws.zhat, ws.zs, ws.zmax);
     run.launches += 1;
     if (c.w)
         k_certify<T, true><<<grid, 256, 0, st>>>(ip.items, ip.nitems, c.row_ptr, c.col, c.w, ws.zhat, ws.zs, ws.sp,
                                                  c.deg64, c.graph_of, epsp, r, da, db, gs, ip.slot_first,
-                                                 ip.slot_nchunk, ip.part, ip.cnt, ws.r64, ws.zmax, c.n);
+                                                 ip.slot_nchunk, ip.part, ip.cnt, ws.r64, ws.zmax, wexp, c.n);
     else
         k_certify<T, false><<<grid, 256, 0, st>>>(ip.items, ip.nitems, c.row_ptr, c.col, c.w, ws.zhat, ws.zs, ws.sp,
                                                   c.deg64, c.graph_of, epsp, r, da, db, gs, ip.slot_first,
-                                                  ip.slot_nchunk, ip.part, ip.cnt, ws.r64, ws.zmax, c.n);
+                                                  ip.slot_nchunk, ip.part, ip.cnt, ws.r64, ws.zmax, 0, c.n);
     FJ_CUDA(cudaGetLastError());
     return FJ_OK;
 }
@@ -1639,6 +1832,19 @@ static fj_status in_lists(fj_graph *g, const Plan &p, cudaStream_t st, InLists &
     return FJ_OK;
 }
 
+// In-neighbour lists longer than this are scattered by a block each
+// (k_frontier_push_long); FJ_FRONTIER_LONG overrides it (0: every entry).
+static int64_t frontier_long_min()
+{
+    const char *e = std::getenv("FJ_FRONTIER_LONG");
+    if (e && *e) {
+        char *end = nullptr;
+        const long long v = std::strtoll(e, &end, 10);
+        if (end && *end == 0 && v >= 0) return (int64_t)v;
+    }
+    return 4096;
+}
+
 // Largest frontier the FP64 push takes on (entries); beyond it another pass
 // of sweeps is cheaper.
 static int64_t frontier_limit(int64_t entries) { return std::max<int64_t>(1024, entries / 64); }
@@ -1658,6 +1864,17 @@ static fj_status frontier_cleanup(fj_graph *g, const Plan &p, int k, double *r64
     InLists L;
     FJ_CHECK(in_lists(g, p, st, L));
     FJ_CHECK(ws_status(ws, scan_tiles(ne, 256 * 8)));
+    if (limit > ws.cap_fdz) {  // [count, pad][entries: limit x int64][steps: limit x double]
+        dev_free(ws.fdz);
+        ws.fdz = nullptr;
+        ws.cap_fdz = 0;
+        FJ_CUDA(dev_malloc(&ws.fdz, 16 + 16 * (size_t)limit));
+        ws.cap_fdz = limit;
+    }
+    unsigned long long *lng_n = reinterpret_cast<unsigned long long *>(ws.fdz);
+    int64_t *lng_e = reinterpret_cast<int64_t *>(ws.fdz + 16);
+    double *lng_dz = reinterpret_cast<double *>(ws.fdz + 16 + 8 * (size_t)limit);
+    const int64_t long_min = frontier_long_min();
     *cleared = false;
     for (int it = 0; it < max_rounds; ++it) {
         FJ_CUDA(compact<256, 8>(ne, CleanPred{r64, sp, zhat, c.deg64, epsp, k}, list, ws.count, ws.status,
@@ -1672,14 +1889,21 @@ static fj_status frontier_cleanup(fj_graph *g, const Plan &p, int k, double *r64
         }
         if (cnt > limit) break;
         const unsigned grid = grid_for(cnt * 32, 256, 152 * 16);
-        if (L.tw)
+        const unsigned lgrid = (unsigned)std::max<long long>(1, std::min<long long>(cnt, 152 * 2));
+        FJ_CUDA(cudaMemsetAsync(lng_n, 0, sizeof(unsigned long long), st));
+        if (L.tw) {
             k_frontier_push<true><<<grid, 256, 0, st>>>(list, ws.count, k, L.tp, L.tc, L.tw, c.deg64, r64, zhat,
-                                                        ws.ctr, c.n);
-        else
+                                                        ws.ctr, c.n, long_min, lng_n, lng_e, lng_dz);
+            k_frontier_push_long<true><<<lgrid, 1024, 0, st>>>(lng_n, lng_e, lng_dz, ws.count, k, L.tp, L.tc, L.tw,
+                                                               r64, ws.ctr, c.n);
+        } else {
             k_frontier_push<false><<<grid, 256, 0, st>>>(list, ws.count, k, L.tp, L.tc, L.tw, c.deg64, r64, zhat,
-                                                         ws.ctr, c.n);
+                                                         ws.ctr, c.n, long_min, lng_n, lng_e, lng_dz);
+            k_frontier_push_long<false><<<lgrid, 1024, 0, st>>>(lng_n, lng_e, lng_dz, ws.count, k, L.tp, L.tc,
+                                                                L.tw, r64, ws.ctr, c.n);
+        }
         FJ_CUDA(cudaGetLastError());
-        ++run.launches;
+        run.launches += 2;
         ++*rounds;
         *pushes += cnt;
     }
@@ -1741,6 +1965,7 @@ static fj_status solve_t(fj_graph *g, const double *s, const double *z0, const f
         if (cpl.nch > ws.cap_carry) {
             dev_free(ws.carry);
             ws.carry = nullptr;
+            ws.cap_carry = 0;
             FJ_CUDA(dev_malloc(&ws.carry, sizeof(double) * (size_t)cpl.nch));
             ws.cap_carry = cpl.nch;
             ws.gen++;
@@ -2414,11 +2639,16 @@ k_sweep_batch(const Item *__restrict__ items, int64_t item0, int64_t nitems, con
 // FP64 certificate of every (node, right-hand side), as k_certify: a plain
 // FP64 sum per (row, vector) with an FP32 magnitude sum beside it, and the
 // compensated (Dot2) re-evaluation of the few entries whose residual lies
-// within the plain sum's error bound of the threshold.  Per-vector statistics
+// within the plain sum's error bound of the threshold; long rows' chunks sum
+// in 128-bit fixed point (fix_add) from the start.  Per-vector statistics
 // are reduced per block in shared memory (maxima of non-negative doubles
 // compare as integers) and added with one atomic per vector and field.
 struct PlainAcc {
     double s;
+};
+struct FixAcc {
+    u128 v;
+    bool bad;
 };
 
 template <typename T, bool W>
@@ -2428,10 +2658,12 @@ k_certify_batch(const Item *__restrict__ items, int64_t nitems, const int64_t *_
                 const double *__restrict__ sp, const double *__restrict__ deg, double epsp, T *__restrict__ r,
                 T *__restrict__ da, T *__restrict__ db, unsigned long long *gs, const int32_t *__restrict__ slot_first,
                 const int32_t *__restrict__ slot_nchunk, double *partk, int32_t *cnt, double *__restrict__ r64,
-                const unsigned long long *__restrict__ zmaxp, int64_t n_rows)
+                const unsigned long long *__restrict__ zmaxp, int wexp, int64_t n_rows)
 {
     __shared__ unsigned long long sred[4][64];
     const double zmax = __longlong_as_double((long long)*zmaxp);
+    bool fix_bad = false;
+    const int fixE = fix_exponent(zmax, W ? wexp : 0, fix_bad);
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < 4 * 64; i += 256) (&sred[0][0])[i] = 0ULL;
     __syncthreads();
@@ -2469,21 +2701,29 @@ k_certify_batch(const Item *__restrict__ items, int64_t nitems, const int64_t *_
         da[q] = T(0);
         db[q] = T(0);
     };
-    // row x, vector lane + 32 hh, from the compensated sum of a_xc zhat_c
-    auto finish_exact = [&](int64_t x, int hh, DD acc) {
+    // row x, vector lane + 32 hh, from the fixed-point sum of a_xc zhat_c
+    // over the row's len nonzeros; the sum's error bound counts against the
+    // row (a row within it of the threshold is not certified)
+    auto finish_fix = [&](int64_t x, int hh, u128 sum, bool bad, int64_t len) {
         const int j = lane + 32 * hh;
         const int64_t q = x * k + j;
-        const double zx = zhat[q], spx = sp[q];
+        const double zx = zhat[q], spx = sp[q], dpl = 1.0 + deg[x];
+        const DD off = fix_value(sum, fixE);
+        DD acc = off;
         dd_add(acc, spx);
-        dd_fma(acc, -(1.0 + deg[x]), zx);
-        const double rx = dd_value(acc);
+        dd_fma(acc, -dpl, zx);
+        double rx = dd_value(acc);
+        if (bad) rx = __longlong_as_double(0x7ff8000000000000ll);  // non-finite input: NaN
+        const double unit = __longlong_as_double((long long)(fixE - kFixBits + 1023) << 52);
+        const double slack =
+            (double)((W ? 2 : 1) * len + 4) * unit + 0x1p-100 * (fabs(off.hi) + dpl * fabs(zx) + fabs(spx));
         const double thr = fmax(epsp * spx, resid_floor(deg[x], zx));
         const double ce = gsd[(int64_t)j * kGs + 1];
         const double ax = fabs(rx) <= 1e300 ? fabs(rx) : INFINITY;
         m_abs[hh] = fmax(m_abs[hh], ax);
         m_rel[hh] = fmax(m_rel[hh], ax / spx);
         m_z[hh] = fmax(m_z[hh], fabs(zx - ce));
-        if (ax > thr) viol[hh] += 1.0;
+        if (ax + slack > thr) viol[hh] += 1.0;
         r[q] = resid_store<T>(rx);
         r64[q] = rx;
         da[q] = T(0);
@@ -2507,25 +2747,34 @@ k_certify_batch(const Item *__restrict__ items, int64_t nitems, const int64_t *_
             warp_tile_k<PlainAcc, double, W, 8>(r0, r1, it.k0, it.k1, false, rp, col, w, no_begin, src, add,
                                                 short_row, lane, has1, has2, n_rows);
         } else {
-            // chunks of long rows: compensated sums from the start (a hub's
-            // plain-sum bound always straddles its threshold)
+            // chunks of long rows: fixed-point sums from the start (a hub's
+            // plain-sum bound always straddles its threshold); a chunk's sum
+            // is below 2^104, so a top word of INT64_MIN marks a bad chunk
             const int slot = it.slot;
             const int first = slot_first[slot], nch = slot_nchunk[slot];
             const int ci = (int)((it.k0 - rp[r0]) / kWarpChunk);
-            double *pc = partk + 2 * ((int64_t)(first + ci) * k + lane);
-            auto add_dd = [](DD &acc, float a, double v) { dd_fma(acc, (double)a, v); };
-            auto store_part = [&](int64_t, DD s1, DD s2) {
-                if (has1) {
-                    pc[0] = s1.hi;
-                    pc[1] = s1.lo;
-                }
-                if (has2) {
-                    pc[64] = s2.hi;
-                    pc[65] = s2.lo;
+            unsigned long long *pc =
+                reinterpret_cast<unsigned long long *>(partk) + 2 * ((int64_t)(first + ci) * k + lane);
+            auto add_fix = [&](FixAcc &acc, float a, double v) {
+                if (W) {
+                    const double av = (double)a, pr = __dmul_rn(av, v);
+                    fix_add(acc.v, pr, fixE, acc.bad);
+                    fix_add(acc.v, fma(av, v, -pr), fixE, acc.bad);  // the product's rounding error
+                } else {
+                    fix_add(acc.v, v, fixE, acc.bad);
                 }
             };
-            warp_tile_k<DD, double, W, 8>(r0, r1, it.k0, it.k1, true, rp, col, w, no_begin, src, add_dd,
-                                          store_part, lane, has1, has2, n_rows);
+            auto put = [&](unsigned long long *q, const FixAcc &a) {
+                const bool b = a.bad || fix_bad;
+                q[0] = b ? 0ull : (unsigned long long)a.v;
+                q[1] = b ? 0x8000000000000000ull : (unsigned long long)(a.v >> 64);
+            };
+            auto store_part = [&](int64_t, FixAcc s1, FixAcc s2) {
+                if (has1) put(pc, s1);
+                if (has2) put(pc + 64, s2);
+            };
+            warp_tile_k<FixAcc, double, W, 8>(r0, r1, it.k0, it.k1, true, rp, col, w, no_begin, src, add_fix,
+                                              store_part, lane, has1, has2, n_rows);
             __threadfence();
             __syncwarp();
             int last = 0;
@@ -2533,15 +2782,26 @@ k_certify_batch(const Item *__restrict__ items, int64_t nitems, const int64_t *_
             last = __shfl_sync(0xffffffffu, last, 0);
             if (last) {
                 __threadfence();
-                DD a1{0.0, 0.0}, a2{0.0, 0.0};
+                u128 a1 = 0, a2 = 0;
+                bool b1 = false, b2 = false;
+                const unsigned long long *pw = reinterpret_cast<const unsigned long long *>(partk);
                 for (int c = 0; c < nch; ++c) {
-                    const double *q = partk + 2 * ((int64_t)(first + c) * k + lane);
-                    if (has1) a1 = dd_merge(a1, DD{__ldcg(q), __ldcg(q + 1)});
-                    if (has2) a2 = dd_merge(a2, DD{__ldcg(q + 64), __ldcg(q + 65)});
+                    const unsigned long long *q = pw + 2 * ((int64_t)(first + c) * k + lane);
+                    if (has1) {
+                        const unsigned long long lo = __ldcg(q), hi = __ldcg(q + 1);
+                        b1 |= hi == 0x8000000000000000ull;
+                        a1 += ((u128)hi << 64) | (u128)lo;
+                    }
+                    if (has2) {
+                        const unsigned long long lo = __ldcg(q + 64), hi = __ldcg(q + 65);
+                        b2 |= hi == 0x8000000000000000ull;
+                        a2 += ((u128)hi << 64) | (u128)lo;
+                    }
                 }
                 if (lane == 0) cnt[slot] = 0;
-                if (has1) finish_exact(r0, 0, a1);
-                if (has2) finish_exact(r0, 1, a2);
+                const int64_t len = rp[r0 + 1] - rp[r0];
+                if (has1) finish_fix(r0, 0, a1, b1, len);
+                if (has2) finish_fix(r0, 1, a2, b2, len);
             }
         }
     }
@@ -2838,6 +3098,7 @@ static fj_status bws_grow(fj_graph *g, int k, int64_t nparts, int64_t nclasses)
 {
     BatchWorkspace &b = g->bws;
     if (nclasses > b.cap_tick) {
+        b.cap_tick = 0;  // stays 0 if an allocation fails, so the next call grows again
         dev_free(b.tick);
         b.tick = nullptr;
         FJ_CUDA(dev_malloc(&b.tick, sizeof(unsigned int) * 2 * (size_t)nclasses));
@@ -2846,6 +3107,7 @@ static fj_status bws_grow(fj_graph *g, int k, int64_t nparts, int64_t nclasses)
     }
     const int64_t need = g->csr.n * k;
     if (need > b.cap) {
+        b.cap = 0;
         void **vb[] = {&b.r, &b.h, &b.da, &b.db, &b.z32};
         for (void **p : vb) {
             dev_free(*p);
@@ -2865,15 +3127,20 @@ static fj_status bws_grow(fj_graph *g, int k, int64_t nparts, int64_t nclasses)
     }
     if (!b.om) FJ_CUDA(dev_malloc(&b.om, sizeof(double) * (size_t)g->csr.n));
     if (k > b.cap_k) {
+        b.cap_k = 0;
         dev_free(b.gstat);
+        b.gstat = nullptr;
         if (b.gstat_host) cudaFreeHost(b.gstat_host);
+        b.gstat_host = nullptr;
         FJ_CUDA(dev_malloc(&b.gstat, sizeof(double) * kGs * k));
         FJ_CUDA(cudaMallocHost(&b.gstat_host, sizeof(double) * kGs * k));
         b.cap_k = k;
     }
     const int64_t np = 2 * std::max<int64_t>(nparts, 1) * k;
     if (np > b.cap_partk) {
+        b.cap_partk = 0;
         dev_free(b.partk);
+        b.partk = nullptr;
         FJ_CUDA(dev_malloc(&b.partk, sizeof(double) * (size_t)np));
         b.cap_partk = np;
     }
@@ -2928,6 +3195,8 @@ static fj_status solve_batch_t(fj_graph *g, const double *S, const double *Z0, i
     if constexpr (sizeof(T) == 4) inv = reinterpret_cast<const T *>(c.inv32);
     else inv = reinterpret_cast<const T *>(c.inv64);
     const unsigned cgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(wp.nitems, 8), 152 * 8));
+    int wexp = 0;
+    if (c.w) FJ_CHECK(weight_exponent(c, ws, st, &wexp));
     auto certify = [&]() -> fj_status {
         k_cert_reset<<<1, 64, 0, st>>>(k, gs);
         if (sizeof(T) == 4)
@@ -2937,11 +3206,11 @@ static fj_status solve_batch_t(fj_graph *g, const double *S, const double *Z0, i
         if (c.w)
             k_certify_batch<T, true><<<cgrid, 256, 0, st>>>(wp.items, wp.nitems, c.row_ptr, c.col, c.w, k, b.zhat,
                                                             b.sp, c.deg64, epsp, r, da, db, gs, wp.slot_first,
-                                                            wp.slot_nchunk, b.partk, wp.cnt, b.r64, ws.zmax, c.n);
+                                                            wp.slot_nchunk, b.partk, wp.cnt, b.r64, ws.zmax, wexp, c.n);
         else
             k_certify_batch<T, false><<<cgrid, 256, 0, st>>>(wp.items, wp.nitems, c.row_ptr, c.col, c.w, k, b.zhat,
                                                              b.sp, c.deg64, epsp, r, da, db, gs, wp.slot_first,
-                                                             wp.slot_nchunk, b.partk, wp.cnt, b.r64, ws.zmax, c.n);
+                                                             wp.slot_nchunk, b.partk, wp.cnt, b.r64, ws.zmax, wexp, c.n);
         FJ_CUDA(cudaGetLastError());
         return FJ_OK;
     };

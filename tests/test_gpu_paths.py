@@ -7,7 +7,8 @@
   oracle's, evaluated with compensated sums on the estimate the solve held at
   that point (taken from a solve capped at the same sweep count).
 - The FP64 frontier cleanup (scatter-form push rounds on the few entries the
-  certificate leaves above threshold) runs and still certifies against truth.
+  certificate leaves above threshold) runs and still certifies against truth,
+  also when long in-neighbour lists are scattered by a block each.
 - Update counts of the GPU schedules against the FIFO push of Alg. 1-3 at
   the same omega (Fig. 2's axis): the same order of magnitude; the counts
   themselves are not pinned (the GPU order differs from the FIFO on purpose).
@@ -175,6 +176,57 @@ def test_frontier_cleanup_runs_and_certifies(capi):
                 assert i0["frontier_pushes"] > 0 and i0["frontier_edges"] > 0
                 ran += 1
     assert ran >= 1, "no solve reached the frontier cleanup"
+
+
+def _hub_graph(n, hubs, seed_off):
+    """BA(n, 4) plus `hubs` extra nodes joined to every BA node: each hub's
+    in-neighbour list (n entries) is longer than the block-scatter threshold."""
+    g = W.ba_graph(n, 4, seed_off=seed_off)
+    hs = np.repeat(np.arange(n, n + hubs, dtype=np.int32), n)
+    hd = np.tile(np.arange(n, dtype=np.int32), hubs)
+    src = np.concatenate([g["src"], hs])
+    dst = np.concatenate([g["dst"], hd])
+    a, b, c = W.symmetrize_arcs(src, dst, None)
+    nt = n + hubs
+    rp, col, w = oracle.csr_from_arcs(nt, a, b, c)
+    rng = np.random.default_rng(9000 + seed_off)
+    s = np.concatenate([g["S"][0], rng.uniform(0.0, 1.0, hubs)])
+    return nt, rp, col, w, s
+
+
+@pytest.mark.parametrize("long_min", ["0", None])
+def test_frontier_long_scatter(capi, monkeypatch, long_min):
+    """The frontier round's long in-neighbour lists go to one block each
+    (FJ_FRONTIER_LONG=0 sends every entry there, and these solves must reach
+    the cleanup; under the default the hubs of these graphs would go there if
+    a frontier holds them); results still certify and match truth."""
+    if long_min is None:
+        monkeypatch.delenv("FJ_FRONTIER_LONG", raising=False)
+    else:
+        monkeypatch.setenv("FJ_FRONTIER_LONG", long_min)
+    ran = 0
+    cases = [(85, 5000, 3), (86, 6000, 2)] if long_min is None else [(81, 1500, 0), (83, 5000, 0), (85, 5000, 3)]
+    for seed_off, n, hubs in cases:
+        if hubs:
+            nt, rp, col, w, s = _hub_graph(n, hubs, seed_off)
+        else:
+            g = W.ba_graph(n, 4, seed_off=seed_off)
+            rp, col, w = csr_of(g)
+            nt, s = n, g["S"][0]
+        z_star, _ = oracle.truth(nt, rp, col, w, s)
+        G = capi.Graph.from_csr(nt, *to_dev(rp, col, w), directed=False)
+        (s_d,) = to_dev(s)
+        for prec, tol in ((capi.FJ_PREC_FP32, FP32_TOL), (capi.FJ_PREC_FP64, FP64_TOL)):
+            for omega in (1.0, 1.5):
+                z, info, st = G.solve(s_d, eps=1e-6, omega=omega, precision=prec)
+                i0 = info[0]
+                assert st == capi.FJ_OK and i0["converged"] == 1
+                assert rel_inf(z.cpu().numpy(), z_star) <= tol
+                ok, _ = certificate_holds(nt, rp, col, w, s, z.cpu().numpy(), i0["c_eff"], i0["eps_prime"])
+                assert ok
+                ran += i0["frontier_rounds"] > 0
+    if long_min == "0":  # the hub graphs need not leave a frontier at all
+        assert ran >= 1, "no solve reached the frontier cleanup"
 
 
 # ------------------------------------------------------------ update counts (Fig. 2's axis)
