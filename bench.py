@@ -231,8 +231,11 @@ def whole_job_value(units_per_step: float, steps: int, world: int, ms: float) ->
 
 # ------------------------------------------------------------------ oracle arm
 
-def oracle_solve_time(name, scale, omega):
-    """One FIFO ImprovedBLISOR solve (FP64, one host thread) of the workload at `scale`."""
+def oracle_solve_time(name, scale, omega, allcore=True):
+    """One FIFO ImprovedBLISOR solve (FP64, one host thread) of the workload at `scale`,
+    and the synchronous push rounds of Alg. 1 (omega 1, FP64) on every host core.
+
+    Returns (fifo seconds, nnz, fifo finished, rounds seconds, threads, rounds, rounds finished)."""
     import oracle
     spec, g, src, dst, w = make_workload(name, scale)
     rp, col, wc = oracle.csr_from_arcs(g["n"], src, dst, w)
@@ -240,7 +243,12 @@ def oracle_solve_time(name, scale, omega):
     t0 = time.perf_counter()
     z, r, pushes, upd, ok = oracle.blisor_fifo(g["n"], rp, col, wc, s, EPS, omega)
     dt = time.perf_counter() - t0
-    return dt, int(rp[-1]), ok
+    if not allcore:
+        return dt, int(rp[-1]), ok, None, 0, 0, False
+    t0 = time.perf_counter()
+    _, _, _, _, rounds, ok_r, threads = oracle.push_rounds_threads(g["n"], rp, col, wc, s, EPS, 1.0)
+    dt_r = time.perf_counter() - t0
+    return dt, int(rp[-1]), ok, dt_r, threads, rounds, ok_r
 
 
 def run_reference(args):
@@ -445,19 +453,25 @@ def run_gpu(args):
         _, _, _, tr = G.solve_trace(s_d, out=z_d, **opts)
         detail["trace"] = [[round(float(a), 4), int(b), float(c), int(d)] for a, b, c, d in tr]
 
-    cpu = None
+    cpu = cpu_all = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu_scale = args.cpu_scale if args.cpu_scale is not None else spec.get("cpu_scale")
-        dt, nnz_c, ok = oracle_solve_time(args.workload, cpu_scale, omega)
+        dt, nnz_c, ok, dt_r, threads, rounds, ok_r = oracle_solve_time(args.workload, cpu_scale, omega)
         scale_f = nnz_c / ginfo["nnz"]
         hc = host_cpu()
+        where = ("the full workload" if cpu_scale is None else
+                 f"the same generator at scale {cpu_scale} (a bounded sample: a full-size solve "
+                 f"takes minutes; bench.py --impl reference times full-size solves), rate scaled "
+                 f"by nnz {nnz_c}/{ginfo['nnz']}")
         cpu = {"value": scale_f / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
                "sample": (f"one FIFO ImprovedBLISOR solve (omega={omega}, eps={EPS}, FP64, one host thread) of "
-                          + ("the full workload" if cpu_scale is None else
-                             f"the same generator at scale {cpu_scale} (a bounded sample: a full-size solve "
-                             f"takes minutes; bench.py --impl reference times full-size solves), rate scaled "
-                             f"by nnz {nnz_c}/{ginfo['nnz']}") + f", {dt:.1f} s"),
+                          + where + f", {dt:.1f} s"),
                "host_cpu": hc["model"], "host_cores": hc["host_cores"]}
+        cpu_all = {"value": scale_f / dt_r, "unit": "solves/s", "cores": threads, "kind": "oracle",
+                   "sample": (f"the synchronous push rounds of Alg. 1 (omega 1, eps={EPS}, FP64; {rounds} rounds"
+                              f"{'' if ok_r else ', unfinished'}) on {threads} host threads of " + where
+                              + f", {dt_r:.1f} s"),
+                   "host_cpu": hc["model"], "host_cores": hc["host_cores"]}
 
     if rank == 0:
         line = {
@@ -479,7 +493,8 @@ def run_gpu(args):
             # solve launches plus the five of each metrics call
             "gpu_launches": int(sum(i["launches"] for i in (infos if cols is not None else infos[::k])))
             + 5 * args.steps * (k if cols is not None else 1),
-            "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "detail": detail,
+            "roofline": roofline, "cpu_baseline": cpu, "cpu_baseline_allcore": cpu_all, "clocks": clocks,
+            "detail": detail,
         }
         print(json.dumps(line), flush=True)
     G.close()
@@ -801,7 +816,7 @@ def run_warm(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu_scale = args.cpu_scale if args.cpu_scale is not None else spec.get("cpu_scale")
-        dt, nnz_c, ok = oracle_solve_time(args.workload, cpu_scale, omega)
+        dt, nnz_c, ok = oracle_solve_time(args.workload, cpu_scale, omega, allcore=False)[:3]
         cpu = {"value": (nnz_c / ginfo["nnz"]) / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
                "sample": (f"one FIFO ImprovedBLISOR solve (omega={omega}, eps={EPS}, FP64, zero start, one host "
                           f"thread) of the same generator at scale {cpu_scale}, rate scaled by nnz "

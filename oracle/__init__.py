@@ -39,7 +39,7 @@ def build(force: bool = False) -> str:
     fd, tmp = tempfile.mkstemp(suffix=".so", dir=_BUILD)
     os.close(fd)
     subprocess.run(["gcc", "-O2", "-std=c11", "-fno-fast-math", "-ffp-contract=off", "-shared",
-                    "-fPIC", src, "-o", tmp, "-lm"], check=True)
+                    "-fPIC", "-pthread", src, "-o", tmp, "-lm"], check=True)
     os.replace(tmp, _SO)
     return _SO
 
@@ -55,6 +55,8 @@ def _lib():
     lib.oracle_blisor_fifo.restype = ctypes.c_int
     lib.oracle_push_rounds.argtypes = [I64, VP, VP, VP, VP, D, D, D, D, I64, VP, VP, VP]
     lib.oracle_push_rounds.restype = ctypes.c_int
+    lib.oracle_push_rounds_threads.argtypes = [I64, VP, VP, VP, VP, D, D, D, D, I64, ctypes.c_int, VP, VP, VP]
+    lib.oracle_push_rounds_threads.restype = ctypes.c_int
     lib.oracle_sor_truth.argtypes = [I64, VP, VP, VP, VP, D, D, I64, VP, VP]
     lib.oracle_sor_truth.restype = I64
     lib.oracle_gs_sweep_from_zero.argtypes = [I64, VP, VP, VP, VP, VP]
@@ -247,6 +249,26 @@ def push_rounds(n, row_ptr, col, w, s, eps, omega=1.0, c=C_DEFAULT, sigma=SIGMA_
     if rc < 0:
         raise MemoryError("oracle allocation failed")
     return z, r, int(stats[0]), int(stats[1]), int(stats[2]), rc == 0
+
+
+def push_rounds_threads(n, row_ptr, col, w, s, eps, omega=1.0, threads=None, c=C_DEFAULT,
+                        sigma=SIGMA_DEFAULT, max_rounds=1 << 40):
+    """push_rounds on `threads` host threads (default: every core), for the
+    all-core CPU baseline; bit for bit push_rounds' result.
+
+    Returns ``(z, r, pushes, updates, rounds, finished, threads_used)``.
+    """
+    row_ptr, col, w64 = _graph_args(row_ptr, col, w)
+    s = np.ascontiguousarray(s, np.float64)
+    threads = int(threads or os.cpu_count() or 1)
+    z = np.empty(n)
+    r = np.empty(n)
+    stats = np.zeros(4, np.int64)
+    rc = _lib().oracle_push_rounds_threads(n, _p(row_ptr), _p(col), _p(w64), _p(s), eps, omega, c, sigma,
+                                           max_rounds, threads, _p(z), _p(r), _p(stats))
+    if rc < 0:
+        raise MemoryError("oracle allocation failed")
+    return z, r, int(stats[0]), int(stats[1]), int(stats[2]), rc == 0, int(stats[3])
 
 
 def sor_ordered(n, row_ptr, col, w, s, order, eps, omega, c=C_DEFAULT, sigma=SIGMA_DEFAULT,

@@ -13,9 +13,13 @@
  * a_uv * delta to r_u for every u with a_uv > 0, i.e. every in-neighbour of v
  * (Eqs. sor1-sor3 of Section 5.2; Alg. 1 is the omega = 1 case).
  *
- * Everything is sequential, scalar and in FP64.
+ * Everything is sequential, scalar and in FP64, except
+ * oracle_push_rounds_threads, which runs the rounds of oracle_push_rounds on
+ * several host threads (the all-core CPU baseline) with the same arithmetic.
  */
+#define _POSIX_C_SOURCE 200809L /* pthread barriers */
 #include <math.h>
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -285,6 +289,162 @@ int oracle_push_rounds(int64_t n, const int64_t *row_ptr, const int32_t *col, co
     if (stats) { stats[0] = pushes; stats[1] = updates; stats[2] = rounds; }
     for (int64_t v = 0; v < n; ++v) z_out[v] -= c_eff;
     free(d); free(sp); free(delta); free(indeg);
+    return rc;
+}
+
+/*
+ * The same synchronous rounds as oracle_push_rounds on nthreads host threads,
+ * for the all-core CPU baseline.  Threads own contiguous row ranges of about
+ * equal nonzeros; a round is the two loops of oracle_push_rounds, each thread
+ * over its own rows, with a barrier after each, so every row's arithmetic is
+ * the sequential one (results are bit for bit those of oracle_push_rounds).
+ * Workers wait for a start signal, given once every thread exists, with the
+ * number of threads that did start.  Returns 0, 1 at max_rounds, or -1 on
+ * allocation failure.
+ */
+typedef struct {
+    int64_t n;
+    const int64_t *row_ptr;
+    const int32_t *col;
+    const double *w;
+    const double *d, *sp;
+    const int64_t *indeg;
+    double *delta, *z, *r;
+    double epsp, omega;
+    int64_t max_rounds;
+    int nth;                /* threads taking part (set before the start signal) */
+    int64_t *lo;            /* nth + 1 row boundaries */
+    int64_t *active, *upd;  /* per thread, per round */
+    pthread_barrier_t bar;
+    pthread_mutex_t mu;
+    pthread_cond_t cv;
+    int go;
+    int64_t rounds, pushes, updates;
+    int rc;
+} rounds_ctx;
+
+typedef struct {
+    rounds_ctx *c;
+    int t;
+} rounds_arg;
+
+static void rounds_run(rounds_ctx *c, int t)
+{
+    const int64_t v0 = c->lo[t], v1 = c->lo[t + 1];
+    int64_t rounds = 0;
+    for (;;) {
+        int64_t act = 0, up = 0;
+        for (int64_t v = v0; v < v1; ++v) {
+            c->delta[v] = 0.0;
+            if (fabs(c->r[v]) > c->epsp * c->sp[v]) {
+                c->delta[v] = c->omega * c->r[v] / (1.0 + c->d[v]);
+                c->z[v] += c->delta[v];
+                c->r[v] = (1.0 - c->omega) * c->r[v];
+                ++act;
+                up += c->indeg[v];
+            }
+        }
+        c->active[t] = act;
+        c->upd[t] = up;
+        pthread_barrier_wait(&c->bar);
+        int64_t total = 0;
+        for (int i = 0; i < c->nth; ++i) total += c->active[i];
+        if (total == 0) break;
+        if (t == 0) {
+            c->pushes += total;
+            for (int i = 0; i < c->nth; ++i) c->updates += c->upd[i];
+        }
+        ++rounds;
+        for (int64_t u = v0; u < v1; ++u) {
+            double acc = 0.0;
+            for (int64_t k = c->row_ptr[u]; k < c->row_ptr[u + 1]; ++k)
+                acc += (c->w ? c->w[k] : 1.0) * c->delta[c->col[k]];
+            c->r[u] += acc;
+        }
+        pthread_barrier_wait(&c->bar);
+        if (rounds >= c->max_rounds) {
+            if (t == 0) c->rc = 1;
+            break;
+        }
+    }
+    if (t == 0) c->rounds = rounds;
+}
+
+static void *rounds_worker(void *p)
+{
+    rounds_arg *a = (rounds_arg *)p;
+    rounds_ctx *c = a->c;
+    pthread_mutex_lock(&c->mu);
+    while (!c->go) pthread_cond_wait(&c->cv, &c->mu);
+    pthread_mutex_unlock(&c->mu);
+    if (a->t < c->nth) rounds_run(c, a->t);
+    return NULL;
+}
+
+int oracle_push_rounds_threads(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *w,
+                               const double *s, double eps, double omega, double c, double sigma,
+                               int64_t max_rounds, int nthreads, double *z_out, double *r_out, int64_t *stats)
+{
+    if (nthreads < 1) nthreads = 1;
+    rounds_ctx *ctx = (rounds_ctx *)calloc(1, sizeof(rounds_ctx));
+    double *d = (double *)malloc(sizeof(double) * ((size_t)n + 1));
+    double *sp = (double *)malloc(sizeof(double) * ((size_t)n + 1));
+    double *delta = (double *)malloc(sizeof(double) * ((size_t)n + 1));
+    int64_t *indeg = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    int64_t *lo = (int64_t *)malloc(sizeof(int64_t) * ((size_t)nthreads + 1));
+    int64_t *cnt = (int64_t *)calloc(2 * (size_t)nthreads, sizeof(int64_t));
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)nthreads);
+    rounds_arg *args = (rounds_arg *)malloc(sizeof(rounds_arg) * (size_t)nthreads);
+    int rc = -1;
+    if (!ctx || !d || !sp || !delta || !indeg || !lo || !cnt || !th || !args) goto out;
+    out_degree(n, row_ptr, w, d);
+    for (int64_t k = 0; k < row_ptr[n]; ++k) indeg[col[k]]++;
+    const double c_eff = shift_of(n, s, c);
+    for (int64_t v = 0; v < n; ++v) {
+        sp[v] = s[v] + c_eff;
+        r_out[v] = sp[v];
+        z_out[v] = 0.0;
+    }
+    ctx->n = n; ctx->row_ptr = row_ptr; ctx->col = col; ctx->w = w; ctx->d = d; ctx->sp = sp;
+    ctx->indeg = indeg; ctx->delta = delta; ctx->z = z_out; ctx->r = r_out;
+    ctx->epsp = sigma * eps / (c + sigma); ctx->omega = omega; ctx->max_rounds = max_rounds;
+    ctx->lo = lo; ctx->active = cnt; ctx->upd = cnt + nthreads;
+    pthread_mutex_init(&ctx->mu, NULL);
+    pthread_cond_init(&ctx->cv, NULL);
+    int started = 1;  /* this thread is thread 0 */
+    for (int t = 1; t < nthreads; ++t) {
+        args[t].c = ctx;
+        args[t].t = t;
+        if (pthread_create(&th[t], NULL, rounds_worker, &args[t]) != 0) break;
+        ++started;
+    }
+    /* row ranges of about (nnz + n) / started nonzeros plus rows each */
+    {
+        const double per = (double)(row_ptr[n] + n) / started;
+        int64_t v = 0;
+        lo[0] = 0;
+        for (int t = 1; t < started; ++t) {
+            while (v < n && (double)(row_ptr[v] + v) < per * t) ++v;
+            lo[t] = v;
+        }
+        lo[started] = n;
+    }
+    ctx->nth = started;
+    pthread_barrier_init(&ctx->bar, NULL, (unsigned)started);
+    pthread_mutex_lock(&ctx->mu);
+    ctx->go = 1;
+    pthread_cond_broadcast(&ctx->cv);
+    pthread_mutex_unlock(&ctx->mu);
+    rounds_run(ctx, 0);
+    for (int t = 1; t < started; ++t) pthread_join(th[t], NULL);
+    pthread_barrier_destroy(&ctx->bar);
+    pthread_cond_destroy(&ctx->cv);
+    pthread_mutex_destroy(&ctx->mu);
+    rc = ctx->rc;
+    if (stats) { stats[0] = ctx->pushes; stats[1] = ctx->updates; stats[2] = ctx->rounds; stats[3] = started; }
+    for (int64_t u = 0; u < n; ++u) z_out[u] -= c_eff;
+out:
+    free(ctx); free(d); free(sp); free(delta); free(indeg); free(lo); free(cnt); free(th); free(args);
     return rc;
 }
 

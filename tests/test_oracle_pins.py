@@ -319,6 +319,35 @@ def test_round_schedule_meets_same_bound():
     assert np.all(np.abs(z - z_star) <= epsp * (z_star + c_eff) + 1e-14)
 
 
+@pytest.mark.parametrize("directed,weighted", [(False, False), (True, True)])
+@pytest.mark.parametrize("threads", [1, 2, 5, 16])
+def test_threaded_rounds_equal_sequential_rounds(directed, weighted, threads):
+    """The all-core baseline's threaded rounds are the sequential rounds: every
+    row's arithmetic is the same, so z, r and the counts agree bit for bit
+    (which also pins them to the LU-checked rounds above); more threads than
+    rows and an empty graph included."""
+    n = 700
+    rp, col, w = random_graph(n, 0.01, directed, weighted, seed=31)
+    s = np.random.default_rng(5).random(n)
+    seq = oracle.push_rounds(n, rp, col, w, s, 1e-6, 1.0)
+    thr = oracle.push_rounds_threads(n, rp, col, w, s, 1e-6, 1.0, threads=threads)
+    assert np.array_equal(seq[0], thr[0]) and np.array_equal(seq[1], thr[1])
+    assert seq[2:6] == thr[2:6] and thr[6] == threads
+    z_star = oracle.lu_solve(n, rp, col, w, s)
+    c_eff, epsp = oracle.shift_params(s, 1e-6)
+    assert np.all(np.abs(thr[0] - z_star) <= epsp * (z_star + c_eff) + 1e-13)
+    # three rows, more threads than rows; and no rows at all
+    rp3 = np.array([0, 1, 2, 2], np.int64)
+    col3 = np.array([1, 0], np.int32)
+    s3 = np.array([0.2, 0.9, 0.5])
+    a = oracle.push_rounds(3, rp3, col3, None, s3, 1e-6, 1.0)
+    b = oracle.push_rounds_threads(3, rp3, col3, None, s3, 1e-6, 1.0, threads=threads)
+    assert np.array_equal(a[0], b[0]) and a[2:6] == b[2:6]
+    e = oracle.push_rounds_threads(0, np.zeros(1, np.int64), np.zeros(0, np.int32), None, np.zeros(0), 1e-6,
+                                   1.0, threads=threads)
+    assert e[0].shape == (0,) and e[2] == 0 and e[5]
+
+
 def test_signed_opinions_shift():
     n, rp, col, w, s = small_ba(n=800)
     s = 2 * s - 1.0
