@@ -32,7 +32,7 @@ WORKLOADS = {
     # name: generator, precision, omega, schedule
     "rmat22_dir": dict(gen="rmat_dir", scale=22, precision="fp32", omega=1.6, palette=8),
     "ba20k": dict(gen="ba", n=20000, precision="fp64", omega=1.5),
-    "rmat24_und": dict(gen="rmat_und", scale=24, precision="fp32", omega=1.8, cpu_scale=20),
+    "rmat24_und": dict(gen="rmat_und", scale=24, precision="fp32", omega=1.8, palette=12, cpu_scale=20),
     "rmat23_und": dict(gen="rmat_und", scale=23, precision="fp32", omega=1.8, cpu_scale=20),
     "rmat22_und": dict(gen="rmat_und", scale=22, precision="fp32", omega=1.8, cpu_scale=20),
     "rmat16_dir": dict(gen="rmat_dir", scale=16, precision="fp32", omega=1.6),
