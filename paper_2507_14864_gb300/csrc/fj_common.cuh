@@ -39,6 +39,17 @@ inline cudaError_t dev_malloc(T **p, size_t bytes)
         if (fj_s_ != FJ_OK) return fj_s_;            \
     } while (0)
 
+// Bounds-checked index for a kernel: true when 0 <= idx < lim; otherwise
+// the first failure is stored in rec[4] (a __device__ long long array of the
+// translation unit) as (site, block, index, limit) and the caller skips the
+// access; the host turns the record into an error.
+#define FJ_IDX_OK_REC(rec, site, idx, lim)                                                            \
+    ((idx) >= 0 && (idx) < (lim)                                                                      \
+         ? true                                                                                       \
+         : (atomicCAS((unsigned long long *)&(rec)[0], 0ULL, (unsigned long long)(site)) == 0ULL     \
+                ? ((rec)[1] = blockIdx.x, (rec)[2] = (long long)(idx), (rec)[3] = (long long)(lim), false) \
+                : false))
+
 #define FJ_ARG(cond, msg)                                                 \
     do {                                                                  \
         if (!(cond)) {                                                    \

@@ -10,6 +10,13 @@
 #include "fj_internal.cuh"
 
 namespace fj {
+// first out-of-range index of the batch measures (see FJ_IDX_OK_REC)
+__device__ long long g_fj_metric_dbg[4];
+}  // namespace fj
+#define FJ_IDX_OK(site, idx, lim) FJ_IDX_OK_REC(fj::g_fj_metric_dbg, site, idx, lim)
+#include "fj_tile.cuh"
+
+namespace fj {
 
 // Deterministic block sum of NV values (thread 0 ends with the totals).
 template <int NV>
@@ -108,60 +115,106 @@ __global__ void k_metric_mean_div(int ng, const int64_t *__restrict__ node_off, 
     if (gi < ng) mean[gi] /= (double)(node_off[gi + 1] - node_off[gi]);
 }
 
-// Multi-vector measures: S and Z node-major [n][k], k <= 64.  Lanes own
-// vectors j = lane and lane + 32; warps take rows with a fixed stride, so every
-// partial sum has a fixed order.  Pass 1: sum z per vector.  Pass 2: C, P, I
-// and the arc sum of a (z_x - z_c)^2.  Partials per block, reduced in block
-// order by k_metric_batch_reduce.
+// Multi-vector measures: S and Z node-major [n][k], k <= 64, lanes owning
+// vectors j = lane and lane + 32.  Pass 1 (k_metric_batch_sum): the sum of z
+// per vector, warps taking rows with a fixed stride.  Pass 2
+// (k_metric_batch_items): C, P, I and the arc sum of a (z_x - z_c)^2 over the
+// warp-tile item plan, warps taking items with a fixed stride: a tile's rows
+// are walked by warp_tile_k (D neighbour rows in flight for both halves), a
+// long row's 512-nonzero chunks are items of their own spread over the warps
+// (the arc sum is a plain sum over arcs, so a chunk's part joins the warp's
+// running sum directly), and the row's own terms are taken with its first
+// chunk.  Partials per block, reduced in block order by
+// k_metric_batch_reduce: every sum has a fixed order.
 constexpr int kMetricBatchBlocks = 152 * 4;
 
-template <bool W>
 __global__ void __launch_bounds__(256)
-k_metric_batch(int pass, int64_t n, int k, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
-               const float *__restrict__ w, const double *__restrict__ S, const double *__restrict__ Z,
-               const double *__restrict__ mean, double *__restrict__ part)
+k_metric_batch_sum(int64_t n, int k, const double *__restrict__ Z, double *__restrict__ part)
 {
-    __shared__ double red[8][4][64];
+    __shared__ double red[8][64];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const int64_t warp = (int64_t)blockIdx.x * 8 + wl, nwarps = (int64_t)gridDim.x * 8;
     const bool has[2] = {lane < k, lane + 32 < k};
-    double acc[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
-    double mu[2] = {0, 0};
-    if (pass == 2)
+    double acc[2] = {0.0, 0.0};
+    for (int64_t x = warp; x < n; x += nwarps)
+#pragma unroll
         for (int hh = 0; hh < 2; ++hh)
-            if (has[hh]) mu[hh] = mean[lane + 32 * hh];
-    for (int64_t x = warp; x < n; x += nwarps) {
+            if (has[hh]) acc[hh] += Z[x * k + lane + 32 * hh];
+    for (int hh = 0; hh < 2; ++hh) red[wl][lane + 32 * hh] = acc[hh];
+    __syncthreads();
+    for (int j = threadIdx.x; j < k; j += 256) {
+        double t = 0.0;
+        for (int ww = 0; ww < 8; ++ww) t += red[ww][j];
+        part[(int64_t)blockIdx.x * k + j] = t;
+    }
+}
+
+template <bool W>
+__global__ void __launch_bounds__(256)
+k_metric_batch_items(const Item *__restrict__ items, int64_t nitems, int64_t n, int k,
+                     const int64_t *__restrict__ rp, const int32_t *__restrict__ col, const float *__restrict__ w,
+                     const double *__restrict__ S, const double *__restrict__ Z, const double *__restrict__ mean,
+                     double *__restrict__ part)
+{
+    __shared__ double red[8][4][64];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const bool has1 = lane < k, has2 = lane + 32 < k;
+    const bool has[2] = {has1, has2};
+    double acc[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+    const double mu[2] = {has1 ? mean[lane] : 0.0, has2 ? mean[lane + 32] : 0.0};
+    double zx[2] = {0.0, 0.0};  // the current row's z, per half
+    auto begin = [&](int64_t x) {
+        zx[0] = has1 ? Z[x * k + lane] : 0.0;
+        zx[1] = has2 ? Z[x * k + lane + 32] : 0.0;
+    };
+    auto src = [&](int32_t c) -> const double * { return Z + (int64_t)c * k; };
+    auto add = [&](double &a, float wt, double v, int h) {
+        const double d = zx[h] - v;
+        a += (W ? (double)wt : 1.0) * d * d;
+    };
+    auto row_terms = [&](int64_t x) {
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh) {
             if (!has[hh]) continue;
-            const int j = lane + 32 * hh;
-            const double zx = Z[x * k + j];
-            if (pass == 1) {
-                acc[hh][0] += zx;
-            } else {
-                const double sx = S[x * k + j];
-                acc[hh][0] += zx * zx;
-                acc[hh][1] += (zx - mu[hh]) * (zx - mu[hh]);
-                acc[hh][2] += (zx - sx) * (zx - sx);
-                double dd = 0.0;
-                for (int64_t kk = rp[x]; kk < rp[x + 1]; ++kk) {
-                    const double d = zx - Z[(int64_t)col[kk] * k + j];
-                    dd += (W ? (double)w[kk] : 1.0) * d * d;
-                }
-                acc[hh][3] += dd;
-            }
+            const double sx = S[x * k + lane + 32 * hh], z = zx[hh];
+            acc[hh][0] += z * z;
+            acc[hh][1] += (z - mu[hh]) * (z - mu[hh]);
+            acc[hh][2] += (z - sx) * (z - sx);
+        }
+    };
+    for (int64_t ii = (int64_t)blockIdx.x * 8 + wl; ii < nitems; ii += (int64_t)gridDim.x * 8) {
+        const Item it = items[ii];
+        const int64_t r0 = it.r0, r1 = it.r1;
+        if (!FJ_IDX_OK(1, r0, n) || !FJ_IDX_OK(2, r1, n + 1) ||
+            (it.slot < 0 && !FJ_IDX_OK(3, r1 - r0, kWarpRows + 1)))
+            continue;
+        if (it.slot < 0) {
+            auto apply = [&](int64_t x, double s1, double s2) {
+                row_terms(x);  // zx is row x's until the next row begins
+                acc[0][3] += s1;
+                acc[1][3] += s2;
+            };
+            warp_tile_k<double, double, W, 8>(r0, r1, it.k0, it.k1, false, rp, col, w, begin, src, add, apply, lane,
+                                              has1, has2, n);
+        } else {
+            auto apply = [&](int64_t, double s1, double s2) {
+                acc[0][3] += s1;
+                acc[1][3] += s2;
+            };
+            warp_tile_k<double, double, W, 8>(r0, r0 + 1, it.k0, it.k1, true, rp, col, w, begin, src, add, apply,
+                                              lane, has1, has2, n);
+            if (it.k0 == rp[r0]) row_terms(r0);  // the row's own terms, once
         }
     }
-    const int nf = pass == 1 ? 1 : 4;
     for (int hh = 0; hh < 2; ++hh)
-        for (int f = 0; f < nf; ++f) red[wl][f][lane + 32 * hh] = acc[hh][f];
+        for (int f = 0; f < 4; ++f) red[wl][f][lane + 32 * hh] = acc[hh][f];
     __syncthreads();
-    for (int i = threadIdx.x; i < nf * 64; i += 256) {
+    for (int i = threadIdx.x; i < 4 * 64; i += 256) {
         const int f = i / 64, j = i % 64;
         if (j >= k) continue;
         double t = 0.0;
         for (int ww = 0; ww < 8; ++ww) t += red[ww][f][j];
-        part[((int64_t)blockIdx.x * nf + f) * k + j] = t;
+        part[((int64_t)blockIdx.x * 4 + f) * k + j] = t;
     }
 }
 
@@ -277,12 +330,17 @@ extern "C" fj_status fj_metrics_batch(fj_graph *g, const double *S, const double
         Sd = stage;
         Zd = stage + n * k;
     }
-    if (c.w) k_metric_batch<true><<<nb, 256, 0, st>>>(1, n, k, c.row_ptr, c.col, c.w, Sd, Zd, mean, part);
-    else k_metric_batch<false><<<nb, 256, 0, st>>>(1, n, k, c.row_ptr, c.col, c.w, Sd, Zd, mean, part);
+    const ItemPlan *ip = nullptr;
+    FJ_CHECK(plain_items(g, st, &ip));
+    k_metric_batch_sum<<<nb, 256, 0, st>>>(n, k, Zd, part);
     k_metric_batch_reduce<<<1, 64, 0, st>>>(nb, 1, k, part, mean);
     k_metric_batch_mean<<<1, 64, 0, st>>>(k, n, mean);
-    if (c.w) k_metric_batch<true><<<nb, 256, 0, st>>>(2, n, k, c.row_ptr, c.col, c.w, Sd, Zd, mean, part);
-    else k_metric_batch<false><<<nb, 256, 0, st>>>(2, n, k, c.row_ptr, c.col, c.w, Sd, Zd, mean, part);
+    if (c.w)
+        k_metric_batch_items<true><<<nb, 256, 0, st>>>(ip->items, ip->nitems, n, k, c.row_ptr, c.col, c.w, Sd, Zd,
+                                                       mean, part);
+    else
+        k_metric_batch_items<false><<<nb, 256, 0, st>>>(ip->items, ip->nitems, n, k, c.row_ptr, c.col, c.w, Sd, Zd,
+                                                        mean, part);
     k_metric_batch_reduce<<<1, 256, 0, st>>>(nb, 4, k, part, res);
     FJ_CUDA(cudaGetLastError());
     std::vector<double> hres((size_t)4 * k), hmean((size_t)k);
@@ -290,6 +348,15 @@ extern "C" fj_status fj_metrics_batch(fj_graph *g, const double *S, const double
     FJ_CUDA(cudaMemcpyAsync(hmean.data(), mean, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
     FJ_CUDA(cudaFreeAsync(buf, st));
     FJ_CUDA(cudaStreamSynchronize(st));
+    long long dbg[4] = {0, 0, 0, 0};
+    FJ_CUDA(cudaMemcpyFromSymbol(dbg, g_fj_metric_dbg, sizeof(dbg)));
+    if (dbg[0]) {
+        const long long zero[4] = {0, 0, 0, 0};
+        FJ_CUDA(cudaMemcpyToSymbol(g_fj_metric_dbg, zero, sizeof(zero)));
+        set_error("index check failed in the batch measures: site %lld block %lld index %lld limit %lld", dbg[0],
+                  dbg[1], dbg[2], dbg[3]);
+        return FJ_ERR_INVALID_ARG;
+    }
     for (int j = 0; j < k; ++j) {
         out[j].C = hres[(size_t)0 * k + j];
         out[j].P = hres[(size_t)1 * k + j];

@@ -195,12 +195,10 @@ __device__ __forceinline__ T arc_w(const float *__restrict__ w, int64_t k)
 // is skipped, and the host turns the record into an error.  The checks cost one
 // compare per nonzero in kernels that are bound by memory traffic.
 __device__ long long g_fj_dbg[4];
-#define FJ_IDX_OK(site, idx, lim)                                                     \
-    ((idx) >= 0 && (idx) < (lim)                                                      \
-         ? true                                                                       \
-         : (atomicCAS((unsigned long long *)&g_fj_dbg[0], 0ULL, (unsigned long long)(site)) == 0ULL \
-                ? (g_fj_dbg[1] = blockIdx.x, g_fj_dbg[2] = (long long)(idx), g_fj_dbg[3] = (long long)(lim), false) \
-                : false))
+#define FJ_IDX_OK(site, idx, lim) FJ_IDX_OK_REC(g_fj_dbg, site, idx, lim)
+}  // namespace fj
+#include "fj_tile.cuh"
+namespace fj {
 
 // ============================================================== sweep: gather and apply
 
@@ -2416,90 +2414,6 @@ __global__ void k_unshift_batch(int64_t n, int k, const double *__restrict__ zha
     }
 }
 
-// Walk of one warp tile for k right-hand sides.  Lane j owns vectors j and
-// j + 32.  Columns and weights are read 32 nonzeros at a time (one coalesced
-// load per lane) and broadcast by shuffles; D gathers of the neighbours'
-// k-vectors (contiguous in the node-major layout) are issued before any is
-// consumed.  Rows are finished as the walk passes their ends, so short rows
-// share load batches.  begin(x) is called when row x becomes current (to
-// start its own loads early); src(c) gives the k-vector read for column c;
-// add(acc, a, v) accumulates a * v; apply(x, acc1, acc2) receives row x's
-// sums.  A chunk of a long row (chunk = true) sums [k0, k1) of row r0 and
-// calls apply once.
-template <typename Acc, typename V, bool W, int D, typename Begin, typename Src, typename Add, typename Apply>
-__device__ __forceinline__ void warp_tile_k(int64_t r0, int64_t r1, int64_t k0, int64_t k1, bool chunk,
-                                            const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
-                                            const float *__restrict__ w, Begin begin, Src src, Add add, Apply apply,
-                                            int lane, bool has1, bool has2, int64_t n_rows)
-{
-    constexpr unsigned FULL = 0xffffffffu;
-    static_assert(32 % D == 0, "gather depth divides the load batch");
-    // row ends of the tile (at most kWarpRows = 64 rows): lane i holds the ends of rows r0+i and r0+32+i
-    int64_t e_lo = k1, e_hi = k1;
-    if (!chunk) {
-        if (r0 + lane < r1) e_lo = rp[r0 + lane + 1];
-        if (r0 + 32 + lane < r1) e_hi = rp[r0 + 33 + lane];
-    } else {
-        r1 = r0 + 1;
-    }
-    int64_t x = r0;
-    auto row_end = [&](int64_t xx) -> int64_t {
-        const int i = (int)(xx - r0);
-        return __shfl_sync(FULL, i < 32 ? e_lo : e_hi, i & 31);
-    };
-    int64_t xe = x < r1 ? row_end(x) : k1;
-    if (x < r1) begin(x);
-    Acc a1{}, a2{};
-    auto flush_until = [&](int64_t pos) {
-        while (x < r1 && xe <= pos) {
-            apply(x, a1, a2);
-            a1 = Acc{};
-            a2 = Acc{};
-            ++x;
-            if (x < r1) {
-                xe = row_end(x);
-                begin(x);
-            }
-        }
-    };
-    for (int64_t base = k0; base < k1; base += 32) {
-        const int64_t kk = base + lane;
-        int32_t cl = 0;
-        float al = 0.f;
-        if (kk < k1) {
-            cl = __ldg(col + kk);
-            al = W ? __ldg(w + kk) : 1.f;
-            if (!FJ_IDX_OK(15, cl, n_rows)) {
-                cl = 0;
-                al = 0.f;
-            }
-        }
-        const int m = (int)(k1 - base < 32 ? k1 - base : 32);
-        for (int t = 0; t < m; t += D) {
-            V v1[D], v2[D];
-            float aa[D];
-#pragma unroll
-            for (int u = 0; u < D; ++u) {
-                const int32_t c = __shfl_sync(FULL, cl, (t + u) & 31);
-                aa[u] = __shfl_sync(FULL, al, (t + u) & 31);
-                const V *p = src(c);
-                const bool in = t + u < m;
-                v1[u] = (in && has1) ? __ldg(p + lane) : V(0);
-                v2[u] = (in && has2) ? __ldg(p + lane + 32) : V(0);
-            }
-#pragma unroll
-            for (int u = 0; u < D; ++u) {
-                if (t + u < m) {
-                    flush_until(base + t + u);
-                    add(a1, aa[u], v1[u]);
-                    add(a2, aa[u], v2[u]);
-                }
-            }
-        }
-    }
-    flush_until(k1);
-}
-
 // One colour class of a multi-RHS sweep: the update of k_sweep applied to k
 // opinion vectors at once, one warp per warp tile.  A long row's chunks keep
 // k partial sums each and the last chunk to finish applies the update.
@@ -2738,6 +2652,15 @@ k_certify_batch(const Item *__restrict__ items, int64_t nitems, const int64_t *_
         if (!FJ_IDX_OK(1, r0, n_rows) || !FJ_IDX_OK(2, r1, n_rows + 1) ||
             (it.slot < 0 && !FJ_IDX_OK(13, r1 - r0, kWarpRows + 1)))
             continue;
+        auto add_fix = [&](FixAcc &acc, float a, double v) {
+            if (W) {
+                const double av = (double)a, pr = __dmul_rn(av, v);
+                fix_add(acc.v, pr, fixE, acc.bad);
+                fix_add(acc.v, fma(av, v, -pr), fixE, acc.bad);  // the product's rounding error
+            } else {
+                fix_add(acc.v, v, fixE, acc.bad);
+            }
+        };
         if (it.slot < 0) {
             auto short_row = [&](int64_t x, PlainAcc s1, PlainAcc s2) {
                 const int64_t len = rp[x + 1] - rp[x];
@@ -2755,15 +2678,6 @@ k_certify_batch(const Item *__restrict__ items, int64_t nitems, const int64_t *_
             const int ci = (int)((it.k0 - rp[r0]) / kWarpChunk);
             unsigned long long *pc =
                 reinterpret_cast<unsigned long long *>(partk) + 2 * ((int64_t)(first + ci) * k + lane);
-            auto add_fix = [&](FixAcc &acc, float a, double v) {
-                if (W) {
-                    const double av = (double)a, pr = __dmul_rn(av, v);
-                    fix_add(acc.v, pr, fixE, acc.bad);
-                    fix_add(acc.v, fma(av, v, -pr), fixE, acc.bad);  // the product's rounding error
-                } else {
-                    fix_add(acc.v, v, fixE, acc.bad);
-                }
-            };
             auto put = [&](unsigned long long *q, const FixAcc &a) {
                 const bool b = a.bad || fix_bad;
                 q[0] = b ? 0ull : (unsigned long long)a.v;

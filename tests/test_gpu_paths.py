@@ -229,6 +229,54 @@ def test_frontier_long_scatter(capi, monkeypatch, long_min):
         assert ran >= 1, "no solve reached the frontier cleanup"
 
 
+# ------------------------------------------------------------ certificate against the exact residual
+
+def _oracle_stats(n, rp, col, w, s, z):
+    """max_v |r_v| and max_v |r_v| / s'_v of the exact residual of z."""
+    ce = oracle.shift_params(s, 1e-6)[0]
+    r = oracle.residual_accurate(n, rp, col, w, s, z)
+    return float(np.max(np.abs(r))), float(np.max(np.abs(r) / (s + ce)))
+
+
+@pytest.mark.parametrize("kind", ["hubs", "weighted"])
+def test_certificate_statistics_equal_exact_residual(capi, kind):
+    """The certificate's reported max |r| and max |r|/s' equal the oracle's
+    compensated residual of the returned z, on solves stopped early (large
+    residuals, decided mostly far from the threshold).  The hub graph's rows of
+    5000 nonzeros and the weighted R-MAT's long rows are summed by the
+    certificate's 128-bit fixed-point chunks (with the product's FMA error on
+    the weighted graph); the hub rows carry the largest residuals."""
+    if kind == "hubs":
+        n, rp, col, w, s = _hub_graph(5000, 3, 87)
+        directed = False
+    else:
+        g = W.rmat_directed(13, seed_off=88)
+        rp, col, w = csr_of(g)
+        n, s, directed = g["n"], g["S"][0], True
+    assert int(np.max(np.diff(rp))) > 512  # long rows present
+    G = capi.Graph.from_csr(n, *to_dev(rp, col, w), directed=directed)
+    (s_d,) = to_dev(s)
+    for prec in (capi.FJ_PREC_FP32, capi.FJ_PREC_FP64):
+        for sw in (2, 6, 12):
+            z, inf, st = G.solve(s_d, eps=1e-6, omega=1.5, precision=prec, max_sweeps=sw, max_refine=0,
+                                 allow_unconverged=True)
+            a, rel = _oracle_stats(n, rp, col, w, s, z.cpu().numpy())
+            i0 = inf[0]
+            assert i0["resid_inf"] == pytest.approx(a, rel=1e-9, abs=1e-15), (prec, sw)
+            assert i0["resid_rel_max"] == pytest.approx(rel, rel=2e-6), (prec, sw)
+    # the batch certificate, per vector
+    rng = np.random.default_rng(89)
+    k = 4
+    S = np.stack([s, rng.random(n), 1.0 - s, rng.random(n) ** 3], axis=1)
+    (S_d,) = to_dev(np.ascontiguousarray(S))
+    Z, infos, st = G.solve_batch(S_d, eps=1e-6, omega=1.5, max_sweeps=6, max_refine=0, allow_unconverged=True)
+    Zh = Z.cpu().numpy()
+    for j in range(k):
+        a, rel = _oracle_stats(n, rp, col, w, S[:, j], Zh[:, j])
+        assert infos[j]["resid_inf"] == pytest.approx(a, rel=1e-9, abs=1e-15), j
+        assert infos[j]["resid_rel_max"] == pytest.approx(rel, rel=2e-6), j
+
+
 # ------------------------------------------------------------ update counts (Fig. 2's axis)
 
 @pytest.mark.parametrize("omega", [1.0, 1.5])
