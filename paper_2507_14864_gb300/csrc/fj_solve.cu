@@ -1021,8 +1021,12 @@ struct CleanPred {
     int k;
     __device__ bool operator()(int64_t e) const
     {
+        // the FP64 resolution term is read only for an entry above eps' s'
+        // (a NaN residual fails both tests)
+        const double a = fabs(r64[e]), t = epsp * sp[e];
+        if (!(a > t)) return false;
         const int64_t v = k == 1 ? e : e / k;
-        return fabs(r64[e]) > fmax(epsp * sp[e], resid_floor(deg[v], zhat[e]));
+        return a > fmax(t, resid_floor(deg[v], zhat[e]));
     }
 };
 
