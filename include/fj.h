@@ -257,8 +257,11 @@ fj_status fj_graph_order(fj_graph *g, int palette, int32_t *perm, int64_t *nhub,
  * s[n] (FP64) innate opinions; z_out[n] (FP64) receives
  * zhat = (push estimate of (I+L)^{-1}(s + c_eff)) - c_eff.  On FJ_OK every
  * node meets the FP64 certificate |r_v| <= max(eps' s'_v, 2^-51 (1 + d_v)
- * |zhat'_v|), where r = s' - (I + L) zhat' is evaluated with compensated
- * (twice-working-precision) sums.  The second term is the FP64 resolution of
+ * |zhat'_v|), where r = s' - (I + L) zhat' is evaluated with sums good to
+ * twice the working precision (FP32-pair sums with an error bound on short
+ * rows, re-summed in FP64 Dot2 where the bound cannot decide; 128-bit
+ * fixed-point sums on rows over 512 nonzeros, whose truncation bound counts
+ * against the row).  The second term is the FP64 resolution of
  * row v (one ulp of zhat'_v moves r_v by (1 + d_v) ulp); it binds only where
  * eps' s'_v is finer than that (high degree, s'_v near c).  Where the first
  * term binds everywhere, |z_v - zhat_v| <= eps' (z_v + c_eff) (Lemma 5); in
