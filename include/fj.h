@@ -31,6 +31,12 @@
  *
  * A handle is not thread-safe: calls on one handle must not overlap.
  * Separate handles are independent.
+ *
+ * Environment.  FJ_FRONTIER_LONG=<m> (read at each FP64 frontier cleanup of
+ * a solve): in-neighbour lists longer than m are scattered by a block each
+ * rather than a warp (default 4096; 0 sends every entry to the block path).
+ * It changes the schedule of the cleanup's atomic updates, not its result
+ * beyond their order.
  */
 #ifndef FJ_H
 #define FJ_H
